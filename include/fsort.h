@@ -1,0 +1,174 @@
+/*
+ * fsort.h -- C ABI of libfsort, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of the compressed radix sort of "FractalSortCPU:
+ * Bandwidth-Efficient Compressed Radix Sort on CPU" (arXiv 2605.10390).
+ *
+ * Problem (paper Sec. I and II): sort n keys of key_bits bits, optionally
+ * carrying one 32-bit value each, in ascending order of their top
+ * precision_bits bits ("arbitrary-precision keys"; a reduced precision gives
+ * the approximate sort of Sec. I).  The sort is stable: keys whose top bits are
+ * equal keep their input order, which makes the result unique.  Full keys and
+ * values are moved.
+ *
+ * The hot path (every step a CUDA kernel of this library):
+ *   1. digit plan: least-significant-digit-first passes of d-bit digits over
+ *      bits [key_bits - precision_bits, key_bits) (Sec. II);
+ *   2. upfront histogram: every pass's digit counts from one read of the keys
+ *      (the leaf level of the histogram tree of Sec. III-A/B, with counters
+ *      whose width tapers with the size of what they count, Sec. III-D-1);
+ *   3. exclusive scan of each histogram (the rank of Alg. 3 for every leaf);
+ *   4. one stable scatter per pass (Sec. II), skipped on the device when a
+ *      pass's digit is the same for every key;
+ *   5. keys-only 16-bit sorts at full precision instead rebuild the output from
+ *      the 65,536-bin histogram (Alg. 5 with no trailing bits).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named keys/vals/counts/... are DEVICE pointers (e.g. a torch
+ *     tensor's data_ptr()) unless the name ends in _host.  Key arrays hold
+ *     uint16_t, uint32_t or uint64_t elements for key_bits 16, 32, 64; values
+ *     are uint32_t.  Key and value arrays must be 16-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered: they enqueue work and return; the
+ *     caller owns and keeps alive every buffer until the stream reaches it.
+ *   - The plan owns all scratch memory (allocated by fsort_plan_create, freed
+ *     by fsort_plan_destroy); no call allocates device memory afterwards, and
+ *     the caller owns every buffer it passes.  One plan serves one stream at a
+ *     time: concurrent calls on one plan race on its scratch.
+ *   - Argument errors are returned synchronously and nothing is enqueued.
+ *     Errors found on the device (a bounded wait that timed out) are latched
+ *     in a plan-owned status word and returned by fsort_plan_sync or by the
+ *     first call that finds the previous call's work finished.
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef FSORT_H
+#define FSORT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FSORT_API __attribute__((visibility("default")))
+#else
+#define FSORT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fsort_status {
+  FSORT_OK = 0,
+  FSORT_ERR_INVALID_ARG = 1, /* bad size, width, pointer, alignment or plan */
+  FSORT_ERR_OOM = 2,         /* device or pinned host memory could not be allocated */
+  FSORT_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  FSORT_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up; output is invalid */
+  FSORT_ERR_BUSY = 5,        /* no free slot / memory to admit the request now */
+  FSORT_NOT_READY = 6,       /* the queried work has not finished */
+  FSORT_ERR_INTERNAL = 7,    /* an invariant of the library was violated */
+  FSORT_ERR_UNSUPPORTED = 8  /* valid request this build does not support */
+} fsort_status;
+
+/* fsort_plan_desc.flags */
+#define FSORT_FLAG_HOST_IO 0x4u /* also allocate device buffers of max_n keys (+values) for fsort_sort_pairs_host */
+
+typedef struct fsort_plan fsort_plan;
+
+typedef struct fsort_plan_desc {
+  uint64_t max_n;     /* largest n any call on this plan will pass (>= 1) */
+  int32_t key_bits;   /* 16, 32 or 64 */
+  int32_t has_values; /* 1 if calls may carry uint32_t values, else 0 */
+  int32_t digit_bits; /* radix digit width of the scatter passes: 0 = library default (8), or 8 */
+  uint32_t flags;     /* FSORT_FLAG_* */
+} fsort_plan_desc;
+
+/* What a call with these arguments will do (filled by fsort_plan_describe). */
+typedef struct fsort_plan_info {
+  int32_t passes;          /* scatter passes of the digit plan (before device-side skipping) */
+  int32_t digit_bits;      /* d */
+  int32_t expand_path;     /* 1: keys-only full-precision 16-bit sort rebuilt from the histogram */
+  int32_t tile_keys;       /* keys per scatter tile */
+  uint64_t num_tiles;      /* tiles per scatter pass */
+  uint64_t chunk_keys;     /* keys per look-back chunk (counts inside a chunk fit 30 bits) */
+  uint64_t workspace_bytes;/* device scratch owned by the plan */
+  uint64_t algorithmic_bytes; /* bytes the hot path must move: key read for the histogram plus
+                                 read+write of keys(+values) per pass (expand: read + write of keys) */
+} fsort_plan_info;
+
+/* Create a plan: validates desc, allocates all device scratch for sorts of up
+ * to max_n keys of key_bits bits on the current device.  Returns
+ * FSORT_ERR_INVALID_ARG for a bad desc, FSORT_ERR_OOM if scratch cannot be
+ * allocated; *out_plan is set only on FSORT_OK. */
+FSORT_API fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_plan);
+
+/* Synchronise with the plan's last stream and free everything it owns.
+ * NULL is accepted (no-op). */
+FSORT_API fsort_status fsort_plan_destroy(fsort_plan* plan);
+
+/* Wait for all work enqueued by this plan, then return and clear the latched
+ * device status (FSORT_OK, FSORT_ERR_TIMEOUT or FSORT_ERR_CUDA). */
+FSORT_API fsort_status fsort_plan_sync(fsort_plan* plan);
+
+/* Describe the schedule of a sort of n keys (no work is enqueued). */
+FSORT_API fsort_status fsort_plan_describe(const fsort_plan* plan, uint64_t n, int key_bits, int precision_bits,
+                                 int has_values, fsort_plan_info* out_info);
+
+/* Stable in-place sort of keys[0..n) (and vals, if not NULL) by the top
+ * precision_bits bits of each key (paper Sec. I-II).  1 <= precision_bits <=
+ * key_bits; key_bits must equal the plan's; n <= max_n; vals requires a plan
+ * with has_values.  n == 0 returns FSORT_OK without enqueuing work. */
+FSORT_API fsort_status fsort_sort_pairs(fsort_plan* plan, void* keys, uint32_t* vals, uint64_t n, int key_bits,
+                              int precision_bits, void* stream);
+
+/* Out-of-place form: keys_in/vals_in are read only; the result lands in
+ * keys_out/vals_out.  Input and output ranges must not overlap.  vals_in and
+ * vals_out are both NULL (keys only) or both set. */
+FSORT_API fsort_status fsort_sort_pairs_out(fsort_plan* plan, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                                  uint32_t* vals_out, uint64_t n, int key_bits, int precision_bits, void* stream);
+
+/* Host-buffer form (plan created with FSORT_FLAG_HOST_IO): copies keys_host
+ * (and vals_host) to the plan's device buffers, sorts them and copies the
+ * result back in place, all on `stream`, and returns after the stream has
+ * finished (the call is synchronous).  Pinned host memory makes the copies
+ * asynchronous DMA; pageable memory works but is slower. */
+FSORT_API fsort_status fsort_sort_pairs_host(fsort_plan* plan, void* keys_host, uint32_t* vals_host, uint64_t n,
+                                   int key_bits, int precision_bits, void* stream);
+
+/* ---- the hot-path steps one at a time (same kernels as the full sort) ---- */
+
+/* Step 2: per-pass digit histograms of keys[0..n).  counts_out (device, uint64_t)
+ * receives passes x 2^digit_bits counts, pass-major, where passes =
+ * ceil(precision_bits / digit_bits) and pass j counts bits [key_bits -
+ * precision_bits + j*digit_bits, ...) (the last digit may be narrower; its
+ * unused bins are 0).  digit_bits must be the plan's digit width, or 16 for the
+ * 65,536-bin histogram of 16-bit keys at precision 16 (the expand path). */
+FSORT_API fsort_status fsort_histogram(fsort_plan* plan, const void* keys, uint64_t n, int key_bits, int precision_bits,
+                             int digit_bits, uint64_t* counts_out, void* stream);
+
+/* Step 3: row-wise exclusive scan (Alg. 3's rank of every leaf):
+ * offsets_out[r*bins + v] = sum_{u<v} counts[r*bins + u] for r < rows.
+ * bins must be 2^digit_bits of the plan or 65536; device pointers, uint64_t. */
+FSORT_API fsort_status fsort_exclusive_scan(fsort_plan* plan, const uint64_t* counts, uint64_t rows, uint64_t bins,
+                                  uint64_t* offsets_out, void* stream);
+
+/* Step 4: one stable scatter pass on raw key bits [shift, shift + width),
+ * 1 <= width <= the plan's digit width, out of place.  vals_in/vals_out both
+ * NULL or both set. */
+FSORT_API fsort_status fsort_scatter_pass(fsort_plan* plan, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                                uint32_t* vals_out, uint64_t n, int key_bits, int shift, int width, void* stream);
+
+/* Step 5: write key v counts[v] times for v = 0..65535 in ascending order
+ * (Alg. 5 with no trailing bits); n must equal the sum of counts (device,
+ * uint64_t, 65,536 entries).  16-bit keys only. */
+FSORT_API fsort_status fsort_expand(fsort_plan* plan, const uint64_t* counts, void* keys_out, uint64_t n, int key_bits,
+                          void* stream);
+
+/* Human-readable name of a status code (static storage). */
+FSORT_API const char* fsort_status_string(fsort_status status);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+FSORT_API int fsort_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSORT_H */

@@ -1,0 +1,34 @@
+"""libfsort: GB300-native compressed radix sort (arXiv 2605.10390 hot path).
+
+Python binding over the C ABI declared in ``include/fsort.h``.  Every function
+here only marshals arguments (tensors -> device pointers, the current torch
+stream -> cudaStream_t) and raises :class:`FsortError` on a non-OK status; the
+sort itself runs in the CUDA kernels of ``libfsort.so``.  There is no CPU or
+PyTorch fallback: if the library is missing, every call raises.
+
+Low-level names mirror the C ABI (``fsort_plan_create``, ``fsort_sort_pairs``,
+...).  :class:`Plan` is a small convenience wrapper for torch tensors.
+"""
+from ._binding import (  # noqa: F401
+    FSORT_FLAG_HOST_IO,
+    FsortError,
+    FsortPlanDesc,
+    FsortPlanInfo,
+    Plan,
+    STATUS,
+    fsort_exclusive_scan,
+    fsort_expand,
+    fsort_histogram,
+    fsort_plan_create,
+    fsort_plan_describe,
+    fsort_plan_destroy,
+    fsort_plan_sync,
+    fsort_scatter_pass,
+    fsort_sort_pairs,
+    fsort_sort_pairs_host,
+    fsort_sort_pairs_out,
+    fsort_status_string,
+    fsort_version,
+    lib_path,
+    load_library,
+)

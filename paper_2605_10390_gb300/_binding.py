@@ -1,0 +1,256 @@
+"""ctypes binding of libfsort (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_PKG, "libfsort.so")
+_lock = threading.Lock()
+_lib = None
+
+FSORT_FLAG_HOST_IO = 0x4
+
+STATUS = {
+    0: "FSORT_OK", 1: "FSORT_ERR_INVALID_ARG", 2: "FSORT_ERR_OOM", 3: "FSORT_ERR_CUDA", 4: "FSORT_ERR_TIMEOUT",
+    5: "FSORT_ERR_BUSY", 6: "FSORT_NOT_READY", 7: "FSORT_ERR_INTERNAL", 8: "FSORT_ERR_UNSUPPORTED",
+}
+
+
+class FsortError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class FsortPlanDesc(ctypes.Structure):
+    _fields_ = [("max_n", ctypes.c_uint64), ("key_bits", ctypes.c_int32), ("has_values", ctypes.c_int32),
+                ("digit_bits", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class FsortPlanInfo(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int32), ("digit_bits", ctypes.c_int32), ("expand_path", ctypes.c_int32),
+                ("tile_keys", ctypes.c_int32), ("num_tiles", ctypes.c_uint64), ("chunk_keys", ctypes.c_uint64),
+                ("workspace_bytes", ctypes.c_uint64), ("algorithmic_bytes", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def lib_path() -> str:
+    return _LIB
+
+
+def load_library():
+    """Load libfsort.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB):
+            raise RuntimeError(f"libfsort.so is not built ({_LIB}); run __graft_entry__.build() first")
+        lib = ctypes.CDLL(_LIB)
+        vp, u64, i32, st = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int
+        sig = {
+            "fsort_plan_create": ([ctypes.POINTER(FsortPlanDesc), ctypes.POINTER(vp)], st),
+            "fsort_plan_destroy": ([vp], st),
+            "fsort_plan_sync": ([vp], st),
+            "fsort_plan_describe": ([vp, u64, i32, i32, i32, ctypes.POINTER(FsortPlanInfo)], st),
+            "fsort_sort_pairs": ([vp, vp, vp, u64, i32, i32, vp], st),
+            "fsort_sort_pairs_out": ([vp, vp, vp, vp, vp, u64, i32, i32, vp], st),
+            "fsort_sort_pairs_host": ([vp, vp, vp, u64, i32, i32, vp], st),
+            "fsort_histogram": ([vp, vp, u64, i32, i32, i32, vp, vp], st),
+            "fsort_exclusive_scan": ([vp, vp, u64, u64, vp, vp], st),
+            "fsort_scatter_pass": ([vp, vp, vp, vp, vp, u64, i32, i32, i32, vp], st),
+            "fsort_expand": ([vp, vp, vp, u64, i32, vp], st),
+            "fsort_status_string": ([i32], ctypes.c_char_p),
+            "fsort_version": ([], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+# ---- marshalling helpers ------------------------------------------------------
+
+def _ptr(x) -> int | None:
+    """Device (or host) address of a torch tensor, numpy array or int; None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x).__name__}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int, where: str) -> None:
+    if status != 0:
+        raise FsortError(status, where)
+
+
+_BITS = {"torch.uint16": 16, "torch.uint32": 32, "torch.uint64": 64, "torch.int16": 16, "torch.int32": 32,
+         "torch.int64": 64, "uint16": 16, "uint32": 32, "uint64": 64}
+
+
+def _key_bits_of(t, key_bits):
+    if key_bits is not None:
+        return key_bits
+    kb = _BITS.get(str(getattr(t, "dtype", "")))
+    if kb is None:
+        raise TypeError("key_bits not given and not inferable from the key array's dtype")
+    return kb
+
+
+def _numel(t, n):
+    if n is not None:
+        return n
+    if hasattr(t, "numel"):
+        return int(t.numel())
+    if hasattr(t, "size"):
+        return int(t.size)
+    raise TypeError("n not given and not inferable")
+
+
+# ---- C ABI, same names -----------------------------------------------------------
+
+def fsort_plan_create(max_n: int, key_bits: int, has_values: bool = True, digit_bits: int = 0, flags: int = 0):
+    lib = load_library()
+    desc = FsortPlanDesc(max_n=max_n, key_bits=key_bits, has_values=int(bool(has_values)), digit_bits=digit_bits,
+                         flags=flags)
+    h = ctypes.c_void_p()
+    _check(lib.fsort_plan_create(ctypes.byref(desc), ctypes.byref(h)), "fsort_plan_create")
+    return h.value
+
+
+def fsort_plan_destroy(plan) -> None:
+    _check(load_library().fsort_plan_destroy(plan), "fsort_plan_destroy")
+
+
+def fsort_plan_sync(plan) -> None:
+    _check(load_library().fsort_plan_sync(plan), "fsort_plan_sync")
+
+
+def fsort_plan_describe(plan, n: int, key_bits: int, precision_bits: int, has_values: bool) -> dict:
+    info = FsortPlanInfo()
+    _check(load_library().fsort_plan_describe(plan, n, key_bits, precision_bits, int(bool(has_values)),
+                                              ctypes.byref(info)), "fsort_plan_describe")
+    return info.as_dict()
+
+
+def fsort_sort_pairs(plan, keys, vals=None, n=None, key_bits=None, precision_bits=None, stream=None) -> None:
+    kb = _key_bits_of(keys, key_bits)
+    _check(load_library().fsort_sort_pairs(plan, _ptr(keys), _ptr(vals), _numel(keys, n), kb,
+                                           kb if precision_bits is None else precision_bits, _stream(stream)),
+           "fsort_sort_pairs")
+
+
+def fsort_sort_pairs_out(plan, keys_in, vals_in, keys_out, vals_out, n=None, key_bits=None, precision_bits=None,
+                         stream=None) -> None:
+    kb = _key_bits_of(keys_in, key_bits)
+    _check(load_library().fsort_sort_pairs_out(plan, _ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
+                                               _numel(keys_in, n), kb, kb if precision_bits is None else precision_bits,
+                                               _stream(stream)), "fsort_sort_pairs_out")
+
+
+def fsort_sort_pairs_host(plan, keys_host, vals_host=None, n=None, key_bits=None, precision_bits=None,
+                          stream=None) -> None:
+    kb = _key_bits_of(keys_host, key_bits)
+    _check(load_library().fsort_sort_pairs_host(plan, _ptr(keys_host), _ptr(vals_host), _numel(keys_host, n), kb,
+                                                kb if precision_bits is None else precision_bits, _stream(stream)),
+           "fsort_sort_pairs_host")
+
+
+def fsort_histogram(plan, keys, counts_out, n=None, key_bits=None, precision_bits=None, digit_bits=8,
+                    stream=None) -> None:
+    kb = _key_bits_of(keys, key_bits)
+    _check(load_library().fsort_histogram(plan, _ptr(keys), _numel(keys, n), kb,
+                                          kb if precision_bits is None else precision_bits, digit_bits,
+                                          _ptr(counts_out), _stream(stream)), "fsort_histogram")
+
+
+def fsort_exclusive_scan(plan, counts, rows: int, bins: int, offsets_out, stream=None) -> None:
+    _check(load_library().fsort_exclusive_scan(plan, _ptr(counts), rows, bins, _ptr(offsets_out), _stream(stream)),
+           "fsort_exclusive_scan")
+
+
+def fsort_scatter_pass(plan, keys_in, vals_in, keys_out, vals_out, shift: int, width: int, n=None, key_bits=None,
+                       stream=None) -> None:
+    kb = _key_bits_of(keys_in, key_bits)
+    _check(load_library().fsort_scatter_pass(plan, _ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
+                                             _numel(keys_in, n), kb, shift, width, _stream(stream)),
+           "fsort_scatter_pass")
+
+
+def fsort_expand(plan, counts, keys_out, n=None, key_bits=16, stream=None) -> None:
+    _check(load_library().fsort_expand(plan, _ptr(counts), _ptr(keys_out), _numel(keys_out, n), key_bits,
+                                       _stream(stream)), "fsort_expand")
+
+
+def fsort_status_string(status: int) -> str:
+    return load_library().fsort_status_string(status).decode()
+
+
+def fsort_version() -> int:
+    return int(load_library().fsort_version())
+
+
+class Plan:
+    """Owns a libfsort plan; sorts torch tensors on the current CUDA stream."""
+
+    def __init__(self, max_n: int, key_bits: int, has_values: bool = True, digit_bits: int = 0, flags: int = 0):
+        self.key_bits = key_bits
+        self.has_values = has_values
+        self.handle = fsort_plan_create(max_n, key_bits, has_values, digit_bits, flags)
+
+    def close(self) -> None:
+        if self.handle:
+            fsort_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sort(self, keys, vals=None, precision_bits=None, stream=None) -> None:
+        fsort_sort_pairs(self.handle, keys, vals, None, self.key_bits, precision_bits, stream)
+
+    def sort_out(self, keys_in, vals_in, keys_out, vals_out, precision_bits=None, stream=None) -> None:
+        fsort_sort_pairs_out(self.handle, keys_in, vals_in, keys_out, vals_out, None, self.key_bits, precision_bits,
+                             stream)
+
+    def sync(self) -> None:
+        fsort_plan_sync(self.handle)
+
+    def describe(self, n: int, precision_bits=None, has_values=None) -> dict:
+        return fsort_plan_describe(self.handle, n, self.key_bits,
+                                   self.key_bits if precision_bits is None else precision_bits,
+                                   self.has_values if has_values is None else has_values)

@@ -1,0 +1,500 @@
+// fsort_api.cu -- the C ABI of libfsort (include/fsort.h): argument checks,
+// plan-owned scratch, the digit plan, kernel sequencing and status latching.
+// Every step of a sort runs in this library's CUDA kernels; the host only
+// validates, enqueues and reports.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "../../include/fsort.h"
+#include "fsort_dev.cuh"
+#include "fsort_internal.h"
+
+using namespace fsort;
+
+struct fsort_plan {
+  int device = 0;
+  int sms = 0;
+  fsort_plan_desc desc{};
+  int digit_bits = 8;
+  int tile = 0;
+  uint64_t chunk_keys = 0;
+  uint64_t max_tiles = 0;
+  uint64_t max_chunks = 0;
+
+  unsigned char* ws = nullptr;  // one allocation holds all device scratch
+  size_t ws_bytes = 0;
+  void* alt_keys = nullptr;
+  uint32_t* alt_vals = nullptr;
+  uint32_t* counters = nullptr;  // [2] tile counters, directly followed by look-back region 0
+  uint32_t* lookback[2] = {nullptr, nullptr};
+  uint64_t* hist = nullptr;      // [kMaxPasses][max_chunks][256], all zero between calls
+  uint64_t* bases = nullptr;     // same shape
+  Schedule* sched = nullptr;
+  uint32_t* status = nullptr;    // sticky device error bits
+  uint32_t* leaf_part = nullptr; // expand path (16-bit keys)
+  uint64_t* leaf_spill = nullptr;
+  uint64_t* leaf_counts = nullptr;
+  uint64_t* leaf_off = nullptr;
+  void* io_keys = nullptr;       // FSORT_FLAG_HOST_IO
+  uint32_t* io_vals = nullptr;
+
+  uint32_t* h_status = nullptr;  // pinned copy of *status
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+};
+
+namespace {
+
+constexpr int kRadix = 256;
+constexpr size_t kCounterBytes = 256;  // two counters, padded
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool valid_key_bits(int kb) { return kb == 16 || kb == 32 || kb == 64; }
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+fsort_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return FSORT_OK;
+  if (e == cudaErrorMemoryAllocation) return FSORT_ERR_OOM;
+  return FSORT_ERR_CUDA;
+}
+
+DigitPlan make_plan(int key_bits, int precision_bits, int d) {
+  DigitPlan p{};
+  p.passes = (precision_bits + d - 1) / d;
+  const int base = key_bits - precision_bits;
+  for (int j = 0; j < p.passes; ++j) {
+    const int lo = j * d;
+    const int width = (precision_bits - lo < d) ? (precision_bits - lo) : d;
+    p.shift[j] = uint32_t(base + lo);
+    p.mask[j] = (1u << width) - 1u;
+  }
+  return p;
+}
+
+bool use_expand(int key_bits, int precision_bits, bool has_vals) {
+  return key_bits == 16 && precision_bits == 16 && !has_vals;
+}
+
+// Report (and clear) a device error latched by earlier work of this plan.
+// wait: block until that work is done; otherwise look only if it already is.
+fsort_status take_latched(fsort_plan* p, bool wait, cudaStream_t stream) {
+  if (!p->pending) return FSORT_OK;
+  if (wait) {
+    if (cudaEventSynchronize(p->done) != cudaSuccess) return FSORT_ERR_CUDA;
+  } else {
+    const cudaError_t q = cudaEventQuery(p->done);
+    if (q == cudaErrorNotReady) return FSORT_OK;
+    if (q != cudaSuccess) return FSORT_ERR_CUDA;
+  }
+  p->pending = false;
+  const uint32_t s = *p->h_status;
+  if (!s) return FSORT_OK;
+  *p->h_status = 0;
+  if (cudaMemsetAsync(p->status, 0, sizeof(uint32_t), stream) != cudaSuccess) return FSORT_ERR_CUDA;
+  if (wait && cudaStreamSynchronize(stream) != cudaSuccess) return FSORT_ERR_CUDA;
+  return (s & (kDevTimeoutLookback | kDevTimeoutLoad)) ? FSORT_ERR_TIMEOUT : FSORT_ERR_INTERNAL;
+}
+
+// After enqueuing work: copy the sticky device status back and mark the call.
+fsort_status finish_call(fsort_plan* p, cudaStream_t stream) {
+  cudaError_t e = cudaMemcpyAsync(p->h_status, p->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaEventRecord(p->done, stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  p->pending = true;
+  return FSORT_OK;
+}
+
+fsort_status check_call(const fsort_plan* p, uint64_t n, int key_bits, int precision_bits, bool has_vals) {
+  if (!p) return FSORT_ERR_INVALID_ARG;
+  if (key_bits != p->desc.key_bits) return FSORT_ERR_INVALID_ARG;
+  if (precision_bits < 1 || precision_bits > key_bits) return FSORT_ERR_INVALID_ARG;
+  if (n > p->desc.max_n) return FSORT_ERR_INVALID_ARG;
+  if (has_vals && !p->desc.has_values) return FSORT_ERR_INVALID_ARG;
+  return FSORT_OK;
+}
+
+bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + bn && y < x + an;
+}
+
+// The whole sort, keys_in -> keys_out (equal pointers: in place).
+fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                          uint32_t* vals_out, uint64_t n, int key_bits, int precision_bits, cudaStream_t s) {
+  const bool has_vals = vals_in != nullptr;
+  const bool in_place = keys_in == keys_out;
+  cudaError_t e = cudaSuccess;
+  if (use_expand(key_bits, precision_bits, has_vals)) {
+    // Expand path: the 65,536-bin histogram is the whole sorted multiset.
+    e = launch_leaf_histogram(static_cast<const uint16_t*>(keys_in), n, p->leaf_part, p->leaf_spill, p->sms, s);
+    if (e == cudaSuccess) e = launch_leaf_reduce(p->leaf_part, p->leaf_spill, leaf_hist_grid(p->sms), p->leaf_counts, s);
+    if (e == cudaSuccess) e = launch_scan_rows(p->leaf_counts, p->leaf_off, 1, 65536, s);
+    if (e == cudaSuccess) e = launch_expand(p->leaf_off, static_cast<uint16_t*>(keys_out), n, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return finish_call(p, s);
+  }
+  const DigitPlan plan = make_plan(key_bits, precision_bits, p->digit_bits);
+  const uint64_t tiles = (n + p->tile - 1) / p->tile;
+  const uint64_t chunks = (n + p->chunk_keys - 1) / p->chunk_keys;
+  const uint64_t clear_words = kCounterBytes / 4 + tiles * kRadix;
+  e = launch_histogram(keys_in, key_bits, n, p->chunk_keys, plan, p->hist, chunks * kRadix, kRadix, p->counters,
+                       clear_words, p->sms, s);
+  if (e == cudaSuccess)
+    e = launch_scan_schedule(p->hist, p->bases, plan.passes, uint32_t(chunks), in_place ? 1 : 0, p->sched, s);
+  const void* kb[3] = {keys_in, p->alt_keys, keys_out};
+  const uint32_t* vb[3] = {vals_in, p->alt_vals, vals_out};
+  for (int j = 0; j < plan.passes && e == cudaSuccess; ++j) {
+    OnesweepArgs a{};
+    for (int b = 0; b < 3; ++b) {
+      a.keys[b] = kb[b];
+      a.vals[b] = has_vals ? vb[b] : nullptr;
+    }
+    a.n = n;
+    a.shift = plan.shift[j];
+    a.mask = plan.mask[j];
+    a.lookback = p->lookback[j & 1];
+    a.tile_counter = p->counters + (j & 1);
+    const bool last = (j + 1 == plan.passes);
+    a.next_lookback = last ? nullptr : p->lookback[(j + 1) & 1];
+    a.next_counter = last ? nullptr : p->counters + ((j + 1) & 1);
+    a.bases = p->bases + uint64_t(j) * chunks * kRadix;
+    a.sched = p->sched;
+    a.pass = j;
+    a.tiles_per_chunk = uint32_t(p->chunk_keys / p->tile);
+    a.status = p->status;
+    e = launch_onesweep(a, key_bits, has_vals, s);
+  }
+  if (e == cudaSuccess) e = launch_schedule_copy(kb, vb, key_bits, has_vals, n, p->sched, p->sms, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  return finish_call(p, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_plan) {
+  if (!desc || !out_plan) return FSORT_ERR_INVALID_ARG;
+  if (!valid_key_bits(desc->key_bits) || desc->max_n < 1) return FSORT_ERR_INVALID_ARG;
+  if (desc->has_values != 0 && desc->has_values != 1) return FSORT_ERR_INVALID_ARG;
+  if (desc->digit_bits != 0 && desc->digit_bits != 8) return FSORT_ERR_UNSUPPORTED;
+  if (desc->flags & ~FSORT_FLAG_HOST_IO) return FSORT_ERR_INVALID_ARG;
+  if (desc->max_n > (1ull << 36)) return FSORT_ERR_UNSUPPORTED;
+
+  fsort_plan* p = new (std::nothrow) fsort_plan();
+  if (!p) return FSORT_ERR_OOM;
+  p->desc = *desc;
+  p->digit_bits = 8;
+  if (cudaGetDevice(&p->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    delete p;
+    return FSORT_ERR_CUDA;
+  }
+  const int kb = desc->key_bits / 8;
+  const uint64_t n = desc->max_n;
+  p->tile = tile_keys_for(desc->key_bits);
+  p->chunk_keys = chunk_keys_for(desc->key_bits);
+  p->max_tiles = (n + p->tile - 1) / p->tile;
+  p->max_chunks = (n + p->chunk_keys - 1) / p->chunk_keys;
+
+  // Carve the scratch out of one allocation.
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  const size_t o_alt_k = take(n * kb);
+  const size_t o_alt_v = desc->has_values ? take(n * 4) : 0;
+  const size_t o_cnt = take(kCounterBytes + p->max_tiles * kRadix * 4);  // counters + region 0
+  const size_t o_lb1 = take(p->max_tiles * kRadix * 4);
+  const size_t hist_bytes = size_t(kMaxPasses) * p->max_chunks * kRadix * 8;
+  const size_t o_hist = take(hist_bytes);
+  const size_t o_bases = take(hist_bytes);
+  const size_t o_sched = take(sizeof(Schedule));
+  const size_t o_status = take(sizeof(uint32_t));
+  size_t o_lpart = 0, o_lspill = 0, o_lcnt = 0, o_loff = 0;
+  const bool leaf = desc->key_bits == 16;
+  if (leaf) {
+    o_lpart = take(size_t(leaf_hist_grid(p->sms)) * 32768 * 4);
+    o_lspill = take(65536 * 8);
+    o_lcnt = take(65536 * 8);
+    o_loff = take(65536 * 8);
+  }
+  size_t o_iok = 0, o_iov = 0;
+  const bool hio = (desc->flags & FSORT_FLAG_HOST_IO) != 0;
+  if (hio) {
+    o_iok = take(n * kb);
+    if (desc->has_values) o_iov = take(n * 4);
+  }
+  p->ws_bytes = off;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->ws), p->ws_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return FSORT_ERR_OOM;
+  }
+  unsigned char* w = p->ws;
+  p->alt_keys = w + o_alt_k;
+  p->alt_vals = desc->has_values ? reinterpret_cast<uint32_t*>(w + o_alt_v) : nullptr;
+  p->counters = reinterpret_cast<uint32_t*>(w + o_cnt);
+  p->lookback[0] = reinterpret_cast<uint32_t*>(w + o_cnt + kCounterBytes);
+  p->lookback[1] = reinterpret_cast<uint32_t*>(w + o_lb1);
+  p->hist = reinterpret_cast<uint64_t*>(w + o_hist);
+  p->bases = reinterpret_cast<uint64_t*>(w + o_bases);
+  p->sched = reinterpret_cast<Schedule*>(w + o_sched);
+  p->status = reinterpret_cast<uint32_t*>(w + o_status);
+  if (leaf) {
+    p->leaf_part = reinterpret_cast<uint32_t*>(w + o_lpart);
+    p->leaf_spill = reinterpret_cast<uint64_t*>(w + o_lspill);
+    p->leaf_counts = reinterpret_cast<uint64_t*>(w + o_lcnt);
+    p->leaf_off = reinterpret_cast<uint64_t*>(w + o_loff);
+  }
+  if (hio) {
+    p->io_keys = w + o_iok;
+    p->io_vals = desc->has_values ? reinterpret_cast<uint32_t*>(w + o_iov) : nullptr;
+  }
+  // Zero what must start at zero: histogram accumulators, status, counters.
+  e = cudaMemset(p->hist, 0, hist_bytes);
+  if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(p->counters, 0, kCounterBytes);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&p->h_status), sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (p->h_status) cudaFreeHost(p->h_status);
+    if (p->done) cudaEventDestroy(p->done);
+    cudaFree(p->ws);
+    delete p;
+    return FSORT_ERR_CUDA;
+  }
+  *p->h_status = 0;
+  *out_plan = p;
+  return FSORT_OK;
+}
+
+fsort_status fsort_plan_destroy(fsort_plan* plan) {
+  if (!plan) return FSORT_OK;
+  fsort_status st = FSORT_OK;
+  if (plan->pending && cudaEventSynchronize(plan->done) != cudaSuccess) st = FSORT_ERR_CUDA;
+  if (plan->done) cudaEventDestroy(plan->done);
+  if (plan->h_status) cudaFreeHost(plan->h_status);
+  if (plan->ws && cudaFree(plan->ws) != cudaSuccess) st = FSORT_ERR_CUDA;
+  delete plan;
+  return st;
+}
+
+fsort_status fsort_plan_sync(fsort_plan* plan) {
+  if (!plan) return FSORT_ERR_INVALID_ARG;
+  return take_latched(plan, true, nullptr);
+}
+
+fsort_status fsort_plan_describe(const fsort_plan* plan, uint64_t n, int key_bits, int precision_bits,
+                                 int has_values, fsort_plan_info* out) {
+  if (!out) return FSORT_ERR_INVALID_ARG;
+  const fsort_status st = check_call(plan, n, key_bits, precision_bits, has_values != 0);
+  if (st != FSORT_OK) return st;
+  std::memset(out, 0, sizeof(*out));
+  const uint64_t kb = uint64_t(key_bits) / 8, vb = has_values ? 4 : 0;
+  out->digit_bits = plan->digit_bits;
+  out->tile_keys = plan->tile;
+  out->chunk_keys = plan->chunk_keys;
+  out->workspace_bytes = plan->ws_bytes;
+  if (use_expand(key_bits, precision_bits, has_values != 0)) {
+    out->expand_path = 1;
+    out->passes = 0;
+    out->num_tiles = 0;
+    out->algorithmic_bytes = 2 * kb * n;
+  } else {
+    out->passes = (precision_bits + plan->digit_bits - 1) / plan->digit_bits;
+    out->num_tiles = (n + plan->tile - 1) / plan->tile;
+    out->algorithmic_bytes = kb * n + uint64_t(out->passes) * 2 * (kb + vb) * n;
+  }
+  return FSORT_OK;
+}
+
+fsort_status fsort_sort_pairs(fsort_plan* plan, void* keys, uint32_t* vals, uint64_t n, int key_bits,
+                              int precision_bits, void* stream) {
+  fsort_status st = check_call(plan, n, key_bits, precision_bits, vals != nullptr);
+  if (st != FSORT_OK) return st;
+  if (n == 0) return FSORT_OK;
+  if (!keys || !aligned16(keys) || (vals && !aligned16(vals))) return FSORT_ERR_INVALID_ARG;
+  if (vals && overlaps(keys, n * (key_bits / 8), vals, n * 4)) return FSORT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = take_latched(plan, false, s);
+  if (st != FSORT_OK) return st;
+  return enqueue_sort(plan, keys, vals, keys, vals, n, key_bits, precision_bits, s);
+}
+
+fsort_status fsort_sort_pairs_out(fsort_plan* plan, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                                  uint32_t* vals_out, uint64_t n, int key_bits, int precision_bits, void* stream) {
+  if ((vals_in == nullptr) != (vals_out == nullptr)) return FSORT_ERR_INVALID_ARG;
+  fsort_status st = check_call(plan, n, key_bits, precision_bits, vals_in != nullptr);
+  if (st != FSORT_OK) return st;
+  if (n == 0) return FSORT_OK;
+  if (!keys_in || !keys_out || !aligned16(keys_in) || !aligned16(keys_out)) return FSORT_ERR_INVALID_ARG;
+  if (vals_in && (!aligned16(vals_in) || !aligned16(vals_out))) return FSORT_ERR_INVALID_ARG;
+  const size_t kbytes = size_t(n) * (key_bits / 8);
+  if (overlaps(keys_in, kbytes, keys_out, kbytes)) return FSORT_ERR_INVALID_ARG;
+  if (vals_in && (overlaps(vals_in, n * 4, vals_out, n * 4) || overlaps(keys_out, kbytes, vals_out, n * 4) ||
+                  overlaps(keys_in, kbytes, vals_out, n * 4) || overlaps(vals_in, n * 4, keys_out, kbytes)))
+    return FSORT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = take_latched(plan, false, s);
+  if (st != FSORT_OK) return st;
+  return enqueue_sort(plan, keys_in, vals_in, keys_out, vals_out, n, key_bits, precision_bits, s);
+}
+
+fsort_status fsort_sort_pairs_host(fsort_plan* plan, void* keys_host, uint32_t* vals_host, uint64_t n, int key_bits,
+                                   int precision_bits, void* stream) {
+  fsort_status st = check_call(plan, n, key_bits, precision_bits, vals_host != nullptr);
+  if (st != FSORT_OK) return st;
+  if (!(plan->desc.flags & FSORT_FLAG_HOST_IO)) return FSORT_ERR_INVALID_ARG;
+  if (n == 0) return FSORT_OK;
+  if (!keys_host) return FSORT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = take_latched(plan, false, s);
+  if (st != FSORT_OK) return st;
+  const size_t kbytes = size_t(n) * (key_bits / 8);
+  cudaError_t e = cudaMemcpyAsync(plan->io_keys, keys_host, kbytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && vals_host) e = cudaMemcpyAsync(plan->io_vals, vals_host, n * 4, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  st = enqueue_sort(plan, plan->io_keys, vals_host ? plan->io_vals : nullptr, plan->io_keys,
+                    vals_host ? plan->io_vals : nullptr, n, key_bits, precision_bits, s);
+  if (st != FSORT_OK) return st;
+  e = cudaMemcpyAsync(keys_host, plan->io_keys, kbytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && vals_host) e = cudaMemcpyAsync(vals_host, plan->io_vals, n * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  return take_latched(plan, true, s);
+}
+
+fsort_status fsort_histogram(fsort_plan* plan, const void* keys, uint64_t n, int key_bits, int precision_bits,
+                             int digit_bits, uint64_t* counts_out, void* stream) {
+  fsort_status st = check_call(plan, n, key_bits, precision_bits, false);
+  if (st != FSORT_OK) return st;
+  if (!counts_out || (n && (!keys || !aligned16(keys)))) return FSORT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = take_latched(plan, false, s);
+  if (st != FSORT_OK) return st;
+  cudaError_t e;
+  if (digit_bits == 16) {
+    if (key_bits != 16 || precision_bits != 16) return FSORT_ERR_INVALID_ARG;
+    e = launch_leaf_histogram(static_cast<const uint16_t*>(keys), n, plan->leaf_part, plan->leaf_spill, plan->sms, s);
+    if (e == cudaSuccess)
+      e = launch_leaf_reduce(plan->leaf_part, plan->leaf_spill, leaf_hist_grid(plan->sms), counts_out, s);
+  } else {
+    if (digit_bits != plan->digit_bits) return FSORT_ERR_INVALID_ARG;
+    const DigitPlan dp = make_plan(key_bits, precision_bits, digit_bits);
+    e = cudaMemsetAsync(counts_out, 0, sizeof(uint64_t) * dp.passes * (1u << digit_bits), s);
+    if (e == cudaSuccess && n)
+      e = launch_histogram(keys, key_bits, n, plan->chunk_keys, dp, counts_out, uint64_t(1) << digit_bits, 0,
+                           nullptr, 0, plan->sms, s);
+  }
+  if (e != cudaSuccess) return from_cuda(e);
+  return finish_call(plan, s);
+}
+
+fsort_status fsort_exclusive_scan(fsort_plan* plan, const uint64_t* counts, uint64_t rows, uint64_t bins,
+                                  uint64_t* offsets_out, void* stream) {
+  if (!plan || !counts || !offsets_out) return FSORT_ERR_INVALID_ARG;
+  if (bins != (1ull << plan->digit_bits) && bins != 65536) return FSORT_ERR_INVALID_ARG;
+  if (rows < 1 || rows > 65535) return FSORT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  fsort_status st = take_latched(plan, false, s);
+  if (st != FSORT_OK) return st;
+  const cudaError_t e = launch_scan_rows(counts, offsets_out, rows, bins, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  return finish_call(plan, s);
+}
+
+fsort_status fsort_scatter_pass(fsort_plan* plan, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                                uint32_t* vals_out, uint64_t n, int key_bits, int shift, int width, void* stream) {
+  if ((vals_in == nullptr) != (vals_out == nullptr)) return FSORT_ERR_INVALID_ARG;
+  fsort_status st = check_call(plan, n, key_bits, key_bits, vals_in != nullptr);
+  if (st != FSORT_OK) return st;
+  if (width < 1 || width > plan->digit_bits || shift < 0 || shift + width > key_bits) return FSORT_ERR_INVALID_ARG;
+  if (n == 0) return FSORT_OK;
+  if (!keys_in || !keys_out || !aligned16(keys_in) || !aligned16(keys_out)) return FSORT_ERR_INVALID_ARG;
+  if (vals_in && (!aligned16(vals_in) || !aligned16(vals_out))) return FSORT_ERR_INVALID_ARG;
+  const size_t kbytes = size_t(n) * (key_bits / 8);
+  if (overlaps(keys_in, kbytes, keys_out, kbytes)) return FSORT_ERR_INVALID_ARG;
+  if (vals_in && overlaps(vals_in, n * 4, vals_out, n * 4)) return FSORT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = take_latched(plan, false, s);
+  if (st != FSORT_OK) return st;
+  DigitPlan dp{};
+  dp.passes = 1;
+  dp.shift[0] = uint32_t(shift);
+  dp.mask[0] = (1u << width) - 1u;
+  const uint64_t tiles = (n + plan->tile - 1) / plan->tile;
+  const uint64_t chunks = (n + plan->chunk_keys - 1) / plan->chunk_keys;
+  cudaError_t e = launch_histogram(keys_in, key_bits, n, plan->chunk_keys, dp, plan->hist, chunks * kRadix, kRadix,
+                                   plan->counters, kCounterBytes / 4 + tiles * kRadix, plan->sms, s);
+  if (e == cudaSuccess) e = launch_scan_schedule(plan->hist, plan->bases, 1, uint32_t(chunks), 0, nullptr, s);
+  if (e == cudaSuccess) {
+    OnesweepArgs a{};
+    a.keys[0] = keys_in;
+    a.keys[1] = nullptr;
+    a.keys[2] = keys_out;
+    a.vals[0] = vals_in;
+    a.vals[1] = nullptr;
+    a.vals[2] = vals_out;
+    a.n = n;
+    a.shift = dp.shift[0];
+    a.mask = dp.mask[0];
+    a.lookback = plan->lookback[0];
+    a.tile_counter = plan->counters;
+    a.next_lookback = nullptr;
+    a.next_counter = nullptr;
+    a.bases = plan->bases;
+    a.sched = nullptr;
+    a.pass = 0;
+    a.tiles_per_chunk = uint32_t(plan->chunk_keys / plan->tile);
+    a.status = plan->status;
+    e = launch_onesweep(a, key_bits, vals_in != nullptr, s);
+  }
+  if (e != cudaSuccess) return from_cuda(e);
+  return finish_call(plan, s);
+}
+
+fsort_status fsort_expand(fsort_plan* plan, const uint64_t* counts, void* keys_out, uint64_t n, int key_bits,
+                          void* stream) {
+  fsort_status st = check_call(plan, n, key_bits, key_bits, false);
+  if (st != FSORT_OK) return st;
+  if (key_bits != 16 || !counts) return FSORT_ERR_INVALID_ARG;
+  if (n == 0) return FSORT_OK;
+  if (!keys_out || !aligned16(keys_out)) return FSORT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = take_latched(plan, false, s);
+  if (st != FSORT_OK) return st;
+  cudaError_t e = launch_scan_rows(counts, plan->leaf_off, 1, 65536, s);
+  if (e == cudaSuccess) e = launch_expand(plan->leaf_off, static_cast<uint16_t*>(keys_out), n, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  return finish_call(plan, s);
+}
+
+const char* fsort_status_string(fsort_status status) {
+  switch (status) {
+    case FSORT_OK: return "FSORT_OK";
+    case FSORT_ERR_INVALID_ARG: return "FSORT_ERR_INVALID_ARG";
+    case FSORT_ERR_OOM: return "FSORT_ERR_OOM";
+    case FSORT_ERR_CUDA: return "FSORT_ERR_CUDA";
+    case FSORT_ERR_TIMEOUT: return "FSORT_ERR_TIMEOUT";
+    case FSORT_ERR_BUSY: return "FSORT_ERR_BUSY";
+    case FSORT_NOT_READY: return "FSORT_NOT_READY";
+    case FSORT_ERR_INTERNAL: return "FSORT_ERR_INTERNAL";
+    case FSORT_ERR_UNSUPPORTED: return "FSORT_ERR_UNSUPPORTED";
+    default: return "FSORT_UNKNOWN_STATUS";
+  }
+}
+
+int fsort_version(void) { return 100; }
+
+}  // extern "C"

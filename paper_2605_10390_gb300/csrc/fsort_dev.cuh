@@ -1,0 +1,135 @@
+// fsort_dev.cuh -- device-side building blocks shared by libfsort's kernels:
+// inline-PTX wrappers (bulk async copies, mbarriers, relaxed GPU-scope
+// loads/stores, the global timer) and the descriptors the kernels exchange.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fsort {
+
+// ---- device status word bits (latched, read by the host) -------------------
+constexpr uint32_t kDevTimeoutLookback = 1u;  // a look-back wait gave up
+constexpr uint32_t kDevTimeoutLoad = 2u;      // a bulk-copy wait gave up
+constexpr uint32_t kDevBadPlan = 4u;          // a kernel saw an impossible descriptor
+
+// Bounded waits give up after this many nanoseconds of %globaltimer.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// ---- look-back status words -------------------------------------------------
+// One 32-bit word per (tile, digit): 2-bit flag | 30-bit count.  Counts inside
+// one look-back chunk never reach 2^30 (chunks hold fewer keys than that), so
+// the word never overflows; the chunk's base is added as a 64-bit number.
+constexpr uint32_t kFlagShift = 30;
+constexpr uint32_t kFlagAggregate = 1u << kFlagShift;  // tile's own count only
+constexpr uint32_t kFlagPrefix = 2u << kFlagShift;     // inclusive prefix through this tile
+constexpr uint32_t kCountMask = (1u << kFlagShift) - 1;
+constexpr uint64_t kMaxChunkKeys = (1ull << 30) - 1;
+
+// Which buffer a pass reads or writes.
+enum BufSel : int32_t { kBufIn = 0, kBufAlt = 1, kBufOut = 2 };
+
+// Per-pass schedule written by the scan kernel on the device, so that trivial
+// passes (every key has the same digit) are skipped without a host round trip.
+struct PassDesc {
+  int32_t active;   // 1: run the scatter; 0: skip
+  int32_t src;      // BufSel
+  int32_t dst;      // BufSel
+  int32_t pad;
+};
+
+constexpr int kMaxPasses = 16;
+
+struct Schedule {
+  PassDesc pass[kMaxPasses];
+  PassDesc copy;       // final copy when the result would end in the wrong buffer
+  int32_t active_passes;
+  int32_t pad[3];
+};
+
+// ---- PTX wrappers ------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_gpu(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier to complete; gives up after
+// kWaitLimitNs and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return true;
+}
+
+// Bulk (non-tensor) async copy global -> this CTA's shared memory, completing
+// `bytes` of transaction count on `bar`.  dst, src and bytes must be multiples
+// of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Digit of a key: bits [shift, shift + width) (width <= 16).
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K k, uint32_t shift, uint32_t mask) {
+  return static_cast<uint32_t>(static_cast<uint64_t>(k) >> shift) & mask;
+}
+
+}  // namespace fsort

@@ -1,0 +1,481 @@
+// fsort_hist.cu -- histogram, scan and expand kernels of libfsort.
+//
+//  K1  hist_kernel        every pass's digit histogram from one read of the keys
+//                          (Sec. III-A/B: one counter update per key per digit)
+//  K1' leaf_hist_kernel   the 65,536-bin histogram of 16-bit keys with 16-bit
+//                          tapered counters and exact overflow spills (Sec. III-D-1)
+//  K2  scan_schedule      exclusive scan per pass (Alg. 3's rank of every leaf),
+//                          chunk bases, and the device-side pass schedule
+//  K4  expand_kernel      Alg. 5 without trailing bits: key v written C[v] times
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fsort_dev.cuh"
+#include "fsort_internal.h"
+
+namespace fsort {
+namespace {
+
+constexpr int kRadix = 256;
+
+// ---------------------------------------------------------------- K1 -------
+// Every CTA owns a slice of one look-back chunk and keeps one shared-memory
+// counter per (pass, digit).  Counts are added with shared-memory reductions
+// (red.shared.add: same-address adds from a warp are combined by the
+// hardware, so skewed inputs cost no more than uniform ones), then merged into
+// the global 64-bit histogram with one atomic per non-zero counter.
+constexpr int kHistThreads = 512;
+
+template <typename K>
+__global__ void __launch_bounds__(kHistThreads) hist_kernel(const K* __restrict__ keys, uint64_t n,
+                                                            uint64_t chunk_keys, DigitPlan plan,
+                                                            uint64_t* __restrict__ hist, uint64_t pass_stride,
+                                                            uint64_t chunk_stride, uint32_t* clear,
+                                                            uint64_t clear_words) {
+  __shared__ uint32_t counts[kMaxPasses * kRadix];
+  const int passes = plan.passes;
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) counts[i] = 0;
+
+  // Clear the first pass's look-back region and the tile counters.
+  {
+    const uint64_t stride = uint64_t(gridDim.x) * gridDim.y * blockDim.x;
+    const uint64_t first = (uint64_t(blockIdx.y) * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+    for (uint64_t i = first; i < clear_words; i += stride) clear[i] = 0;
+  }
+  __syncthreads();
+
+  const uint64_t chunk = blockIdx.y;
+  const uint64_t c_lo = chunk * chunk_keys;
+  const uint64_t c_hi = (c_lo + chunk_keys < n) ? c_lo + chunk_keys : n;
+  // Slice of the chunk for this CTA, in whole 16-byte vectors.
+  constexpr uint64_t kVec = 16 / sizeof(K);
+  const uint64_t c_vecs = (c_hi - c_lo + kVec - 1) / kVec;
+  const uint64_t per = (c_vecs + gridDim.x - 1) / gridDim.x;
+  const uint64_t v_lo = blockIdx.x * per;
+  const uint64_t v_hi = (v_lo + per < c_vecs) ? v_lo + per : c_vecs;
+
+  uint32_t shift[kMaxPasses], mask[kMaxPasses];
+#pragma unroll
+  for (int j = 0; j < kMaxPasses; ++j) {
+    shift[j] = plan.shift[j];
+    mask[j] = plan.mask[j];
+  }
+
+  auto count_key = [&](K k) {
+#pragma unroll
+    for (int j = 0; j < kMaxPasses; ++j) {
+      if (j < passes) {
+        const uint32_t d = uint32_t(uint64_t(k) >> shift[j]) & mask[j];
+        atomicAdd(&counts[j * kRadix + d], 1u);
+      }
+    }
+  };
+
+  for (uint64_t v = v_lo + threadIdx.x; v < v_hi; v += blockDim.x) {
+    const uint64_t e0 = c_lo + v * kVec;
+    if (e0 + kVec <= c_hi) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(keys + e0));
+      const K* kk = reinterpret_cast<const K*>(&q);
+#pragma unroll
+      for (int e = 0; e < int(kVec); ++e) count_key(kk[e]);
+    } else {
+      for (uint64_t e = e0; e < c_hi; ++e) count_key(keys[e]);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    const uint32_t c = counts[i];
+    if (c) {
+      const int j = i / kRadix, d = i % kRadix;
+      atomicAdd(reinterpret_cast<unsigned long long*>(&hist[j * pass_stride + chunk * chunk_stride + d]),
+                (unsigned long long)c);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K2 -------
+// 256 threads, thread d owns digit d.  For each pass: the digit's total over
+// all chunks, a block-wide exclusive scan over digits (the rank of every leaf,
+// Alg. 3), then running sums over chunks give each (chunk, digit) its 64-bit
+// base.  A pass whose keys all share one digit is trivial (its stable scatter
+// is the identity) and is marked inactive.  Thread 0 then routes the active
+// passes through the input, scratch and output buffers so that the last one
+// writes the output, adding a final copy only when no assignment can.
+__device__ uint64_t block_exclusive_scan_256(uint64_t x, uint64_t* s_warp, uint64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  uint64_t before = 0, all = 0;
+  for (int w = 0; w < 8; ++w) {
+    if (w < warp) before += s_warp[w];
+    all += s_warp[w];
+  }
+  __syncthreads();
+  *total = all;
+  return before + inc - x;
+}
+
+__global__ void __launch_bounds__(kRadix) scan_schedule_kernel(uint64_t* __restrict__ hist,
+                                                               uint64_t* __restrict__ bases, int passes,
+                                                               uint32_t chunks, int in_place, Schedule* sched) {
+  __shared__ uint64_t s_warp[8];
+  __shared__ int s_trivial[kMaxPasses];
+  const int d = threadIdx.x;
+  for (int j = 0; j < passes; ++j) {
+    uint64_t* h = hist + uint64_t(j) * chunks * kRadix;
+    uint64_t tot = 0;
+    for (uint32_t c = 0; c < chunks; ++c) tot += h[uint64_t(c) * kRadix + d];
+    uint64_t all;
+    const uint64_t excl = block_exclusive_scan_256(tot, s_warp, &all);
+    const int nonzero = __syncthreads_count(tot != 0);
+    if (d == 0) s_trivial[j] = (nonzero <= 1);
+    uint64_t run = excl;
+    uint64_t* b = bases + uint64_t(j) * chunks * kRadix;
+    for (uint32_t c = 0; c < chunks; ++c) {
+      b[uint64_t(c) * kRadix + d] = run;
+      run += h[uint64_t(c) * kRadix + d];
+      h[uint64_t(c) * kRadix + d] = 0;  // leave the accumulator zero for the next call
+    }
+  }
+  __syncthreads();
+  if (d == 0 && sched) {
+    int k = 0;
+    for (int j = 0; j < passes; ++j) k += s_trivial[j] ? 0 : 1;
+    // Buffer sequence b_0 = input, ..., b_k = the buffer holding the result.
+    // In place (input == output): alternate scratch/input; odd k ends in the
+    // scratch buffer and needs the copy back.  Out of place: count backwards
+    // from the output so the last active pass writes it; k == 0 copies.
+    int cur = kBufIn, idx = 0;
+    for (int j = 0; j < kMaxPasses; ++j) {
+      PassDesc pd{0, kBufIn, kBufIn, 0};
+      if (j < passes && !s_trivial[j]) {
+        ++idx;
+        int nxt;
+        if (in_place) nxt = (idx & 1) ? kBufAlt : kBufIn;
+        else nxt = ((k - idx) & 1) ? kBufAlt : kBufOut;
+        pd.active = 1;
+        pd.src = cur;
+        pd.dst = nxt;
+        cur = nxt;
+      }
+      sched->pass[j] = pd;
+    }
+    PassDesc cp{0, cur, in_place ? kBufIn : kBufOut, 0};
+    if (in_place) cp.active = (cur != kBufIn);
+    else cp.active = (cur != kBufOut);
+    sched->copy = cp;
+    sched->active_passes = k;
+  }
+}
+
+// Generic row-wise exclusive scan: one CTA of 1024 threads per row.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) scan_rows_kernel(const uint64_t* __restrict__ in,
+                                                                 uint64_t* __restrict__ out, uint64_t bins) {
+  __shared__ uint64_t s_warp[32];
+  const uint64_t* r_in = in + blockIdx.x * bins;
+  uint64_t* r_out = out + blockIdx.x * bins;
+  const uint64_t per = (bins + kScanThreads - 1) / kScanThreads;
+  const uint64_t lo = threadIdx.x * per;
+  const uint64_t hi = (lo + per < bins) ? lo + per : bins;
+  uint64_t sum = 0;
+  for (uint64_t i = lo; i < hi; ++i) sum += r_in[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  uint64_t before = 0;
+  for (int w = 0; w < warp; ++w) before += s_warp[w];
+  uint64_t run = before + inc - sum;
+  for (uint64_t i = lo; i < hi; ++i) {
+    const uint64_t c = r_in[i];
+    r_out[i] = run;
+    run += c;
+  }
+}
+
+// Final copy of keys (and values) between buffers when the schedule asks.
+template <typename K>
+__global__ void schedule_copy_kernel(const K* k0, const K* k1, const K* k2, const uint32_t* v0, const uint32_t* v1,
+                                     const uint32_t* v2, uint64_t n, const Schedule* sched) {
+  const PassDesc cp = sched->copy;
+  if (!cp.active) return;
+  const K* ks[3] = {k0, k1, k2};
+  const uint32_t* vs[3] = {v0, v1, v2};
+  const K* src = ks[cp.src];
+  K* dst = const_cast<K*>(ks[cp.dst]);
+  const uint32_t* vsrc = vs[cp.src];
+  uint32_t* vdst = const_cast<uint32_t*>(vs[cp.dst]);
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  constexpr uint64_t kVec = 16 / sizeof(K);
+  const uint64_t nv = n / kVec;
+  for (uint64_t i = tid; i < nv; i += stride)
+    reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+  for (uint64_t i = nv * kVec + tid; i < n; i += stride) dst[i] = src[i];
+  if (vsrc && vdst) {
+    const uint64_t nv4 = n / 4;
+    for (uint64_t i = tid; i < nv4; i += stride)
+      reinterpret_cast<uint4*>(vdst)[i] = reinterpret_cast<const uint4*>(vsrc)[i];
+    for (uint64_t i = nv4 * 4 + tid; i < n; i += stride) vdst[i] = vsrc[i];
+  }
+}
+
+// --------------------------------------------------------------- K1' -------
+// 65,536 counters of 16 bits, two per 32-bit shared-memory word (128 KB).
+// Counters are added with red.shared (no return value).  Every round of
+// kLeafRound keys per CTA is followed by a drain: any counter that reached
+// 2^15 hands 2^15 to its global 64-bit spill counter.  After a drain every
+// counter is below 2^15, and a round adds at most kLeafRound = 2^15 to any
+// counter, so no counter ever exceeds 2^16 - 1 (no carry into the neighbour
+// half) -- the counter width follows the size of what one round can count,
+// as the tapering of Sec. III-D-1 asks, and overflow is exact.
+constexpr int kLeafThreads = 1024;
+constexpr int kLeafWords = 32768;
+constexpr int kLeafVecPerThread = 4;                                   // uint4 = 8 keys each
+constexpr int kLeafRound = kLeafThreads * kLeafVecPerThread * 8;       // 32768 keys
+static_assert(kLeafRound <= 32768, "a round must not be able to overflow a drained 16-bit counter");
+
+__global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16_t* __restrict__ keys, uint64_t n,
+                                                                    uint32_t* __restrict__ partials,
+                                                                    unsigned long long* __restrict__ spill) {
+  extern __shared__ uint32_t hw[];
+  for (int i = threadIdx.x; i < kLeafWords; i += blockDim.x) hw[i] = 0;
+  __syncthreads();
+  // Rounds are dealt to CTAs round-robin over the whole input.
+  const uint64_t rounds = (n + kLeafRound - 1) / kLeafRound;
+  auto add = [&](uint32_t k) { atomicAdd(&hw[k >> 1], 1u << ((k & 1) * 16)); };
+  for (uint64_t r = blockIdx.x; r < rounds; r += gridDim.x) {
+    const uint64_t base = r * kLeafRound;
+    if (base + kLeafRound <= n) {
+      uint4 q[kLeafVecPerThread];
+#pragma unroll
+      for (int u = 0; u < kLeafVecPerThread; ++u)
+        q[u] = __ldg(reinterpret_cast<const uint4*>(keys + base) + u * kLeafThreads + threadIdx.x);
+#pragma unroll
+      for (int u = 0; u < kLeafVecPerThread; ++u) {
+        const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          add(w[e] & 0xFFFFu);
+          add(w[e] >> 16);
+        }
+      }
+    } else {
+      for (uint64_t i = base + threadIdx.x; i < n; i += blockDim.x) add(keys[i]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kLeafWords; i += blockDim.x) {
+      uint32_t w = hw[i];
+      if ((w & 0x8000u) | (w & 0x80000000u)) {
+        if (w & 0x8000u) {
+          atomicAdd(&spill[2 * i], 0x8000ull);
+          w -= 0x8000u;
+        }
+        if (w & 0x80000000u) {
+          atomicAdd(&spill[2 * i + 1], 0x8000ull);
+          w -= 0x80000000u;
+        }
+        hw[i] = w;
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < kLeafWords; i += blockDim.x) partials[uint64_t(blockIdx.x) * kLeafWords + i] = hw[i];
+}
+
+__global__ void leaf_reduce_kernel(const uint32_t* __restrict__ partials, const uint64_t* __restrict__ spill,
+                                   int grid, uint64_t* __restrict__ counts) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= kLeafWords) return;
+  uint64_t lo = spill[2 * w], hi = spill[2 * w + 1];
+  for (int c = 0; c < grid; ++c) {
+    const uint32_t x = partials[uint64_t(c) * kLeafWords + w];
+    lo += x & 0xFFFFu;
+    hi += x >> 16;
+  }
+  counts[2 * w] = lo;
+  counts[2 * w + 1] = hi;
+}
+
+// ---------------------------------------------------------------- K4 -------
+// Output-centric: each CTA covers kExpandPerCta consecutive output positions.
+// Thread 0 finds the bins of the first and last position by binary search
+// over the 65,537 bin boundaries; each thread then writes 8 consecutive keys
+// (one 16-byte store) after locating its first key's bin inside that range.
+constexpr int kExpandThreads = 256;
+constexpr int kExpandPerThread = 8;
+constexpr int kExpandPerCta = kExpandThreads * kExpandPerThread * 4;
+
+__device__ __forceinline__ uint32_t bin_of(const uint64_t* off, uint32_t lo, uint32_t hi, uint64_t pos) {
+  // largest v in [lo, hi] with off[v] <= pos (off ascending, off[lo] <= pos)
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= pos) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kExpandThreads) expand_kernel(const uint64_t* __restrict__ offsets,
+                                                                uint16_t* __restrict__ out, uint64_t n) {
+  __shared__ uint32_t s_range[2];
+  const uint64_t c0 = uint64_t(blockIdx.x) * kExpandPerCta;
+  const uint64_t c1 = (c0 + kExpandPerCta < n) ? c0 + kExpandPerCta : n;
+  if (threadIdx.x == 0) {
+    s_range[0] = bin_of(offsets, 0, 65535, c0);
+    s_range[1] = bin_of(offsets, s_range[0], 65535, c1 - 1);
+  }
+  __syncthreads();
+  const uint32_t b_lo = s_range[0], b_hi = s_range[1];
+  for (uint64_t p0 = c0 + uint64_t(threadIdx.x) * kExpandPerThread; p0 < c1;
+       p0 += uint64_t(kExpandThreads) * kExpandPerThread) {
+    uint32_t b = bin_of(offsets, b_lo, b_hi, p0);
+    uint64_t next = (b < 65535) ? offsets[b + 1] : n;
+    if (p0 + kExpandPerThread <= c1) {
+      uint16_t v[kExpandPerThread];
+#pragma unroll
+      for (int e = 0; e < kExpandPerThread; ++e) {
+        while (p0 + e >= next) {
+          ++b;
+          next = (b < 65535) ? offsets[b + 1] : n;
+        }
+        v[e] = uint16_t(b);
+      }
+      uint4 q;
+      q.x = uint32_t(v[0]) | (uint32_t(v[1]) << 16);
+      q.y = uint32_t(v[2]) | (uint32_t(v[3]) << 16);
+      q.z = uint32_t(v[4]) | (uint32_t(v[5]) << 16);
+      q.w = uint32_t(v[6]) | (uint32_t(v[7]) << 16);
+      *reinterpret_cast<uint4*>(out + p0) = q;
+    } else {
+      for (uint64_t p = p0; p < c1; ++p) {
+        while (p >= next) {
+          ++b;
+          next = (b < 65535) ? offsets[b + 1] : n;
+        }
+        out[p] = uint16_t(b);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers ----
+
+cudaError_t launch_histogram(const void* keys, int key_bits, uint64_t n, uint64_t chunk_keys, const DigitPlan& plan,
+                             uint64_t* hist, uint64_t pass_stride, uint64_t chunk_stride, uint32_t* clear,
+                             uint64_t clear_words, int sms, cudaStream_t stream) {
+  const uint64_t chunks = n ? (n + chunk_keys - 1) / chunk_keys : 1;
+  // About two resident CTAs per SM over all chunks.
+  uint64_t per_chunk = (uint64_t(sms) * 2 + chunks - 1) / chunks;
+  if (per_chunk < 1) per_chunk = 1;
+  const uint64_t keys_per_chunk = n < chunk_keys ? n : chunk_keys;
+  const uint64_t max_useful = (keys_per_chunk + 8 * kHistThreads - 1) / (8 * kHistThreads);
+  if (per_chunk > max_useful && max_useful > 0) per_chunk = max_useful;
+  const dim3 grid{unsigned(per_chunk), unsigned(chunks), 1u};
+  switch (key_bits) {
+    case 16:
+      hist_kernel<uint16_t><<<grid, kHistThreads, 0, stream>>>(static_cast<const uint16_t*>(keys), n, chunk_keys,
+                                                               plan, hist, pass_stride, chunk_stride, clear,
+                                                               clear_words);
+      break;
+    case 32:
+      hist_kernel<uint32_t><<<grid, kHistThreads, 0, stream>>>(static_cast<const uint32_t*>(keys), n, chunk_keys,
+                                                               plan, hist, pass_stride, chunk_stride, clear,
+                                                               clear_words);
+      break;
+    case 64:
+      hist_kernel<uint64_t><<<grid, kHistThreads, 0, stream>>>(static_cast<const uint64_t*>(keys), n, chunk_keys,
+                                                               plan, hist, pass_stride, chunk_stride, clear,
+                                                               clear_words);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_schedule(uint64_t* hist, uint64_t* bases, int passes, uint32_t chunks, int in_place,
+                                 Schedule* sched, cudaStream_t stream) {
+  scan_schedule_kernel<<<1, kRadix, 0, stream>>>(hist, bases, passes, chunks, in_place, sched);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_rows(const uint64_t* in, uint64_t* out, uint64_t rows, uint64_t bins, cudaStream_t stream) {
+  if (!rows || !bins) return cudaSuccess;
+  scan_rows_kernel<<<unsigned(rows), kScanThreads, 0, stream>>>(in, out, bins);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schedule_copy(const void* const keys[3], const uint32_t* const vals[3], int key_bits,
+                                 bool has_vals, uint64_t n, const Schedule* sched, int sms, cudaStream_t stream) {
+  const unsigned grid = unsigned(sms) * 4;
+  const uint32_t* v0 = has_vals ? vals[0] : nullptr;
+  const uint32_t* v1 = has_vals ? vals[1] : nullptr;
+  const uint32_t* v2 = has_vals ? vals[2] : nullptr;
+  switch (key_bits) {
+    case 16:
+      schedule_copy_kernel<uint16_t><<<grid, 256, 0, stream>>>(
+          static_cast<const uint16_t*>(keys[0]), static_cast<const uint16_t*>(keys[1]),
+          static_cast<const uint16_t*>(keys[2]), v0, v1, v2, n, sched);
+      break;
+    case 32:
+      schedule_copy_kernel<uint32_t><<<grid, 256, 0, stream>>>(
+          static_cast<const uint32_t*>(keys[0]), static_cast<const uint32_t*>(keys[1]),
+          static_cast<const uint32_t*>(keys[2]), v0, v1, v2, n, sched);
+      break;
+    case 64:
+      schedule_copy_kernel<uint64_t><<<grid, 256, 0, stream>>>(
+          static_cast<const uint64_t*>(keys[0]), static_cast<const uint64_t*>(keys[1]),
+          static_cast<const uint64_t*>(keys[2]), v0, v1, v2, n, sched);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int leaf_hist_grid(int sms) { return sms; }
+
+cudaError_t launch_leaf_histogram(const uint16_t* keys, uint64_t n, uint32_t* partials, uint64_t* spill, int sms,
+                                  cudaStream_t stream) {
+  static bool attr_set = false;
+  const size_t smem = size_t(kLeafWords) * 4;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(leaf_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cudaError_t e = cudaMemsetAsync(spill, 0, sizeof(uint64_t) * 65536, stream);
+  if (e != cudaSuccess) return e;
+  leaf_hist_kernel<<<leaf_hist_grid(sms), kLeafThreads, smem, stream>>>(
+      keys, n, partials, reinterpret_cast<unsigned long long*>(spill));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_reduce(const uint32_t* partials, const uint64_t* spill, int grid, uint64_t* counts,
+                               cudaStream_t stream) {
+  leaf_reduce_kernel<<<kLeafWords / 256, 256, 0, stream>>>(partials, spill, grid, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const uint64_t* offsets, uint16_t* keys_out, uint64_t n, cudaStream_t stream) {
+  if (!n) return cudaSuccess;
+  const uint64_t grid = (n + kExpandPerCta - 1) / kExpandPerCta;
+  expand_kernel<<<unsigned(grid), kExpandThreads, 0, stream>>>(offsets, keys_out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace fsort

@@ -1,0 +1,79 @@
+// fsort_internal.h -- launchers shared between the kernel translation units
+// and the C-ABI layer.  Host-only declarations; no CUDA types beyond streams.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fsort_dev.cuh"
+
+namespace fsort {
+
+// Digit plan of one sort: pass j extracts bits [shift[j], shift[j] + width[j]).
+struct DigitPlan {
+  int32_t passes;
+  int32_t pad;
+  uint32_t shift[kMaxPasses];
+  uint32_t mask[kMaxPasses];
+};
+
+// Keys per scatter tile for each key width (also sizes the look-back regions).
+int tile_keys_for(int key_bits);
+// Keys per look-back chunk: whole tiles, fewer than 2^30 keys.
+uint64_t chunk_keys_for(int key_bits);
+
+// K1: per-pass digit histograms of keys[0, n).  hist[j * pass_stride +
+// chunk * chunk_stride + d] += count of digit d of pass j among the keys of
+// look-back chunk `chunk` (chunk_stride 0 folds all chunks into one row).
+// Also zeroes clear_words words at `clear` (the first pass's look-back region
+// and the tile counters) on the way.
+cudaError_t launch_histogram(const void* keys, int key_bits, uint64_t n, uint64_t chunk_keys, const DigitPlan& plan,
+                             uint64_t* hist, uint64_t pass_stride, uint64_t chunk_stride, uint32_t* clear,
+                             uint64_t clear_words, int sms, cudaStream_t stream);
+
+// K2: per pass, exclusive scan over digits of the chunk-summed histogram, the
+// 64-bit base of every (chunk, digit), and the device-side pass schedule.
+// hist/bases are [passes][chunks][256]; hist is left all zero.  in_place: the result must land in the
+// input buffer.  sched may be null (no schedule: used by the one-pass step).
+cudaError_t launch_scan_schedule(uint64_t* hist, uint64_t* bases, int passes, uint32_t chunks, int in_place,
+                                 Schedule* sched, cudaStream_t stream);
+
+// Row-wise exclusive scan, one CTA per row (bins <= 65536).
+cudaError_t launch_scan_rows(const uint64_t* in, uint64_t* out, uint64_t rows, uint64_t bins, cudaStream_t stream);
+
+// K3: one stable scatter pass.
+struct OnesweepArgs {
+  const void* keys[3];     // by BufSel: input, plan scratch, output
+  const uint32_t* vals[3];
+  uint64_t n;
+  uint32_t shift;
+  uint32_t mask;
+  uint32_t* lookback;      // this pass's region, [tiles][256] words, zero on entry
+  uint32_t* tile_counter;  // this pass's dynamic tile counter, zero on entry
+  uint32_t* next_lookback; // region the next pass will use (cleared here), or null
+  uint32_t* next_counter;  // the next pass's counter (cleared here), or null
+  const uint64_t* bases;   // [chunks][256]
+  const Schedule* sched;   // null: always run, input -> output
+  int32_t pass;
+  uint32_t tiles_per_chunk;
+  uint32_t* status;
+};
+cudaError_t launch_onesweep(const OnesweepArgs& args, int key_bits, bool has_vals, cudaStream_t stream);
+
+// Final copy when the schedule leaves the result in the wrong buffer.
+cudaError_t launch_schedule_copy(const void* const keys[3], const uint32_t* const vals[3], int key_bits,
+                                 bool has_vals, uint64_t n, const Schedule* sched, int sms, cudaStream_t stream);
+
+// Expand path (16-bit keys, precision 16, keys only).
+// K1 leaf histogram with 16-bit tapered counters: per-CTA packed partials
+// [grid][32768] words plus exact overflow spills [65536] (spill zeroed here).
+int leaf_hist_grid(int sms);
+cudaError_t launch_leaf_histogram(const uint16_t* keys, uint64_t n, uint32_t* partials, uint64_t* spill, int sms,
+                                  cudaStream_t stream);
+// Sum the partials and spills into counts[65536].
+cudaError_t launch_leaf_reduce(const uint32_t* partials, const uint64_t* spill, int grid, uint64_t* counts,
+                               cudaStream_t stream);
+// K4: keys_out[offsets[v] .. offsets[v] + counts[v]) = v.
+cudaError_t launch_expand(const uint64_t* offsets, uint16_t* keys_out, uint64_t n, cudaStream_t stream);
+
+}  // namespace fsort

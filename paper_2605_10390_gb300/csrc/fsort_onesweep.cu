@@ -1,0 +1,325 @@
+// fsort_onesweep.cu -- K3, the stable scatter of one radix pass (Sec. II:
+// "stable scatter"), in a single read and write of keys and values.
+//
+// One CTA per tile of kTile consecutive keys, tiles taken in order from a
+// dynamic counter so that a tile only ever waits for tiles already running.
+//
+//  1. A bulk async copy (cp.async.bulk + mbarrier) stages the tile's keys and
+//     values in shared memory.
+//  2. Stable rank within each warp's strip of the tile: for every round of 32
+//     keys, each lane adds its lane bit to a warp-private shared word of its
+//     digit; the word then holds exactly the __match_any_sync peer mask of the
+//     lane (lanes with the same digit).  The lowest peer adds the group size to
+//     the warp's 16-bit-range digit counter and broadcasts the old value; a
+//     lane's rank is that value plus its peers below it.  (The hardware
+//     match.any instruction computes the same mask but measured 5-6x slower on
+//     uniform 8-bit digits on GB300; see the design notes.)
+//  3. Warp counters -> per-warp exclusive prefixes and the tile's digit counts,
+//     published at once to the decoupled look-back (2-bit flag | 30-bit count,
+//     the tapered counter width of Sec. III-D-1: a chunk never holds 2^30 keys).
+//  4. Keys and values are permuted into digit order inside shared memory.
+//  5. The look-back walks predecessor tiles (bounded wait) to find each digit's
+//     exclusive prefix among earlier tiles of the chunk, adds the chunk's 64-bit
+//     base from the scan, and publishes its inclusive prefix.
+//  6. The staged tile is written out in digit runs, consecutive threads to
+//     consecutive addresses.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fsort_dev.cuh"
+#include "fsort_internal.h"
+
+namespace fsort {
+namespace {
+
+constexpr int kRadix = 256;
+constexpr int kBlock = 256;  // == kRadix: thread d owns digit d in the per-digit steps
+
+template <typename K>
+struct TileShape;
+template <>
+struct TileShape<uint16_t> { static constexpr int kIpt = 32; };
+template <>
+struct TileShape<uint32_t> { static constexpr int kIpt = 24; };
+template <>
+struct TileShape<uint64_t> { static constexpr int kIpt = 16; };
+
+template <typename K, bool kVals>
+struct SmemLayout {
+  static constexpr int kIpt = TileShape<K>::kIpt;
+  static constexpr int kTile = kBlock * kIpt;
+  static constexpr int kWarps = kBlock / 32;
+  static constexpr size_t kKeys = 0;
+  static constexpr size_t kVals_ = kKeys + size_t(kTile) * sizeof(K);
+  static constexpr size_t kMask = kVals_ + (kVals ? size_t(kTile) * 4 : 0);
+  static constexpr size_t kWcnt = kMask + 2 * size_t(kWarps) * kRadix * 4;  // masks double-buffered
+  static constexpr size_t kExcl = kWcnt + size_t(kWarps) * kRadix * 4;
+  static constexpr size_t kCnt = kExcl + kRadix * 4;
+  static constexpr size_t kOff = kCnt + kRadix * 4;  // 8-byte aligned: all above are multiples of 1 KB
+  static constexpr size_t kScan = kOff + kRadix * 8;
+  static constexpr size_t kBar = kScan + 8 * 4;
+  static constexpr size_t kTileId = kBar + 8;
+  static constexpr size_t kBytes = kTileId + 16;
+};
+
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t x, uint32_t* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  uint32_t before = 0;
+#pragma unroll
+  for (int w = 0; w < kBlock / 32; ++w)
+    if (w < warp) before += s_warp[w];
+  return before + inc - x;
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t dig(K k, uint32_t shift, uint32_t mask) {
+  if (sizeof(K) <= 4) return (uint32_t(k) >> shift) & mask;
+  return uint32_t(uint64_t(k) >> shift) & mask;
+}
+
+template <typename K, bool kVals>
+__global__ void __launch_bounds__(kBlock) onesweep_kernel(const OnesweepArgs a) {
+  using L = SmemLayout<K, kVals>;
+  constexpr int kIpt = L::kIpt;
+  constexpr int kTile = L::kTile;
+  constexpr int kWarps = L::kWarps;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  K* s_keys = reinterpret_cast<K*>(smem + L::kKeys);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + L::kVals_);
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem + L::kMask);
+  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem + L::kWcnt);
+  uint32_t* s_excl = reinterpret_cast<uint32_t*>(smem + L::kExcl);
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + L::kCnt);
+  unsigned long long* s_off = reinterpret_cast<unsigned long long*>(smem + L::kOff);
+  uint32_t* s_scan = reinterpret_cast<uint32_t*>(smem + L::kScan);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + L::kBar);
+  uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::kTileId);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  int src = kBufIn, dst = kBufOut, active = 1;
+  if (a.sched) {
+    const PassDesc pd = a.sched->pass[a.pass];
+    active = pd.active;
+    src = pd.src;
+    dst = pd.dst;
+  }
+  // The next pass uses the other look-back region: clear this block's slot of
+  // it (one block per tile, so the slots cover every tile) and its counter.
+  if (a.next_lookback) a.next_lookback[uint64_t(blockIdx.x) * kRadix + tid] = 0;
+  if (a.next_counter && blockIdx.x == 0 && tid == 0) *a.next_counter = 0;
+  if (!active) return;
+
+  if (tid == 0) {
+    *s_tile = atomicAdd(a.tile_counter, 1u);
+    mbar_init(s_bar, 1);
+    fence_mbar_init();
+  }
+  for (int i = tid; i < 2 * kWarps * kRadix; i += kBlock) s_mask[i] = 0;
+  for (int i = tid; i < kWarps * kRadix; i += kBlock) s_wcnt[i] = 0;
+  __syncthreads();
+
+  const uint32_t tile = *s_tile;
+  if (tile >= gridDim.x) {  // counter not reset: never index past the look-back region
+    if (tid == 0) atomicOr(a.status, kDevBadPlan);
+    return;
+  }
+  const uint64_t t0 = uint64_t(tile) * kTile;
+  const uint32_t tile_n = uint32_t((a.n - t0 < uint64_t(kTile)) ? (a.n - t0) : uint64_t(kTile));
+  const K* kin = static_cast<const K*>(a.keys[src]);
+  const uint32_t* vin = a.vals[src];
+
+  // 1. stage the tile: bulk copies for the 16-byte-aligned body, plain loads
+  // for a ragged end.
+  const uint32_t kbody = (tile_n * uint32_t(sizeof(K))) & ~15u;
+  const uint32_t vbody = kVals ? ((tile_n * 4u) & ~15u) : 0u;
+  if (tid == 0) {
+    mbar_arrive_expect_tx(s_bar, kbody + vbody);
+    if (kbody) bulk_copy_g2s(s_keys, kin + t0, kbody, s_bar);
+    if (vbody) bulk_copy_g2s(s_vals, vin + t0, vbody, s_bar);
+  }
+  for (uint32_t i = kbody / sizeof(K) + tid; i < tile_n; i += kBlock) s_keys[i] = kin[t0 + i];
+  if (kVals)
+    for (uint32_t i = vbody / 4 + tid; i < tile_n; i += kBlock) s_vals[i] = vin[t0 + i];
+  if (!mbar_wait_bounded(s_bar, 0)) atomicOr(a.status, kDevTimeoutLoad);
+  __syncthreads();
+
+  // 2. stable in-warp ranks
+  const uint32_t shift = a.shift, mask = a.mask;
+  const uint32_t lt = lanemask_lt(), me = 1u << lane;
+  // Peer-mask words alternate between two buffers by item parity: a word
+  // cleared by its group leader in item i is reused at item i + 2, after the
+  // warp barriers of item i + 1 have ordered the clear before the reuse.
+  uint32_t* wmask0 = s_mask + warp * kRadix;
+  uint32_t* wmask1 = s_mask + (kWarps + warp) * kRadix;
+  uint32_t* wcnt = s_wcnt + warp * kRadix;
+  const int wbase = warp * 32 * kIpt;
+  K keys[kIpt];
+  uint32_t rank[kIpt];
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    const int pos = wbase + i * 32 + lane;
+    const bool valid = uint32_t(pos) < tile_n;
+    const K k = valid ? s_keys[pos] : K(0);
+    keys[i] = k;
+    const uint32_t d = dig(k, shift, mask);
+    uint32_t* wmask = (i & 1) ? wmask1 : wmask0;
+    if (valid) atomicAdd(&wmask[d], me);
+    __syncwarp();
+    const uint32_t peers = valid ? wmask[d] : 0u;
+    const uint32_t below = __popc(peers & lt);
+    __syncwarp();
+    uint32_t base = 0;
+    if (valid && below == 0) {
+      base = atomicAdd(&wcnt[d], uint32_t(__popc(peers)));
+      wmask[d] = 0;
+    }
+    base = __shfl_sync(0xffffffffu, base, valid ? (__ffs(peers) - 1) : lane);
+    rank[i] = base + below;
+  }
+  __syncthreads();
+
+  // 3. per-digit: warp prefixes, tile count, publish, tile-exclusive prefix
+  const bool first_in_chunk = (tile % a.tiles_per_chunk) == 0;
+  uint32_t* lb = a.lookback + uint64_t(tile) * kRadix;
+  {
+    const int d = tid;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = s_wcnt[w * kRadix + d];
+      s_wcnt[w * kRadix + d] = run;
+      run += c;
+    }
+    s_cnt[d] = run;
+    st_relaxed_gpu(lb + d, (first_in_chunk ? kFlagPrefix : kFlagAggregate) | run);
+    s_excl[d] = block_excl_scan_u32(run, s_scan);
+  }
+  __syncthreads();
+
+  // 4. permute keys and values into digit order in shared memory
+  uint32_t vreg[kVals ? kIpt : 1];
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    const int pos = wbase + i * 32 + lane;
+    if (uint32_t(pos) < tile_n) {
+      const uint32_t d = dig(keys[i], shift, mask);
+      const uint32_t p = s_excl[d] + s_wcnt[warp * kRadix + d] + rank[i];
+      s_keys[p] = keys[i];
+      rank[i] = p;
+      if (kVals) vreg[i] = s_vals[pos];
+    }
+  }
+  __syncthreads();
+  if (kVals) {
+#pragma unroll
+    for (int i = 0; i < kIpt; ++i) {
+      const int pos = wbase + i * 32 + lane;
+      if (uint32_t(pos) < tile_n) s_vals[rank[i]] = vreg[i];
+    }
+  }
+
+  // 5. decoupled look-back for digit d = tid
+  {
+    const int d = tid;
+    const uint32_t cnt = s_cnt[d];
+    uint32_t excl = 0;
+    if (!first_in_chunk) {
+      const uint32_t chunk_first = tile - tile % a.tiles_per_chunk;
+      uint32_t t = tile - 1;
+      uint64_t t_start = 0;
+      while (true) {
+        const uint32_t w = ld_relaxed_gpu(a.lookback + uint64_t(t) * kRadix + d);
+        const uint32_t flag = w & ~kCountMask;
+        if (flag == 0) {
+          if (t_start == 0) t_start = global_timer_ns();
+          else if (global_timer_ns() - t_start > kWaitLimitNs) {
+            atomicOr(a.status, kDevTimeoutLookback);
+            break;
+          }
+          continue;
+        }
+        t_start = 0;
+        excl += w & kCountMask;
+        if (flag == kFlagPrefix) break;
+        if (t == chunk_first) {  // a chunk's first tile always publishes a prefix
+          atomicOr(a.status, kDevBadPlan);
+          break;
+        }
+        --t;
+      }
+      st_relaxed_gpu(lb + d, kFlagPrefix | (excl + cnt));
+    }
+    const uint64_t chunk = tile / a.tiles_per_chunk;
+    s_off[d] = a.bases[chunk * kRadix + d] + excl - s_excl[d];
+  }
+  __syncthreads();
+
+  // 6. write the staged tile out in digit runs
+  K* kout = const_cast<K*>(static_cast<const K*>(a.keys[dst]));
+  uint32_t* vout = const_cast<uint32_t*>(a.vals[dst]);
+  bool out_of_range = false;
+#pragma unroll 4
+  for (uint32_t s = tid; s < tile_n; s += kBlock) {
+    const K k = s_keys[s];
+    const uint64_t o = s_off[dig(k, shift, mask)] + s;
+    if (o >= a.n) {  // only reachable after a timed-out wait; never write outside the output
+      out_of_range = true;
+      continue;
+    }
+    kout[o] = k;
+    if (kVals) vout[o] = s_vals[s];
+  }
+  if (out_of_range) atomicOr(a.status, kDevBadPlan);
+}
+
+template <typename K, bool kVals>
+cudaError_t launch_typed(const OnesweepArgs& a, cudaStream_t stream) {
+  using L = SmemLayout<K, kVals>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<K, kVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(L::kBytes));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const uint64_t tiles = (a.n + L::kTile - 1) / L::kTile;
+  if (!tiles) return cudaSuccess;
+  onesweep_kernel<K, kVals><<<unsigned(tiles), kBlock, L::kBytes, stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tile_keys_for(int key_bits) {
+  switch (key_bits) {
+    case 16: return SmemLayout<uint16_t, true>::kTile;
+    case 32: return SmemLayout<uint32_t, true>::kTile;
+    case 64: return SmemLayout<uint64_t, true>::kTile;
+    default: return 0;
+  }
+}
+
+uint64_t chunk_keys_for(int key_bits) {
+  const uint64_t t = uint64_t(tile_keys_for(key_bits));
+  return t ? (kMaxChunkKeys / t) * t : 0;
+}
+
+cudaError_t launch_onesweep(const OnesweepArgs& args, int key_bits, bool has_vals, cudaStream_t stream) {
+  switch (key_bits) {
+    case 16: return has_vals ? launch_typed<uint16_t, true>(args, stream) : launch_typed<uint16_t, false>(args, stream);
+    case 32: return has_vals ? launch_typed<uint32_t, true>(args, stream) : launch_typed<uint32_t, false>(args, stream);
+    case 64: return has_vals ? launch_typed<uint64_t, true>(args, stream) : launch_typed<uint64_t, false>(args, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fsort

@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every symbol include/fsort.h declares.
+No compute: only calls that return before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2605_10390_gb300 as fs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if hdr.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", hdr)).read()
+            names += re.findall(r"FSORT_API\s+[\w\s\*]*?\b(fsort_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["fsort_plan_create", "fsort_plan_destroy", "fsort_plan_sync", "fsort_sort_pairs",
+                     "fsort_sort_pairs_out", "fsort_sort_pairs_host", "fsort_histogram", "fsort_exclusive_scan",
+                     "fsort_scatter_pass", "fsort_expand", "fsort_status_string"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(fs.lib_path())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    missing = [n for n in declared_functions() if not hasattr(fs, n)]
+    assert not missing, missing
+
+
+def test_calls_without_gpu_work():
+    assert fs.fsort_status_string(0) == "FSORT_OK"
+    assert fs.fsort_status_string(4) == "FSORT_ERR_TIMEOUT"
+    assert fs.fsort_status_string(99) == "FSORT_UNKNOWN_STATUS"
+    assert fs.fsort_version() >= 100
+    lib = fs.load_library()
+    assert lib.fsort_plan_create(None, None) == 1
+    h = ctypes.c_void_p()
+    for desc in [fs.FsortPlanDesc(max_n=0, key_bits=16, has_values=1, digit_bits=0, flags=0),
+                 fs.FsortPlanDesc(max_n=10, key_bits=24, has_values=1, digit_bits=0, flags=0),
+                 fs.FsortPlanDesc(max_n=10, key_bits=16, has_values=2, digit_bits=0, flags=0),
+                 fs.FsortPlanDesc(max_n=10, key_bits=16, has_values=1, digit_bits=0, flags=0x100)]:
+        assert lib.fsort_plan_create(ctypes.byref(desc), ctypes.byref(h)) == 1
+    desc = fs.FsortPlanDesc(max_n=10, key_bits=16, has_values=1, digit_bits=5, flags=0)
+    assert lib.fsort_plan_create(ctypes.byref(desc), ctypes.byref(h)) == 8
+    assert lib.fsort_plan_destroy(None) == 0
+    assert lib.fsort_plan_sync(None) == 1
+    assert lib.fsort_sort_pairs(None, None, None, 10, 16, 16, None) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2605_10390_gb300 import _binding
+    monkeypatch.setattr(_binding, "_LIB", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(_binding, "_lib", None)
+    with pytest.raises(RuntimeError):
+        _binding.load_library()
