@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Throughput of libfsort on the 512 MB workload, with its HBM roofline.
+
+Workload (one step): five out-of-place stable sorts of 2^28 uint16 keys with
+uint32 values (the original index) at 16-bit precision, one per seeded
+distribution (uniform, Zipf s=1.1, Gaussian N(32768, 1024), 90 % presorted,
+all-equal): 512 MB of keys+values per sort, 7.5 GB per step.  Inputs are
+generated in HBM before timing and are far larger than L2 (1.5 GiB per sort vs
+129 MB), so no L2 flush is needed.
+
+Printed JSON line (rank 0): value = whole-job Gkeys/s (keys sorted by all ranks
+/ max-over-ranks device time), plus
+  roofline      the dominant kernel (the scatter pass): algorithmic bytes per
+                launch (read + write of keys and values, 12 n) / its average
+                CUDA-event duration over the timed region, against the measured
+                HBM copy peak; traffic = DRAM bytes per launch from an ncu
+                capture of the same kernel source, or null
+  job_hbm       the whole step's algorithmic bytes over its time
+  cpu_baseline  the CPU oracle on this machine's host cores, on a bounded sample
+  e2e           the same metric through fsort_sort_pairs_host with pinned host
+                buffers (H2D + sort + D2H inside the timed region)
+  clocks        nvidia-smi samples taken during the timed region
+
+--impl reference times the CPU oracle as the reference arm (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DISTS = ["uniform", "zipf1.1", "gauss", "presorted", "equal"]
+LOG2N = 28
+KEY_BITS = 16
+PRECISION = 16
+WORKLOAD = ("512 MB: 2^28 uint16 keys + uint32 index values, stable, 16-bit precision, out of place; "
+            "5 distributions per step (uniform, zipf s=1.1, gauss mu=32768 sigma=1024, 90% presorted, all-equal)")
+METRIC = "Gkeys/s (16-bit keys + 32-bit values, 512 MB per sort, 5 distributions)"
+SCATTER_SRC = [os.path.join(ROOT, "paper_2605_10390_gb300", "csrc", f) for f in ("fsort_onesweep.cu", "fsort_dev.cuh")]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fsort", choices=["fsort", "reference"])
+    ap.add_argument("--log2n", type=int, default=LOG2N, help="keys per sort (log2); the workload is 28")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    return 6800.0, "fallback (6.8 TB/s, earlier GB300 measurement)"
+
+
+def source_hash(paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(n):
+    """DRAM bytes per scatter launch from the committed ncu summary, if it was
+    taken on the current kernel source; scaled to n keys if taken smaller."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None, "no ncu capture committed"
+    with open(path) as f:
+        d = json.load(f).get("scatter")
+    if not d or d.get("source_sha256") != source_hash(SCATTER_SRC):
+        return None, "kernel changed since the ncu capture"
+    return d["bytes_per_launch"] * n / d["n"], d.get("note", "")
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [[c.strip() for c in line.split(",")] for line in out.strip().splitlines() if line.count(",") >= 8]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds: float = 10.0, log2n: int = 24):
+    """The CPU oracle (single-threaded C) on a bounded sample of the same
+    workload: 2^log2n keys of each distribution, repeated for >= `seconds`."""
+    import numpy as np
+
+    import oracle
+    import workloads
+
+    samples = [(workloads.generate(d, 1 << log2n, KEY_BITS, seed=0, stream=i),
+                np.arange(1 << log2n, dtype=np.uint32)) for i, d in enumerate(DISTS)]
+    oracle.sort(samples[0][0][:1000], samples[0][1][:1000], KEY_BITS, PRECISION)  # load + warm
+    keys = 0
+    t0 = time.perf_counter()
+    while True:
+        for k, v in samples:
+            oracle.sort(k, v, KEY_BITS, PRECISION)
+            keys += k.size
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": keys / el / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": f"5 distributions x 2^{log2n} keys (uint16 + uint32 index, p=16), repeated for {el:.1f} s, "
+                      f"single-threaded C LSD counting sort on {os.cpu_count()} host cores (1 used)"}
+
+
+def run_reference(args, rank: int):
+    """Reference arm: the CPU oracle, timed per step on a bounded sample."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import workloads
+
+    total_steps = args.steps + args.warmup
+    log2n = 26
+    while log2n > 18 and total_steps * 5 * (1 << log2n) * 9e-9 > 120:  # keep the run to about two minutes
+        log2n -= 1
+    n = 1 << log2n
+    samples = [(workloads.generate(d, n, KEY_BITS, seed=0, stream=i), np.arange(n, dtype=np.uint32))
+               for i, d in enumerate(DISTS)]
+    for _ in range(args.warmup):
+        for k, v in samples:
+            oracle.sort(k, v, KEY_BITS, PRECISION)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for k, v in samples:
+            oracle.sort(k, v, KEY_BITS, PRECISION)
+    el = time.perf_counter() - t0
+    value = args.steps * 5 * n / el / 1e9
+    sample = f"each step: 5 distributions x 2^{log2n} keys (bounded sample of the 2^28-key workload)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference": "CPU oracle (single-threaded C LSD counting sort)",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import workloads
+    import paper_2605_10390_gb300 as fs
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    n = 1 << args.log2n
+    stream = torch.cuda.current_stream()
+
+    # Inputs in HBM (generated on the device by the shared workload generator).
+    inputs = []
+    for i, d in enumerate(DISTS):
+        keys = torch.empty(n, dtype=torch.uint16, device="cuda")
+        vals = torch.empty(n, dtype=torch.uint32, device="cuda")
+        table = workloads.table_for(d, KEY_BITS)
+        tdev = torch.from_numpy(table).cuda() if table is not None else None
+        workloads.generate_device(d, keys.data_ptr(), n, KEY_BITS, seed=rank, stream=i,
+                                  cuda_stream=stream.cuda_stream, table_dev_ptr=tdev.data_ptr() if tdev is not None else None)
+        workloads.iota_device(vals.data_ptr(), n, cuda_stream=stream.cuda_stream)
+        inputs.append((keys, vals))
+    keys_out = torch.empty(n, dtype=torch.uint16, device="cuda")
+    vals_out = torch.empty(n, dtype=torch.uint32, device="cuda")
+    torch.cuda.synchronize()
+
+    plan = fs.Plan(n, KEY_BITS, has_values=True)
+    info = plan.describe(n, PRECISION, True)
+
+    def step():
+        for k, v in inputs:
+            plan.sort_out(k, v, keys_out, vals_out, precision_bits=PRECISION)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync()
+    fs.fsort_plan_set_timing(plan.handle, True)
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    plan.sync()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    recs = fs.fsort_plan_timing_report(plan.handle, 1 << 14)
+    fs.fsort_plan_set_timing(plan.handle, False)
+
+    keys_total = world * args.steps * len(DISTS) * n
+    value = keys_total / (ms / 1e3) / 1e9
+
+    # Roofline of the dominant kernel (scatter): algorithmic 12 n bytes per active launch.
+    kb, vb = KEY_BITS // 8, 4
+    sc = [r for r in recs if r["kind"] == "scatter" and r["active"]]
+    sc_ms = sum(r["ms"] for r in sc)
+    per_launch = 2 * (kb + vb) * n
+    peak, peak_src = measured_peaks()
+    achieved = (per_launch * len(sc) / (sc_ms / 1e3) / 1e9) if sc_ms > 0 else None
+    traffic, traffic_note = ncu_traffic(n)
+    kernels = {}
+    for r in recs:
+        key = r["kind"] + ("" if r["active"] else "_skipped")
+        kk = kernels.setdefault(key, {"launches": 0, "ms": 0.0})
+        kk["launches"] += 1
+        kk["ms"] += r["ms"]
+    total_kernel_ms = sum(v["ms"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["ms"] / total_kernel_ms
+        v["avg_us"] = v["ms"] / v["launches"] * 1e3
+    # Whole-step algorithmic bytes: one key read for the histogram, read+write of
+    # keys+values per executed pass, and read+write for a final copy when run.
+    calls = {}
+    for r in recs:
+        c = calls.setdefault(r["call"], {"ms": 0.0, "bytes": kb * n})
+        c["ms"] += r["ms"]
+        if r["kind"] in ("scatter", "copy") and r["active"]:
+            c["bytes"] += 2 * (kb + vb) * n
+    job_bytes = sum(c["bytes"] for c in calls.values()) / max(1, args.steps)
+    per_dist = {}
+    for idx, c in calls.items():
+        per_dist.setdefault(DISTS[idx % len(DISTS)], []).append(c["ms"])
+    per_dist_gkeys = {d: n / (statistics.mean(v) / 1e3) / 1e9 for d, v in per_dist.items()}
+
+    result = None
+    if rank == 0:
+        ms_per_step = ms / args.steps
+        result = {
+            "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_per_sort": n, "key_bits": KEY_BITS, "precision_bits": PRECISION,
+                       "values": "uint32 original index", "sorts_per_step": len(DISTS), "digit_bits": info["digit_bits"],
+                       "tile_keys": info["tile_keys"], "l2": "inputs larger than L2 (1.5 GiB per sort), no flush",
+                       "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "kernel": "onesweep scatter pass (K3)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": per_launch, "launches": len(sc),
+                         "avg_launch_ms": sc_ms / len(sc) if sc else None, "peak_source": peak_src,
+                         "traffic_note": traffic_note},
+            "job_hbm": {"algorithmic_bytes_per_step": job_bytes,
+                        "achieved_gbs": job_bytes / (ms_per_step / 1e3) / 1e9,
+                        "frac": job_bytes / (ms_per_step / 1e3) / 1e9 / peak},
+            "per_distribution_gkeys": per_dist_gkeys,
+            "kernels": kernels,
+            "gpu_launches": len(recs),
+            "clocks": clocks,
+        }
+    plan.close()
+    del inputs
+
+    # End to end through the public host-buffer entry point (rank-local).
+    e2e = None
+    if not args.no_e2e:
+        hplan = fs.Plan(n, KEY_BITS, has_values=True, flags=fs.FSORT_FLAG_HOST_IO)
+        pristine = [(torch.from_numpy(workloads.generate(d, n, KEY_BITS, seed=rank, stream=i)).pin_memory(),
+                     torch.from_numpy(np.arange(n, dtype=np.uint32)).pin_memory()) for i, d in enumerate(DISTS)]
+        wk = torch.empty(n, dtype=torch.uint16).pin_memory()
+        wv = torch.empty(n, dtype=torch.uint32).pin_memory()
+        e2e_steps = max(1, min(args.steps, 10))
+        total = 0.0
+        for s in range(e2e_steps + 1):
+            for pk, pv in pristine:
+                wk.copy_(pk)
+                wv.copy_(pv)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fs.fsort_sort_pairs_host(hplan.handle, wk, wv, key_bits=KEY_BITS, precision_bits=PRECISION)
+                if s > 0:  # first round warms up
+                    total += time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([total], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        e2e = {"value": world * e2e_steps * len(DISTS) * n / total / 1e9, "unit": "Gkeys/s",
+               "h2d_bytes_per_step": len(DISTS) * n * (kb + vb), "d2h_bytes_per_step": len(DISTS) * n * (kb + vb),
+               "steps": e2e_steps, "api": "fsort_sort_pairs_host (pinned host buffers, synchronous)"}
+        hplan.close()
+    if rank == 0:
+        result["e2e"] = e2e
+        if world == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline()
+        else:
+            result["cpu_baseline"] = None
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -161,6 +161,39 @@ FSORT_API fsort_status fsort_scatter_pass(fsort_plan* plan, const void* keys_in,
 FSORT_API fsort_status fsort_expand(fsort_plan* plan, const uint64_t* counts, void* keys_out, uint64_t n, int key_bits,
                           void* stream);
 
+/* ---- per-kernel device timing (instrumentation) --------------------------- */
+
+/* Kernel kinds reported by fsort_plan_timing_report. */
+#define FSORT_KERNEL_HISTOGRAM 1   /* step 2, per-pass digit histograms */
+#define FSORT_KERNEL_SCAN 2        /* step 3 with the pass schedule */
+#define FSORT_KERNEL_SCATTER 3     /* step 4, one pass */
+#define FSORT_KERNEL_COPY 4        /* final copy when the schedule needs one */
+#define FSORT_KERNEL_LEAF_HIST 5   /* expand path: 65,536-bin histogram */
+#define FSORT_KERNEL_LEAF_REDUCE 6 /* expand path: sum of per-CTA partial counts */
+#define FSORT_KERNEL_LEAF_SCAN 7   /* expand path: exclusive scan of 65,536 bins */
+#define FSORT_KERNEL_EXPAND 8      /* step 5 */
+
+typedef struct fsort_kernel_time {
+  int32_t kind;   /* FSORT_KERNEL_* */
+  int32_t pass;   /* scatter pass index, else -1 */
+  int32_t active; /* scatter/copy: 1 if the device schedule ran it (0: exited at once); others 1 */
+  int32_t call;   /* index of the sort call since timing was enabled or last reported */
+  uint64_t n;     /* keys of that call */
+  float ms;       /* device time between CUDA events recorded around the launch on the call's stream */
+  float reserved;
+} fsort_kernel_time;
+
+/* Enable (1) or disable (0) per-kernel timing on this plan.  While enabled,
+ * every sort call records a CUDA event before its first kernel and after each
+ * kernel on the call's stream (a pool of 8192 events, allocated here; calls
+ * beyond the pool are not recorded).  Disabling frees the pool. */
+FSORT_API fsort_status fsort_plan_set_timing(fsort_plan* plan, int enable);
+
+/* Wait for the recorded calls, write up to `capacity` records to `out` (host
+ * memory), set *count to the number written, and start a new recording. */
+FSORT_API fsort_status fsort_plan_timing_report(fsort_plan* plan, fsort_kernel_time* out, uint32_t capacity,
+                                                uint32_t* count);
+
 /* Human-readable name of a status code (static storage). */
 FSORT_API const char* fsort_status_string(fsort_status status);
 

@@ -12,6 +12,8 @@ Low-level names mirror the C ABI (``fsort_plan_create``, ``fsort_sort_pairs``,
 from ._binding import (  # noqa: F401
     FSORT_FLAG_HOST_IO,
     FsortError,
+    FsortKernelTime,
+    KERNEL_KINDS,
     FsortPlanDesc,
     FsortPlanInfo,
     Plan,
@@ -22,7 +24,9 @@ from ._binding import (  # noqa: F401
     fsort_plan_create,
     fsort_plan_describe,
     fsort_plan_destroy,
+    fsort_plan_set_timing,
     fsort_plan_sync,
+    fsort_plan_timing_report,
     fsort_scatter_pass,
     fsort_sort_pairs,
     fsort_sort_pairs_host,

@@ -38,6 +38,15 @@ class FsortPlanInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class FsortKernelTime(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pass_", ctypes.c_int32), ("active", ctypes.c_int32),
+                ("call", ctypes.c_int32), ("n", ctypes.c_uint64), ("ms", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+
+KERNEL_KINDS = {1: "histogram", 2: "scan", 3: "scatter", 4: "copy", 5: "leaf_hist", 6: "leaf_reduce",
+                7: "leaf_scan", 8: "expand"}
+
+
 def lib_path() -> str:
     return _LIB
 
@@ -64,6 +73,9 @@ def load_library():
             "fsort_exclusive_scan": ([vp, vp, u64, u64, vp, vp], st),
             "fsort_scatter_pass": ([vp, vp, vp, vp, vp, u64, i32, i32, i32, vp], st),
             "fsort_expand": ([vp, vp, vp, u64, i32, vp], st),
+            "fsort_plan_set_timing": ([vp, i32], st),
+            "fsort_plan_timing_report": ([vp, ctypes.POINTER(FsortKernelTime), ctypes.c_uint32,
+                                          ctypes.POINTER(ctypes.c_uint32)], st),
             "fsort_status_string": ([i32], ctypes.c_char_p),
             "fsort_version": ([], i32),
         }
@@ -205,6 +217,21 @@ def fsort_scatter_pass(plan, keys_in, vals_in, keys_out, vals_out, shift: int, w
 def fsort_expand(plan, counts, keys_out, n=None, key_bits=16, stream=None) -> None:
     _check(load_library().fsort_expand(plan, _ptr(counts), _ptr(keys_out), _numel(keys_out, n), key_bits,
                                        _stream(stream)), "fsort_expand")
+
+
+def fsort_plan_set_timing(plan, enable: bool) -> None:
+    _check(load_library().fsort_plan_set_timing(plan, int(bool(enable))), "fsort_plan_set_timing")
+
+
+def fsort_plan_timing_report(plan, capacity: int = 8192) -> list:
+    """Per-launch device times of the calls recorded since timing was enabled
+    (or last reported), as dicts."""
+    buf = (FsortKernelTime * capacity)()
+    count = ctypes.c_uint32()
+    _check(load_library().fsort_plan_timing_report(plan, buf, capacity, ctypes.byref(count)),
+           "fsort_plan_timing_report")
+    return [{"kind": KERNEL_KINDS.get(r.kind, r.kind), "pass": r.pass_, "active": bool(r.active), "call": r.call,
+             "n": r.n, "ms": r.ms} for r in buf[:count.value]]
 
 
 def fsort_status_string(status: int) -> str:

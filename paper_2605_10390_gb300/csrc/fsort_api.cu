@@ -7,12 +7,36 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/fsort.h"
 #include "fsort_dev.cuh"
 #include "fsort_internal.h"
 
 using namespace fsort;
+
+namespace {
+
+// Per-kernel timing: events recorded around launches, reported on demand.
+struct TimingRec {
+  int32_t kind, pass, call, slot;
+  uint64_t n;
+  int32_t ev0, ev1;
+};
+
+struct Timing {
+  static constexpr int kEvents = 8192;
+  static constexpr int kSlots = 2048;
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  int next_ev = 0;
+  fsort::Schedule* h_sched = nullptr;  // pinned copies of the device schedule, one per recorded call
+  int next_slot = 0;
+  int calls = 0;
+  std::vector<TimingRec> recs;
+};
+
+}  // namespace
 
 struct fsort_plan {
   int device = 0;
@@ -44,6 +68,8 @@ struct fsort_plan {
   uint32_t* h_status = nullptr;  // pinned copy of *status
   cudaEvent_t done = nullptr;
   bool pending = false;
+
+  Timing timing;
 };
 
 namespace {
@@ -123,6 +149,39 @@ bool overlaps(const void* a, size_t an, const void* b, size_t bn) {
   return x < y + bn && y < x + an;
 }
 
+// Records the device time of each launch of one call when timing is on.
+class CallTimer {
+ public:
+  CallTimer(fsort_plan* p, uint64_t n, cudaStream_t s, bool has_schedule) : p_(p), n_(n), s_(s) {
+    Timing& t = p->timing;
+    if (!t.on || t.next_ev + 40 > Timing::kEvents || t.next_slot >= Timing::kSlots) return;
+    on_ = true;
+    call_ = t.calls++;
+    slot_ = has_schedule ? t.next_slot++ : -1;
+    prev_ = t.next_ev++;
+    cudaEventRecord(t.ev[prev_], s_);
+  }
+  void mark(int kind, int pass) {
+    if (!on_) return;
+    Timing& t = p_->timing;
+    const int e = t.next_ev++;
+    cudaEventRecord(t.ev[e], s_);
+    t.recs.push_back(TimingRec{kind, pass, call_, slot_, n_, prev_, e});
+    prev_ = e;
+  }
+  void finish() {
+    if (on_ && slot_ >= 0)
+      cudaMemcpyAsync(&p_->timing.h_sched[slot_], p_->sched, sizeof(Schedule), cudaMemcpyDeviceToHost, s_);
+  }
+
+ private:
+  fsort_plan* p_;
+  uint64_t n_;
+  cudaStream_t s_;
+  bool on_ = false;
+  int call_ = -1, slot_ = -1, prev_ = -1;
+};
+
 // The whole sort, keys_in -> keys_out (equal pointers: in place).
 fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* vals_in, void* keys_out,
                           uint32_t* vals_out, uint64_t n, int key_bits, int precision_bits, cudaStream_t s) {
@@ -131,21 +190,29 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
   cudaError_t e = cudaSuccess;
   if (use_expand(key_bits, precision_bits, has_vals)) {
     // Expand path: the 65,536-bin histogram is the whole sorted multiset.
+    CallTimer tm(p, n, s, false);
     e = launch_leaf_histogram(static_cast<const uint16_t*>(keys_in), n, p->leaf_part, p->leaf_spill, p->sms, s);
+    tm.mark(FSORT_KERNEL_LEAF_HIST, -1);
     if (e == cudaSuccess) e = launch_leaf_reduce(p->leaf_part, p->leaf_spill, leaf_hist_grid(p->sms), p->leaf_counts, s);
+    tm.mark(FSORT_KERNEL_LEAF_REDUCE, -1);
     if (e == cudaSuccess) e = launch_scan_rows(p->leaf_counts, p->leaf_off, 1, 65536, s);
+    tm.mark(FSORT_KERNEL_LEAF_SCAN, -1);
     if (e == cudaSuccess) e = launch_expand(p->leaf_off, static_cast<uint16_t*>(keys_out), n, s);
+    tm.mark(FSORT_KERNEL_EXPAND, -1);
     if (e != cudaSuccess) return from_cuda(e);
     return finish_call(p, s);
   }
+  CallTimer tm(p, n, s, true);
   const DigitPlan plan = make_plan(key_bits, precision_bits, p->digit_bits);
   const uint64_t tiles = (n + p->tile - 1) / p->tile;
   const uint64_t chunks = (n + p->chunk_keys - 1) / p->chunk_keys;
   const uint64_t clear_words = kCounterBytes / 4 + tiles * kRadix;
   e = launch_histogram(keys_in, key_bits, n, p->chunk_keys, plan, p->hist, chunks * kRadix, kRadix, p->counters,
                        clear_words, p->sms, s);
+  tm.mark(FSORT_KERNEL_HISTOGRAM, -1);
   if (e == cudaSuccess)
     e = launch_scan_schedule(p->hist, p->bases, plan.passes, uint32_t(chunks), in_place ? 1 : 0, p->sched, s);
+  tm.mark(FSORT_KERNEL_SCAN, -1);
   const void* kb[3] = {keys_in, p->alt_keys, keys_out};
   const uint32_t* vb[3] = {vals_in, p->alt_vals, vals_out};
   for (int j = 0; j < plan.passes && e == cudaSuccess; ++j) {
@@ -168,8 +235,11 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
     a.tiles_per_chunk = uint32_t(p->chunk_keys / p->tile);
     a.status = p->status;
     e = launch_onesweep(a, key_bits, has_vals, s);
+    tm.mark(FSORT_KERNEL_SCATTER, j);
   }
   if (e == cudaSuccess) e = launch_schedule_copy(kb, vb, key_bits, has_vals, n, p->sched, p->sms, s);
+  tm.mark(FSORT_KERNEL_COPY, -1);
+  tm.finish();
   if (e != cudaSuccess) return from_cuda(e);
   return finish_call(p, s);
 }
@@ -285,6 +355,7 @@ fsort_status fsort_plan_destroy(fsort_plan* plan) {
   if (plan->pending && cudaEventSynchronize(plan->done) != cudaSuccess) st = FSORT_ERR_CUDA;
   if (plan->done) cudaEventDestroy(plan->done);
   if (plan->h_status) cudaFreeHost(plan->h_status);
+  fsort_plan_set_timing(plan, 0);
   if (plan->ws && cudaFree(plan->ws) != cudaSuccess) st = FSORT_ERR_CUDA;
   delete plan;
   return st;
@@ -478,6 +549,67 @@ fsort_status fsort_expand(fsort_plan* plan, const uint64_t* counts, void* keys_o
   if (e == cudaSuccess) e = launch_expand(plan->leaf_off, static_cast<uint16_t*>(keys_out), n, s);
   if (e != cudaSuccess) return from_cuda(e);
   return finish_call(plan, s);
+}
+
+fsort_status fsort_plan_set_timing(fsort_plan* plan, int enable) {
+  if (!plan) return FSORT_ERR_INVALID_ARG;
+  Timing& t = plan->timing;
+  if (enable && !t.on) {
+    t.ev.assign(Timing::kEvents, nullptr);
+    for (auto& e : t.ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        fsort_plan_set_timing(plan, 0);
+        return FSORT_ERR_CUDA;
+      }
+    if (cudaMallocHost(reinterpret_cast<void**>(&t.h_sched), sizeof(Schedule) * Timing::kSlots) != cudaSuccess) {
+      t.h_sched = nullptr;
+      fsort_plan_set_timing(plan, 0);
+      return FSORT_ERR_OOM;
+    }
+    t.on = true;
+    t.next_ev = t.next_slot = t.calls = 0;
+    t.recs.clear();
+  } else if (!enable) {
+    if (!t.ev.empty()) cudaDeviceSynchronize();
+    for (auto& e : t.ev)
+      if (e) cudaEventDestroy(e);
+    t.ev.clear();
+    if (t.h_sched) cudaFreeHost(t.h_sched);
+    t.h_sched = nullptr;
+    t.on = false;
+    t.recs.clear();
+  }
+  return FSORT_OK;
+}
+
+fsort_status fsort_plan_timing_report(fsort_plan* plan, fsort_kernel_time* out, uint32_t capacity,
+                                      uint32_t* count) {
+  if (!plan || !count || (capacity && !out)) return FSORT_ERR_INVALID_ARG;
+  Timing& t = plan->timing;
+  *count = 0;
+  if (!t.on) return FSORT_ERR_INVALID_ARG;
+  if (!t.recs.empty() && cudaEventSynchronize(t.ev[t.recs.back().ev1]) != cudaSuccess) return FSORT_ERR_CUDA;
+  if (plan->pending && cudaEventSynchronize(plan->done) != cudaSuccess) return FSORT_ERR_CUDA;
+  uint32_t k = 0;
+  for (const TimingRec& r : t.recs) {
+    if (k >= capacity) break;
+    fsort_kernel_time& o = out[k++];
+    o.kind = r.kind;
+    o.pass = r.pass;
+    o.call = r.call;
+    o.n = r.n;
+    o.reserved = 0.f;
+    o.active = 1;
+    if (r.slot >= 0 && r.kind == FSORT_KERNEL_SCATTER) o.active = t.h_sched[r.slot].pass[r.pass].active;
+    if (r.slot >= 0 && r.kind == FSORT_KERNEL_COPY) o.active = t.h_sched[r.slot].copy.active;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.ev[r.ev0], t.ev[r.ev1]) != cudaSuccess) return FSORT_ERR_CUDA;
+    o.ms = ms;
+  }
+  *count = k;
+  t.recs.clear();
+  t.next_ev = t.next_slot = t.calls = 0;
+  return FSORT_OK;
 }
 
 const char* fsort_status_string(fsort_status status) {
