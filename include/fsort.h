@@ -194,6 +194,12 @@ FSORT_API fsort_status fsort_plan_set_timing(fsort_plan* plan, int enable);
 FSORT_API fsort_status fsort_plan_timing_report(fsort_plan* plan, fsort_kernel_time* out, uint32_t capacity,
                                                 uint32_t* count);
 
+/* Raw device flag bits behind the last FSORT_ERR_TIMEOUT / FSORT_ERR_INTERNAL
+ * this plan reported (0 if none): 1 look-back wait timed out, 2 bulk-copy wait
+ * timed out, 4 tile id beyond the grid, 8 look-back walk found no prefix at its
+ * chunk's first tile, 16 scatter target outside the output. */
+FSORT_API uint32_t fsort_plan_device_flags(const fsort_plan* plan);
+
 /* Human-readable name of a status code (static storage). */
 FSORT_API const char* fsort_status_string(fsort_status status);
 

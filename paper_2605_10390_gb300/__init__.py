@@ -23,6 +23,7 @@ from ._binding import (  # noqa: F401
     fsort_histogram,
     fsort_plan_create,
     fsort_plan_describe,
+    fsort_plan_device_flags,
     fsort_plan_destroy,
     fsort_plan_set_timing,
     fsort_plan_sync,

@@ -76,6 +76,7 @@ def load_library():
             "fsort_plan_set_timing": ([vp, i32], st),
             "fsort_plan_timing_report": ([vp, ctypes.POINTER(FsortKernelTime), ctypes.c_uint32,
                                           ctypes.POINTER(ctypes.c_uint32)], st),
+            "fsort_plan_device_flags": ([vp], ctypes.c_uint32),
             "fsort_status_string": ([i32], ctypes.c_char_p),
             "fsort_version": ([], i32),
         }
@@ -160,7 +161,14 @@ def fsort_plan_destroy(plan) -> None:
 
 
 def fsort_plan_sync(plan) -> None:
-    _check(load_library().fsort_plan_sync(plan), "fsort_plan_sync")
+    lib = load_library()
+    st = lib.fsort_plan_sync(plan)
+    if st != 0:
+        raise FsortError(st, f"fsort_plan_sync (device flags {lib.fsort_plan_device_flags(plan):#x})")
+
+
+def fsort_plan_device_flags(plan) -> int:
+    return int(load_library().fsort_plan_device_flags(plan))
 
 
 def fsort_plan_describe(plan, n: int, key_bits: int, precision_bits: int, has_values: bool) -> dict:

@@ -68,6 +68,7 @@ struct fsort_plan {
   uint32_t* h_status = nullptr;  // pinned copy of *status
   cudaEvent_t done = nullptr;
   bool pending = false;
+  uint32_t last_device_flags = 0;  // raw bits of the last latched device error
 
   Timing timing;
 };
@@ -120,6 +121,7 @@ fsort_status take_latched(fsort_plan* p, bool wait, cudaStream_t stream) {
   p->pending = false;
   const uint32_t s = *p->h_status;
   if (!s) return FSORT_OK;
+  p->last_device_flags = s;
   *p->h_status = 0;
   if (cudaMemsetAsync(p->status, 0, sizeof(uint32_t), stream) != cudaSuccess) return FSORT_ERR_CUDA;
   if (wait && cudaStreamSynchronize(stream) != cudaSuccess) return FSORT_ERR_CUDA;
@@ -626,6 +628,8 @@ const char* fsort_status_string(fsort_status status) {
     default: return "FSORT_UNKNOWN_STATUS";
   }
 }
+
+uint32_t fsort_plan_device_flags(const fsort_plan* plan) { return plan ? plan->last_device_flags : 0u; }
 
 int fsort_version(void) { return 100; }
 

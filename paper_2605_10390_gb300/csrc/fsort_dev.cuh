@@ -11,7 +11,9 @@ namespace fsort {
 // ---- device status word bits (latched, read by the host) -------------------
 constexpr uint32_t kDevTimeoutLookback = 1u;  // a look-back wait gave up
 constexpr uint32_t kDevTimeoutLoad = 2u;      // a bulk-copy wait gave up
-constexpr uint32_t kDevBadPlan = 4u;          // a kernel saw an impossible descriptor
+constexpr uint32_t kDevBadTile = 4u;          // a dynamic tile id beyond the grid (counter not reset)
+constexpr uint32_t kDevBadLookback = 8u;      // a look-back walk reached its chunk's first tile without a prefix
+constexpr uint32_t kDevBadOutput = 16u;       // a scatter target fell outside the output (only after a timeout)
 
 // Bounded waits give up after this many nanoseconds of %globaltimer.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;

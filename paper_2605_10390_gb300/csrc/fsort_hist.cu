@@ -26,15 +26,16 @@ constexpr int kRadix = 256;
 // the global 64-bit histogram with one atomic per non-zero counter.
 constexpr int kHistThreads = 512;
 
-template <typename K>
+// P = number of passes (compile time, so the per-key loop is exactly P
+// digit extractions and P shared-memory reductions).
+template <typename K, int P>
 __global__ void __launch_bounds__(kHistThreads) hist_kernel(const K* __restrict__ keys, uint64_t n,
                                                             uint64_t chunk_keys, DigitPlan plan,
                                                             uint64_t* __restrict__ hist, uint64_t pass_stride,
                                                             uint64_t chunk_stride, uint32_t* clear,
                                                             uint64_t clear_words) {
-  __shared__ uint32_t counts[kMaxPasses * kRadix];
-  const int passes = plan.passes;
-  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) counts[i] = 0;
+  __shared__ uint32_t counts[P * kRadix];
+  for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) counts[i] = 0;
 
   // Clear the first pass's look-back region and the tile counters.
   {
@@ -54,24 +55,36 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const K* __restrict_
   const uint64_t v_lo = blockIdx.x * per;
   const uint64_t v_hi = (v_lo + per < c_vecs) ? v_lo + per : c_vecs;
 
-  uint32_t shift[kMaxPasses], mask[kMaxPasses];
+  uint32_t shift[P], mask[P];
 #pragma unroll
-  for (int j = 0; j < kMaxPasses; ++j) {
+  for (int j = 0; j < P; ++j) {
     shift[j] = plan.shift[j];
     mask[j] = plan.mask[j];
   }
 
   auto count_key = [&](K k) {
 #pragma unroll
-    for (int j = 0; j < kMaxPasses; ++j) {
-      if (j < passes) {
-        const uint32_t d = uint32_t(uint64_t(k) >> shift[j]) & mask[j];
-        atomicAdd(&counts[j * kRadix + d], 1u);
-      }
+    for (int j = 0; j < P; ++j) {
+      const uint32_t d = (sizeof(K) <= 4 ? (uint32_t(k) >> shift[j]) : uint32_t(uint64_t(k) >> shift[j])) & mask[j];
+      atomicAdd(&counts[j * kRadix + d], 1u);
     }
   };
 
-  for (uint64_t v = v_lo + threadIdx.x; v < v_hi; v += blockDim.x) {
+  // Two 16-byte loads in flight per thread per iteration.
+  uint64_t v = v_lo + threadIdx.x;
+  for (; v + blockDim.x < v_hi; v += 2 * blockDim.x) {
+    const uint64_t e0 = c_lo + v * kVec, e1 = e0 + uint64_t(blockDim.x) * kVec;
+    if (e1 + kVec > c_hi) break;
+    const uint4 q0 = __ldg(reinterpret_cast<const uint4*>(keys + e0));
+    const uint4 q1 = __ldg(reinterpret_cast<const uint4*>(keys + e1));
+    const K* k0 = reinterpret_cast<const K*>(&q0);
+    const K* k1 = reinterpret_cast<const K*>(&q1);
+#pragma unroll
+    for (int e = 0; e < int(kVec); ++e) count_key(k0[e]);
+#pragma unroll
+    for (int e = 0; e < int(kVec); ++e) count_key(k1[e]);
+  }
+  for (; v < v_hi; v += blockDim.x) {
     const uint64_t e0 = c_lo + v * kVec;
     if (e0 + kVec <= c_hi) {
       const uint4 q = __ldg(reinterpret_cast<const uint4*>(keys + e0));
@@ -83,7 +96,7 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const K* __restrict_
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+  for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) {
     const uint32_t c = counts[i];
     if (c) {
       const int j = i / kRadix, d = i % kRadix;
@@ -374,37 +387,59 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(const uint64_t* 
 
 // ------------------------------------------------------------ launchers ----
 
+template <typename K, int P>
+void launch_hist_typed(dim3 grid, cudaStream_t stream, const void* keys, uint64_t n, uint64_t chunk_keys,
+                       const DigitPlan& plan, uint64_t* hist, uint64_t pass_stride, uint64_t chunk_stride,
+                       uint32_t* clear, uint64_t clear_words) {
+  hist_kernel<K, P><<<grid, kHistThreads, 0, stream>>>(static_cast<const K*>(keys), n, chunk_keys, plan, hist,
+                                                       pass_stride, chunk_stride, clear, clear_words);
+}
+
+template <typename K>
+cudaError_t launch_hist_passes(dim3 grid, cudaStream_t stream, const void* keys, uint64_t n, uint64_t chunk_keys,
+                               const DigitPlan& plan, uint64_t* hist, uint64_t pass_stride, uint64_t chunk_stride,
+                               uint32_t* clear, uint64_t clear_words) {
+#define FSORT_HIST_CASE(P_)                                                                                  \
+  case P_:                                                                                                   \
+    launch_hist_typed<K, P_>(grid, stream, keys, n, chunk_keys, plan, hist, pass_stride, chunk_stride, clear, \
+                             clear_words);                                                                   \
+    break;
+  switch (plan.passes) {
+    FSORT_HIST_CASE(1)
+    FSORT_HIST_CASE(2)
+    FSORT_HIST_CASE(3)
+    FSORT_HIST_CASE(4)
+    FSORT_HIST_CASE(5)
+    FSORT_HIST_CASE(6)
+    FSORT_HIST_CASE(7)
+    FSORT_HIST_CASE(8)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef FSORT_HIST_CASE
+  return cudaGetLastError();
+}
+
 cudaError_t launch_histogram(const void* keys, int key_bits, uint64_t n, uint64_t chunk_keys, const DigitPlan& plan,
                              uint64_t* hist, uint64_t pass_stride, uint64_t chunk_stride, uint32_t* clear,
                              uint64_t clear_words, int sms, cudaStream_t stream) {
   const uint64_t chunks = n ? (n + chunk_keys - 1) / chunk_keys : 1;
-  // About two resident CTAs per SM over all chunks.
-  uint64_t per_chunk = (uint64_t(sms) * 2 + chunks - 1) / chunks;
-  if (per_chunk < 1) per_chunk = 1;
+  // About four resident CTAs per SM over all chunks.
+  uint64_t per_chunk = (uint64_t(sms) * 4 + chunks - 1) / chunks;
   const uint64_t keys_per_chunk = n < chunk_keys ? n : chunk_keys;
   const uint64_t max_useful = (keys_per_chunk + 8 * kHistThreads - 1) / (8 * kHistThreads);
-  if (per_chunk > max_useful && max_useful > 0) per_chunk = max_useful;
+  if (per_chunk > max_useful) per_chunk = max_useful;
+  if (per_chunk < 1) per_chunk = 1;
   const dim3 grid{unsigned(per_chunk), unsigned(chunks), 1u};
   switch (key_bits) {
-    case 16:
-      hist_kernel<uint16_t><<<grid, kHistThreads, 0, stream>>>(static_cast<const uint16_t*>(keys), n, chunk_keys,
-                                                               plan, hist, pass_stride, chunk_stride, clear,
-                                                               clear_words);
-      break;
-    case 32:
-      hist_kernel<uint32_t><<<grid, kHistThreads, 0, stream>>>(static_cast<const uint32_t*>(keys), n, chunk_keys,
-                                                               plan, hist, pass_stride, chunk_stride, clear,
-                                                               clear_words);
-      break;
-    case 64:
-      hist_kernel<uint64_t><<<grid, kHistThreads, 0, stream>>>(static_cast<const uint64_t*>(keys), n, chunk_keys,
-                                                               plan, hist, pass_stride, chunk_stride, clear,
-                                                               clear_words);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+    case 16: return launch_hist_passes<uint16_t>(grid, stream, keys, n, chunk_keys, plan, hist, pass_stride,
+                                                 chunk_stride, clear, clear_words);
+    case 32: return launch_hist_passes<uint32_t>(grid, stream, keys, n, chunk_keys, plan, hist, pass_stride,
+                                                 chunk_stride, clear, clear_words);
+    case 64: return launch_hist_passes<uint64_t>(grid, stream, keys, n, chunk_keys, plan, hist, pass_stride,
+                                                 chunk_stride, clear, clear_words);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_scan_schedule(uint64_t* hist, uint64_t* bases, int passes, uint32_t chunks, int in_place,

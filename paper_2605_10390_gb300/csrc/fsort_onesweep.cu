@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const OnesweepArgs a) 
 
   const uint32_t tile = *s_tile;
   if (tile >= gridDim.x) {  // counter not reset: never index past the look-back region
-    if (tid == 0) atomicOr(a.status, kDevBadPlan);
+    if (tid == 0) atomicOr(a.status, kDevBadTile);
     return;
   }
   const uint64_t t0 = uint64_t(tile) * kTile;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const OnesweepArgs a) 
         excl += w & kCountMask;
         if (flag == kFlagPrefix) break;
         if (t == chunk_first) {  // a chunk's first tile always publishes a prefix
-          atomicOr(a.status, kDevBadPlan);
+          atomicOr(a.status, kDevBadLookback);
           break;
         }
         --t;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const OnesweepArgs a) 
     kout[o] = k;
     if (kVals) vout[o] = s_vals[s];
   }
-  if (out_of_range) atomicOr(a.status, kDevBadPlan);
+  if (out_of_range) atomicOr(a.status, kDevBadOutput);
 }
 
 template <typename K, bool kVals>
