@@ -54,8 +54,9 @@ struct fsort_plan {
   uint32_t* alt_vals = nullptr;
   uint32_t* counters = nullptr;  // [2] tile counters, directly followed by look-back region 0
   uint32_t* lookback[2] = {nullptr, nullptr};
-  uint64_t* hist = nullptr;      // [kMaxPasses][max_chunks][256], all zero between calls
-  uint64_t* bases = nullptr;     // same shape
+  uint64_t* hist = nullptr;       // [kMaxPasses][256], all zero between calls
+  uint64_t* chunk_base = nullptr; // [kMaxPasses][max_chunks][256]
+  uint32_t* chunk_flag = nullptr; // [kMaxPasses][max_chunks]
   Schedule* sched = nullptr;
   uint32_t* status = nullptr;    // sticky device error bits
   uint32_t* leaf_part = nullptr; // expand path (16-bit keys)
@@ -209,11 +210,11 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
   const uint64_t tiles = (n + p->tile - 1) / p->tile;
   const uint64_t chunks = (n + p->chunk_keys - 1) / p->chunk_keys;
   const uint64_t clear_words = kCounterBytes / 4 + tiles * kRadix;
-  e = launch_histogram(keys_in, key_bits, n, p->chunk_keys, plan, p->hist, chunks * kRadix, kRadix, p->counters,
-                       clear_words, p->sms, s);
+  e = launch_histogram(keys_in, key_bits, n, plan, p->hist, kRadix, p->counters, clear_words, p->sms, s);
   tm.mark(FSORT_KERNEL_HISTOGRAM, -1);
   if (e == cudaSuccess)
-    e = launch_scan_schedule(p->hist, p->bases, plan.passes, uint32_t(chunks), in_place ? 1 : 0, p->sched, s);
+    e = launch_scan_schedule(p->hist, p->chunk_base, p->chunk_flag, plan.passes, uint32_t(chunks),
+                             in_place ? 1 : 0, p->sched, s);
   tm.mark(FSORT_KERNEL_SCAN, -1);
   const void* kb[3] = {keys_in, p->alt_keys, keys_out};
   const uint32_t* vb[3] = {vals_in, p->alt_vals, vals_out};
@@ -231,7 +232,8 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
     const bool last = (j + 1 == plan.passes);
     a.next_lookback = last ? nullptr : p->lookback[(j + 1) & 1];
     a.next_counter = last ? nullptr : p->counters + ((j + 1) & 1);
-    a.bases = p->bases + uint64_t(j) * chunks * kRadix;
+    a.chunk_base = p->chunk_base + uint64_t(j) * chunks * kRadix;
+    a.chunk_flag = p->chunk_flag + uint64_t(j) * chunks;
     a.sched = p->sched;
     a.pass = j;
     a.tiles_per_chunk = uint32_t(p->chunk_keys / p->tile);
@@ -285,9 +287,10 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   const size_t o_alt_v = desc->has_values ? take(n * 4) : 0;
   const size_t o_cnt = take(kCounterBytes + p->max_tiles * kRadix * 4);  // counters + region 0
   const size_t o_lb1 = take(p->max_tiles * kRadix * 4);
-  const size_t hist_bytes = size_t(kMaxPasses) * p->max_chunks * kRadix * 8;
+  const size_t hist_bytes = size_t(kMaxPasses) * kRadix * 8;
   const size_t o_hist = take(hist_bytes);
-  const size_t o_bases = take(hist_bytes);
+  const size_t o_cbase = take(size_t(kMaxPasses) * p->max_chunks * kRadix * 8);
+  const size_t o_cflag = take(size_t(kMaxPasses) * p->max_chunks * 4);
   const size_t o_sched = take(sizeof(Schedule));
   const size_t o_status = take(sizeof(uint32_t));
   size_t o_lpart = 0, o_lspill = 0, o_lcnt = 0, o_loff = 0;
@@ -318,7 +321,8 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   p->lookback[0] = reinterpret_cast<uint32_t*>(w + o_cnt + kCounterBytes);
   p->lookback[1] = reinterpret_cast<uint32_t*>(w + o_lb1);
   p->hist = reinterpret_cast<uint64_t*>(w + o_hist);
-  p->bases = reinterpret_cast<uint64_t*>(w + o_bases);
+  p->chunk_base = reinterpret_cast<uint64_t*>(w + o_cbase);
+  p->chunk_flag = reinterpret_cast<uint32_t*>(w + o_cflag);
   p->sched = reinterpret_cast<Schedule*>(w + o_sched);
   p->status = reinterpret_cast<uint32_t*>(w + o_status);
   if (leaf) {
@@ -467,8 +471,7 @@ fsort_status fsort_histogram(fsort_plan* plan, const void* keys, uint64_t n, int
     const DigitPlan dp = make_plan(key_bits, precision_bits, digit_bits);
     e = cudaMemsetAsync(counts_out, 0, sizeof(uint64_t) * dp.passes * (1u << digit_bits), s);
     if (e == cudaSuccess && n)
-      e = launch_histogram(keys, key_bits, n, plan->chunk_keys, dp, counts_out, uint64_t(1) << digit_bits, 0,
-                           nullptr, 0, plan->sms, s);
+      e = launch_histogram(keys, key_bits, n, dp, counts_out, uint64_t(1) << digit_bits, nullptr, 0, plan->sms, s);
   }
   if (e != cudaSuccess) return from_cuda(e);
   return finish_call(plan, s);
@@ -508,9 +511,10 @@ fsort_status fsort_scatter_pass(fsort_plan* plan, const void* keys_in, const uin
   dp.mask[0] = (1u << width) - 1u;
   const uint64_t tiles = (n + plan->tile - 1) / plan->tile;
   const uint64_t chunks = (n + plan->chunk_keys - 1) / plan->chunk_keys;
-  cudaError_t e = launch_histogram(keys_in, key_bits, n, plan->chunk_keys, dp, plan->hist, chunks * kRadix, kRadix,
-                                   plan->counters, kCounterBytes / 4 + tiles * kRadix, plan->sms, s);
-  if (e == cudaSuccess) e = launch_scan_schedule(plan->hist, plan->bases, 1, uint32_t(chunks), 0, nullptr, s);
+  cudaError_t e = launch_histogram(keys_in, key_bits, n, dp, plan->hist, kRadix, plan->counters,
+                                   kCounterBytes / 4 + tiles * kRadix, plan->sms, s);
+  if (e == cudaSuccess)
+    e = launch_scan_schedule(plan->hist, plan->chunk_base, plan->chunk_flag, 1, uint32_t(chunks), 0, nullptr, s);
   if (e == cudaSuccess) {
     OnesweepArgs a{};
     a.keys[0] = keys_in;
@@ -526,7 +530,8 @@ fsort_status fsort_scatter_pass(fsort_plan* plan, const void* keys_in, const uin
     a.tile_counter = plan->counters;
     a.next_lookback = nullptr;
     a.next_counter = nullptr;
-    a.bases = plan->bases;
+    a.chunk_base = plan->chunk_base;
+    a.chunk_flag = plan->chunk_flag;
     a.sched = nullptr;
     a.pass = 0;
     a.tiles_per_chunk = uint32_t(plan->chunk_keys / plan->tile);

@@ -5,7 +5,7 @@
 //  K1' leaf_hist_kernel   the 65,536-bin histogram of 16-bit keys with 16-bit
 //                          tapered counters and exact overflow spills (Sec. III-D-1)
 //  K2  scan_schedule      exclusive scan per pass (Alg. 3's rank of every leaf),
-//                          chunk bases, and the device-side pass schedule
+//                          the first look-back chunk's bases, the device-side pass schedule
 //  K4  expand_kernel      Alg. 5 without trailing bits: key v written C[v] times
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -19,8 +19,8 @@ namespace {
 constexpr int kRadix = 256;
 
 // ---------------------------------------------------------------- K1 -------
-// Every CTA owns a slice of one look-back chunk and keeps one shared-memory
-// counter per (pass, digit).  Counts are added with shared-memory reductions
+// Every CTA owns a slice of the keys and keeps one shared-memory counter per
+// (pass, digit).  Counts are added with shared-memory reductions
 // (red.shared.add: same-address adds from a warp are combined by the
 // hardware, so skewed inputs cost no more than uniform ones), then merged into
 // the global 64-bit histogram with one atomic per non-zero counter.
@@ -29,31 +29,27 @@ constexpr int kHistThreads = 512;
 // P = number of passes (compile time, so the per-key loop is exactly P
 // digit extractions and P shared-memory reductions).
 template <typename K, int P>
-__global__ void __launch_bounds__(kHistThreads) hist_kernel(const K* __restrict__ keys, uint64_t n,
-                                                            uint64_t chunk_keys, DigitPlan plan,
+__global__ void __launch_bounds__(kHistThreads) hist_kernel(const K* __restrict__ keys, uint64_t n, DigitPlan plan,
                                                             uint64_t* __restrict__ hist, uint64_t pass_stride,
-                                                            uint64_t chunk_stride, uint32_t* clear,
-                                                            uint64_t clear_words) {
+                                                            uint32_t* clear, uint64_t clear_words) {
   __shared__ uint32_t counts[P * kRadix];
   for (int i = threadIdx.x; i < P * kRadix; i += blockDim.x) counts[i] = 0;
 
   // Clear the first pass's look-back region and the tile counters.
   {
-    const uint64_t stride = uint64_t(gridDim.x) * gridDim.y * blockDim.x;
-    const uint64_t first = (uint64_t(blockIdx.y) * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t first = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     for (uint64_t i = first; i < clear_words; i += stride) clear[i] = 0;
   }
   __syncthreads();
 
-  const uint64_t chunk = blockIdx.y;
-  const uint64_t c_lo = chunk * chunk_keys;
-  const uint64_t c_hi = (c_lo + chunk_keys < n) ? c_lo + chunk_keys : n;
-  // Slice of the chunk for this CTA, in whole 16-byte vectors.
+  // Slice of the input for this CTA, in whole 16-byte vectors.  A CTA counts
+  // fewer than 2^32 keys (n <= 2^36, >= 16 CTAs), so 32-bit counters suffice.
   constexpr uint64_t kVec = 16 / sizeof(K);
-  const uint64_t c_vecs = (c_hi - c_lo + kVec - 1) / kVec;
-  const uint64_t per = (c_vecs + gridDim.x - 1) / gridDim.x;
+  const uint64_t vecs = (n + kVec - 1) / kVec;
+  const uint64_t per = (vecs + gridDim.x - 1) / gridDim.x;
   const uint64_t v_lo = blockIdx.x * per;
-  const uint64_t v_hi = (v_lo + per < c_vecs) ? v_lo + per : c_vecs;
+  const uint64_t v_hi = (v_lo + per < vecs) ? v_lo + per : vecs;
 
   uint32_t shift[P], mask[P];
 #pragma unroll
@@ -73,8 +69,8 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const K* __restrict_
   // Two 16-byte loads in flight per thread per iteration.
   uint64_t v = v_lo + threadIdx.x;
   for (; v + blockDim.x < v_hi; v += 2 * blockDim.x) {
-    const uint64_t e0 = c_lo + v * kVec, e1 = e0 + uint64_t(blockDim.x) * kVec;
-    if (e1 + kVec > c_hi) break;
+    const uint64_t e0 = v * kVec, e1 = e0 + uint64_t(blockDim.x) * kVec;
+    if (e1 + kVec > n) break;
     const uint4 q0 = __ldg(reinterpret_cast<const uint4*>(keys + e0));
     const uint4 q1 = __ldg(reinterpret_cast<const uint4*>(keys + e1));
     const K* k0 = reinterpret_cast<const K*>(&q0);
@@ -85,14 +81,14 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const K* __restrict_
     for (int e = 0; e < int(kVec); ++e) count_key(k1[e]);
   }
   for (; v < v_hi; v += blockDim.x) {
-    const uint64_t e0 = c_lo + v * kVec;
-    if (e0 + kVec <= c_hi) {
+    const uint64_t e0 = v * kVec;
+    if (e0 + kVec <= n) {
       const uint4 q = __ldg(reinterpret_cast<const uint4*>(keys + e0));
       const K* kk = reinterpret_cast<const K*>(&q);
 #pragma unroll
       for (int e = 0; e < int(kVec); ++e) count_key(kk[e]);
     } else {
-      for (uint64_t e = e0; e < c_hi; ++e) count_key(keys[e]);
+      for (uint64_t e = e0; e < n; ++e) count_key(keys[e]);
     }
   }
   __syncthreads();
@@ -100,17 +96,17 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const K* __restrict_
     const uint32_t c = counts[i];
     if (c) {
       const int j = i / kRadix, d = i % kRadix;
-      atomicAdd(reinterpret_cast<unsigned long long*>(&hist[j * pass_stride + chunk * chunk_stride + d]),
-                (unsigned long long)c);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&hist[j * pass_stride + d]), (unsigned long long)c);
     }
   }
 }
 
 // ---------------------------------------------------------------- K2 -------
-// 256 threads, thread d owns digit d.  For each pass: the digit's total over
-// all chunks, a block-wide exclusive scan over digits (the rank of every leaf,
-// Alg. 3), then running sums over chunks give each (chunk, digit) its 64-bit
-// base.  A pass whose keys all share one digit is trivial (its stable scatter
+// 256 threads, thread d owns digit d.  For each pass: a block-wide exclusive
+// scan over the digit totals (the rank of every leaf, Alg. 3) gives the 64-bit
+// bases of the first look-back chunk; the scatter itself chains the bases of
+// later chunks, whose key sets are only known once the previous pass has
+// permuted the keys.  A pass whose keys all share one digit is trivial (its stable scatter
 // is the identity) and is marked inactive.  Thread 0 then routes the active
 // passes through the input, scratch and output buffers so that the last one
 // writes the output, adding a final copy only when no assignment can.
@@ -135,26 +131,22 @@ __device__ uint64_t block_exclusive_scan_256(uint64_t x, uint64_t* s_warp, uint6
 }
 
 __global__ void __launch_bounds__(kRadix) scan_schedule_kernel(uint64_t* __restrict__ hist,
-                                                               uint64_t* __restrict__ bases, int passes,
+                                                               uint64_t* __restrict__ chunk_base,
+                                                               uint32_t* __restrict__ chunk_flag, int passes,
                                                                uint32_t chunks, int in_place, Schedule* sched) {
   __shared__ uint64_t s_warp[8];
   __shared__ int s_trivial[kMaxPasses];
   const int d = threadIdx.x;
   for (int j = 0; j < passes; ++j) {
-    uint64_t* h = hist + uint64_t(j) * chunks * kRadix;
-    uint64_t tot = 0;
-    for (uint32_t c = 0; c < chunks; ++c) tot += h[uint64_t(c) * kRadix + d];
+    uint64_t* h = hist + uint64_t(j) * kRadix;
+    const uint64_t tot = h[d];
+    h[d] = 0;  // leave the accumulator zero for the next call
     uint64_t all;
     const uint64_t excl = block_exclusive_scan_256(tot, s_warp, &all);
     const int nonzero = __syncthreads_count(tot != 0);
     if (d == 0) s_trivial[j] = (nonzero <= 1);
-    uint64_t run = excl;
-    uint64_t* b = bases + uint64_t(j) * chunks * kRadix;
-    for (uint32_t c = 0; c < chunks; ++c) {
-      b[uint64_t(c) * kRadix + d] = run;
-      run += h[uint64_t(c) * kRadix + d];
-      h[uint64_t(c) * kRadix + d] = 0;  // leave the accumulator zero for the next call
-    }
+    chunk_base[uint64_t(j) * chunks * kRadix + d] = excl;
+    for (uint32_t c = d; c < chunks; c += kRadix) chunk_flag[uint64_t(j) * chunks + c] = 0;
   }
   __syncthreads();
   if (d == 0 && sched) {
@@ -388,21 +380,19 @@ __global__ void __launch_bounds__(kExpandThreads) expand_kernel(const uint64_t* 
 // ------------------------------------------------------------ launchers ----
 
 template <typename K, int P>
-void launch_hist_typed(dim3 grid, cudaStream_t stream, const void* keys, uint64_t n, uint64_t chunk_keys,
-                       const DigitPlan& plan, uint64_t* hist, uint64_t pass_stride, uint64_t chunk_stride,
-                       uint32_t* clear, uint64_t clear_words) {
-  hist_kernel<K, P><<<grid, kHistThreads, 0, stream>>>(static_cast<const K*>(keys), n, chunk_keys, plan, hist,
-                                                       pass_stride, chunk_stride, clear, clear_words);
+void launch_hist_typed(unsigned grid, cudaStream_t stream, const void* keys, uint64_t n, const DigitPlan& plan,
+                       uint64_t* hist, uint64_t pass_stride, uint32_t* clear, uint64_t clear_words) {
+  hist_kernel<K, P><<<grid, kHistThreads, 0, stream>>>(static_cast<const K*>(keys), n, plan, hist, pass_stride,
+                                                       clear, clear_words);
 }
 
 template <typename K>
-cudaError_t launch_hist_passes(dim3 grid, cudaStream_t stream, const void* keys, uint64_t n, uint64_t chunk_keys,
-                               const DigitPlan& plan, uint64_t* hist, uint64_t pass_stride, uint64_t chunk_stride,
-                               uint32_t* clear, uint64_t clear_words) {
-#define FSORT_HIST_CASE(P_)                                                                                  \
-  case P_:                                                                                                   \
-    launch_hist_typed<K, P_>(grid, stream, keys, n, chunk_keys, plan, hist, pass_stride, chunk_stride, clear, \
-                             clear_words);                                                                   \
+cudaError_t launch_hist_passes(unsigned grid, cudaStream_t stream, const void* keys, uint64_t n,
+                               const DigitPlan& plan, uint64_t* hist, uint64_t pass_stride, uint32_t* clear,
+                               uint64_t clear_words) {
+#define FSORT_HIST_CASE(P_)                                                                          \
+  case P_:                                                                                           \
+    launch_hist_typed<K, P_>(grid, stream, keys, n, plan, hist, pass_stride, clear, clear_words); \
     break;
   switch (plan.passes) {
     FSORT_HIST_CASE(1)
@@ -420,31 +410,28 @@ cudaError_t launch_hist_passes(dim3 grid, cudaStream_t stream, const void* keys,
   return cudaGetLastError();
 }
 
-cudaError_t launch_histogram(const void* keys, int key_bits, uint64_t n, uint64_t chunk_keys, const DigitPlan& plan,
-                             uint64_t* hist, uint64_t pass_stride, uint64_t chunk_stride, uint32_t* clear,
-                             uint64_t clear_words, int sms, cudaStream_t stream) {
-  const uint64_t chunks = n ? (n + chunk_keys - 1) / chunk_keys : 1;
-  // About four resident CTAs per SM over all chunks.
-  uint64_t per_chunk = (uint64_t(sms) * 4 + chunks - 1) / chunks;
-  const uint64_t keys_per_chunk = n < chunk_keys ? n : chunk_keys;
-  const uint64_t max_useful = (keys_per_chunk + 8 * kHistThreads - 1) / (8 * kHistThreads);
-  if (per_chunk > max_useful) per_chunk = max_useful;
-  if (per_chunk < 1) per_chunk = 1;
-  const dim3 grid{unsigned(per_chunk), unsigned(chunks), 1u};
+cudaError_t launch_histogram(const void* keys, int key_bits, uint64_t n, const DigitPlan& plan, uint64_t* hist,
+                             uint64_t pass_stride, uint32_t* clear, uint64_t clear_words, int sms,
+                             cudaStream_t stream) {
+  // About four resident CTAs per SM, at least 4096 keys each, at least 16 CTAs.
+  uint64_t grid = uint64_t(sms) * 4;
+  const uint64_t useful = (n + 8 * kHistThreads - 1) / (8 * kHistThreads);
+  if (grid > useful) grid = useful;
+  if (grid < 16) grid = 16;
   switch (key_bits) {
-    case 16: return launch_hist_passes<uint16_t>(grid, stream, keys, n, chunk_keys, plan, hist, pass_stride,
-                                                 chunk_stride, clear, clear_words);
-    case 32: return launch_hist_passes<uint32_t>(grid, stream, keys, n, chunk_keys, plan, hist, pass_stride,
-                                                 chunk_stride, clear, clear_words);
-    case 64: return launch_hist_passes<uint64_t>(grid, stream, keys, n, chunk_keys, plan, hist, pass_stride,
-                                                 chunk_stride, clear, clear_words);
+    case 16: return launch_hist_passes<uint16_t>(unsigned(grid), stream, keys, n, plan, hist, pass_stride, clear,
+                                                 clear_words);
+    case 32: return launch_hist_passes<uint32_t>(unsigned(grid), stream, keys, n, plan, hist, pass_stride, clear,
+                                                 clear_words);
+    case 64: return launch_hist_passes<uint64_t>(unsigned(grid), stream, keys, n, plan, hist, pass_stride, clear,
+                                                 clear_words);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_scan_schedule(uint64_t* hist, uint64_t* bases, int passes, uint32_t chunks, int in_place,
-                                 Schedule* sched, cudaStream_t stream) {
-  scan_schedule_kernel<<<1, kRadix, 0, stream>>>(hist, bases, passes, chunks, in_place, sched);
+cudaError_t launch_scan_schedule(uint64_t* hist, uint64_t* chunk_base, uint32_t* chunk_flag, int passes,
+                                 uint32_t chunks, int in_place, Schedule* sched, cudaStream_t stream) {
+  scan_schedule_kernel<<<1, kRadix, 0, stream>>>(hist, chunk_base, chunk_flag, passes, chunks, in_place, sched);
   return cudaGetLastError();
 }
 

@@ -22,21 +22,20 @@ int tile_keys_for(int key_bits);
 // Keys per look-back chunk: whole tiles, fewer than 2^30 keys.
 uint64_t chunk_keys_for(int key_bits);
 
-// K1: per-pass digit histograms of keys[0, n).  hist[j * pass_stride +
-// chunk * chunk_stride + d] += count of digit d of pass j among the keys of
-// look-back chunk `chunk` (chunk_stride 0 folds all chunks into one row).
-// Also zeroes clear_words words at `clear` (the first pass's look-back region
-// and the tile counters) on the way.
-cudaError_t launch_histogram(const void* keys, int key_bits, uint64_t n, uint64_t chunk_keys, const DigitPlan& plan,
-                             uint64_t* hist, uint64_t pass_stride, uint64_t chunk_stride, uint32_t* clear,
-                             uint64_t clear_words, int sms, cudaStream_t stream);
+// K1: per-pass digit histograms of keys[0, n): hist[j * pass_stride + d] +=
+// count of digit d of pass j.  Also zeroes clear_words words at `clear` (the
+// first pass's look-back region and the tile counters) on the way.
+cudaError_t launch_histogram(const void* keys, int key_bits, uint64_t n, const DigitPlan& plan, uint64_t* hist,
+                             uint64_t pass_stride, uint32_t* clear, uint64_t clear_words, int sms,
+                             cudaStream_t stream);
 
-// K2: per pass, exclusive scan over digits of the chunk-summed histogram, the
-// 64-bit base of every (chunk, digit), and the device-side pass schedule.
-// hist/bases are [passes][chunks][256]; hist is left all zero.  in_place: the result must land in the
-// input buffer.  sched may be null (no schedule: used by the one-pass step).
-cudaError_t launch_scan_schedule(uint64_t* hist, uint64_t* bases, int passes, uint32_t chunks, int in_place,
-                                 Schedule* sched, cudaStream_t stream);
+// K2: per pass, exclusive scan over digits of the histogram (hist[j][256]),
+// written as the 64-bit bases of look-back chunk 0 (chunk_base[j][chunks][256]),
+// the chunk-ready flags of later chunks zeroed (chunk_flag[j][chunks]), and the
+// device-side pass schedule.  hist is left all zero.  in_place: the result must
+// land in the input buffer.  sched may be null (the one-pass step).
+cudaError_t launch_scan_schedule(uint64_t* hist, uint64_t* chunk_base, uint32_t* chunk_flag, int passes,
+                                 uint32_t chunks, int in_place, Schedule* sched, cudaStream_t stream);
 
 // Row-wise exclusive scan, one CTA per row (bins <= 65536).
 cudaError_t launch_scan_rows(const uint64_t* in, uint64_t* out, uint64_t rows, uint64_t bins, cudaStream_t stream);
@@ -52,7 +51,9 @@ struct OnesweepArgs {
   uint32_t* tile_counter;  // this pass's dynamic tile counter, zero on entry
   uint32_t* next_lookback; // region the next pass will use (cleared here), or null
   uint32_t* next_counter;  // the next pass's counter (cleared here), or null
-  const uint64_t* bases;   // [chunks][256]
+  uint64_t* chunk_base;    // [chunks][256] 64-bit digit bases; chunk 0 from the scan, later chunks
+                           // written by the last tile of the chunk before
+  uint32_t* chunk_flag;    // [chunks] set once a chunk's bases are written (entry 0 unused)
   const Schedule* sched;   // null: always run, input -> output
   int32_t pass;
   uint32_t tiles_per_chunk;

@@ -10,17 +10,20 @@
 //     keys, each lane adds its lane bit to a warp-private shared word of its
 //     digit; the word then holds exactly the __match_any_sync peer mask of the
 //     lane (lanes with the same digit).  The lowest peer adds the group size to
-//     the warp's 16-bit-range digit counter and broadcasts the old value; a
-//     lane's rank is that value plus its peers below it.  (The hardware
-//     match.any instruction computes the same mask but measured 5-6x slower on
-//     uniform 8-bit digits on GB300; see the design notes.)
+//     the warp's digit counter and broadcasts the old value; a lane's rank is
+//     that value plus its peers below it.  (The hardware match.any instruction
+//     computes the same mask but measured 5-6x slower on uniform 8-bit digits
+//     on GB300.)
 //  3. Warp counters -> per-warp exclusive prefixes and the tile's digit counts,
 //     published at once to the decoupled look-back (2-bit flag | 30-bit count,
 //     the tapered counter width of Sec. III-D-1: a chunk never holds 2^30 keys).
 //  4. Keys and values are permuted into digit order inside shared memory.
-//  5. The look-back walks predecessor tiles (bounded wait) to find each digit's
-//     exclusive prefix among earlier tiles of the chunk, adds the chunk's 64-bit
-//     base from the scan, and publishes its inclusive prefix.
+//  5. The look-back reads a window of predecessor tiles at a time (bounded
+//     wait) to find each digit's exclusive prefix among earlier tiles of the
+//     chunk, and publishes its inclusive prefix.  The 64-bit base of the chunk
+//     comes from the scan (chunk 0) or from the last tile of the previous chunk,
+//     which publishes the next chunk's bases (a 64-bit running total per digit)
+//     once its own prefix is known.
 //  6. The staged tile is written out in digit runs, consecutive threads to
 //     consecutive addresses.
 #include <cstdint>
@@ -34,15 +37,16 @@ namespace {
 
 constexpr int kRadix = 256;
 constexpr int kBlock = 256;  // == kRadix: thread d owns digit d in the per-digit steps
+constexpr int kWindow = 16;  // predecessor tiles read per look-back round trip
 
 template <typename K>
 struct TileShape;
 template <>
-struct TileShape<uint16_t> { static constexpr int kIpt = 32; };
+struct TileShape<uint16_t> { static constexpr int kIpt = 32; static constexpr int kMinBlocks = 3; };
 template <>
-struct TileShape<uint32_t> { static constexpr int kIpt = 24; };
+struct TileShape<uint32_t> { static constexpr int kIpt = 24; static constexpr int kMinBlocks = 2; };
 template <>
-struct TileShape<uint64_t> { static constexpr int kIpt = 16; };
+struct TileShape<uint64_t> { static constexpr int kIpt = 16; static constexpr int kMinBlocks = 2; };
 
 template <typename K, bool kVals>
 struct SmemLayout {
@@ -85,12 +89,33 @@ __device__ __forceinline__ uint32_t dig(K k, uint32_t shift, uint32_t mask) {
   return uint32_t(uint64_t(k) >> shift) & mask;
 }
 
+// Per-item key and in-warp rank.  16-bit keys share one register with their
+// rank (ranks stay below the tile size, 2^13); wider keys keep two.
+template <typename K>
+struct Item {
+  K key;
+  uint32_t rank;
+  __device__ __forceinline__ void set(K k, uint32_t r) { key = k; rank = r; }
+  __device__ __forceinline__ K k() const { return key; }
+  __device__ __forceinline__ uint32_t r() const { return rank; }
+  __device__ __forceinline__ void set_r(uint32_t r) { rank = r; }
+};
+template <>
+struct Item<uint16_t> {
+  uint32_t packed;
+  __device__ __forceinline__ void set(uint16_t k, uint32_t r) { packed = uint32_t(k) | (r << 16); }
+  __device__ __forceinline__ uint16_t k() const { return uint16_t(packed & 0xFFFFu); }
+  __device__ __forceinline__ uint32_t r() const { return packed >> 16; }
+  __device__ __forceinline__ void set_r(uint32_t r) { packed = (packed & 0xFFFFu) | (r << 16); }
+};
+
 template <typename K, bool kVals>
-__global__ void __launch_bounds__(kBlock) onesweep_kernel(const OnesweepArgs a) {
+__global__ void __launch_bounds__(kBlock, TileShape<K>::kMinBlocks) onesweep_kernel(const OnesweepArgs a) {
   using L = SmemLayout<K, kVals>;
   constexpr int kIpt = L::kIpt;
   constexpr int kTile = L::kTile;
   constexpr int kWarps = L::kWarps;
+  static_assert(kTile <= 65536, "in-warp ranks are kept in 16 bits");
   extern __shared__ __align__(1024) unsigned char smem[];
   K* s_keys = reinterpret_cast<K*>(smem + L::kKeys);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + L::kVals_);
@@ -162,14 +187,12 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const OnesweepArgs a) 
   uint32_t* wmask1 = s_mask + (kWarps + warp) * kRadix;
   uint32_t* wcnt = s_wcnt + warp * kRadix;
   const int wbase = warp * 32 * kIpt;
-  K keys[kIpt];
-  uint32_t rank[kIpt];
+  Item<K> it[kIpt];
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
     const int pos = wbase + i * 32 + lane;
     const bool valid = uint32_t(pos) < tile_n;
     const K k = valid ? s_keys[pos] : K(0);
-    keys[i] = k;
     const uint32_t d = dig(k, shift, mask);
     uint32_t* wmask = (i & 1) ? wmask1 : wmask0;
     if (valid) atomicAdd(&wmask[d], me);
@@ -183,12 +206,16 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const OnesweepArgs a) 
       wmask[d] = 0;
     }
     base = __shfl_sync(0xffffffffu, base, valid ? (__ffs(peers) - 1) : lane);
-    rank[i] = base + below;
+    it[i].set(k, base + below);
   }
   __syncthreads();
 
   // 3. per-digit: warp prefixes, tile count, publish, tile-exclusive prefix
-  const bool first_in_chunk = (tile % a.tiles_per_chunk) == 0;
+  const uint32_t tpc = a.tiles_per_chunk;
+  const uint32_t chunk = tile / tpc;
+  const uint32_t chunk_first = chunk * tpc;
+  const bool first_in_chunk = tile == chunk_first;
+  const bool last_in_chunk = (tile - chunk_first == tpc - 1) && (tile + 1 < gridDim.x);
   uint32_t* lb = a.lookback + uint64_t(tile) * kRadix;
   {
     const int d = tid;
@@ -211,10 +238,11 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const OnesweepArgs a) 
   for (int i = 0; i < kIpt; ++i) {
     const int pos = wbase + i * 32 + lane;
     if (uint32_t(pos) < tile_n) {
-      const uint32_t d = dig(keys[i], shift, mask);
-      const uint32_t p = s_excl[d] + s_wcnt[warp * kRadix + d] + rank[i];
-      s_keys[p] = keys[i];
-      rank[i] = p;
+      const K k = it[i].k();
+      const uint32_t d = dig(k, shift, mask);
+      const uint32_t p = s_excl[d] + s_wcnt[warp * kRadix + d] + it[i].r();
+      s_keys[p] = k;
+      it[i].set_r(p);
       if (kVals) vreg[i] = s_vals[pos];
     }
   }
@@ -223,45 +251,86 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const OnesweepArgs a) 
 #pragma unroll
     for (int i = 0; i < kIpt; ++i) {
       const int pos = wbase + i * 32 + lane;
-      if (uint32_t(pos) < tile_n) s_vals[rank[i]] = vreg[i];
+      if (uint32_t(pos) < tile_n) s_vals[it[i].r()] = vreg[i];
     }
   }
 
-  // 5. decoupled look-back for digit d = tid
+  // 5. decoupled look-back for digit d = tid, kWindow predecessors per round trip
   {
     const int d = tid;
     const uint32_t cnt = s_cnt[d];
     uint32_t excl = 0;
     if (!first_in_chunk) {
-      const uint32_t chunk_first = tile - tile % a.tiles_per_chunk;
-      uint32_t t = tile - 1;
-      uint64_t t_start = 0;
+      uint32_t t = tile;  // tiles [chunk_first, t) are still to the left
+      uint64_t t_wait = 0;
       while (true) {
-        const uint32_t w = ld_relaxed_gpu(a.lookback + uint64_t(t) * kRadix + d);
-        const uint32_t flag = w & ~kCountMask;
-        if (flag == 0) {
-          if (t_start == 0) t_start = global_timer_ns();
-          else if (global_timer_ns() - t_start > kWaitLimitNs) {
-            atomicOr(a.status, kDevTimeoutLookback);
-            break;
+        const uint32_t left = t - chunk_first;
+        const uint32_t w = left < uint32_t(kWindow) ? left : uint32_t(kWindow);
+        uint32_t v[kWindow];
+#pragma unroll
+        for (int i = 0; i < kWindow; ++i)
+          v[i] = (uint32_t(i) < w) ? ld_relaxed_gpu(a.lookback + uint64_t(t - 1 - i) * kRadix + d) : 0u;
+        bool stop = false, found = false;
+        uint32_t used = 0;
+#pragma unroll
+        for (int i = 0; i < kWindow; ++i) {
+          if (!stop && uint32_t(i) < w) {
+            const uint32_t f = v[i] & ~kCountMask;
+            if (f == 0) {
+              stop = true;  // not published yet: read again from here
+            } else {
+              excl += v[i] & kCountMask;
+              ++used;
+              if (f == kFlagPrefix) stop = found = true;
+            }
           }
-          continue;
         }
-        t_start = 0;
-        excl += w & kCountMask;
-        if (flag == kFlagPrefix) break;
+        if (found) break;
+        t -= used;
         if (t == chunk_first) {  // a chunk's first tile always publishes a prefix
           atomicOr(a.status, kDevBadLookback);
           break;
         }
-        --t;
+        if (used < w) {  // blocked on an unpublished predecessor
+          if (t_wait == 0) {
+            t_wait = global_timer_ns();
+          } else if (global_timer_ns() - t_wait > kWaitLimitNs) {
+            atomicOr(a.status, kDevTimeoutLookback);
+            break;
+          }
+          __nanosleep(64);
+        } else {
+          t_wait = 0;
+        }
       }
       st_relaxed_gpu(lb + d, kFlagPrefix | (excl + cnt));
     }
-    const uint64_t chunk = tile / a.tiles_per_chunk;
-    s_off[d] = a.bases[chunk * kRadix + d] + excl - s_excl[d];
+    // 64-bit base of this digit in this chunk.
+    unsigned long long base;
+    if (chunk == 0) {
+      base = a.chunk_base[d];
+    } else {
+      const uint32_t* flag = a.chunk_flag + chunk;
+      if (!ld_acquire_gpu(flag)) {
+        const uint64_t t_wait = global_timer_ns();
+        while (!ld_acquire_gpu(flag)) {
+          if (global_timer_ns() - t_wait > kWaitLimitNs) {
+            atomicOr(a.status, kDevTimeoutLookback);
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      base = a.chunk_base[uint64_t(chunk) * kRadix + d];
+    }
+    s_off[d] = base + excl - s_excl[d];
+    if (last_in_chunk) {  // hand the next chunk its 64-bit bases
+      a.chunk_base[uint64_t(chunk + 1) * kRadix + d] = base + excl + cnt;
+      __threadfence();
+    }
   }
   __syncthreads();
+  if (last_in_chunk && tid == 0) st_release_gpu(a.chunk_flag + chunk + 1, 1u);
 
   // 6. write the staged tile out in digit runs
   K* kout = const_cast<K*>(static_cast<const K*>(a.keys[dst]));
