@@ -35,21 +35,24 @@
 namespace fsort {
 namespace {
 
-constexpr int kRadix = 256;
-constexpr int kBlock = 256;  // == kRadix: thread d owns digit d in the per-digit steps
+constexpr int kRadix = 256;  // threads 0..255 own one digit each in the per-digit steps
 constexpr int kWindow = 16;  // predecessor tiles read per look-back round trip
 
+// Threads per CTA, keys per thread, and the CTAs per SM the register budget
+// is sized for.  Two 16-warp CTAs per SM keep 32 ranking chains of kIpt
+// items in flight per SM.
 template <typename K>
 struct TileShape;
 template <>
-struct TileShape<uint16_t> { static constexpr int kIpt = 32; static constexpr int kMinBlocks = 3; };
+struct TileShape<uint16_t> { static constexpr int kBlock = 512, kIpt = 16, kMinBlocks = 2; };
 template <>
-struct TileShape<uint32_t> { static constexpr int kIpt = 24; static constexpr int kMinBlocks = 2; };
+struct TileShape<uint32_t> { static constexpr int kBlock = 512, kIpt = 12, kMinBlocks = 2; };
 template <>
-struct TileShape<uint64_t> { static constexpr int kIpt = 16; static constexpr int kMinBlocks = 2; };
+struct TileShape<uint64_t> { static constexpr int kBlock = 512, kIpt = 8, kMinBlocks = 2; };
 
 template <typename K, bool kVals>
 struct SmemLayout {
+  static constexpr int kBlock = TileShape<K>::kBlock;
   static constexpr int kIpt = TileShape<K>::kIpt;
   static constexpr int kTile = kBlock * kIpt;
   static constexpr int kWarps = kBlock / 32;
@@ -61,12 +64,15 @@ struct SmemLayout {
   static constexpr size_t kCnt = kExcl + kRadix * 4;
   static constexpr size_t kOff = kCnt + kRadix * 4;  // 8-byte aligned: all above are multiples of 1 KB
   static constexpr size_t kScan = kOff + kRadix * 8;
-  static constexpr size_t kBar = kScan + 8 * 4;
+  static constexpr size_t kBar = kScan + 16 * 4;
   static constexpr size_t kTileId = kBar + 8;
   static constexpr size_t kBytes = kTileId + 16;
 };
 
-__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t x, uint32_t* s_warp) {
+// Exclusive scan of x over threads 0..255 (the digits); every thread of the
+// block must call it (it contains a barrier).
+template <int kBlock>
+__device__ __forceinline__ uint32_t digit_excl_scan(uint32_t x, uint32_t* s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t inc = x;
 #pragma unroll
@@ -74,11 +80,11 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t x, uint32_t* s_
     const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc += y;
   }
-  if (lane == 31) s_warp[warp] = inc;
+  if (lane == 31 && warp < kRadix / 32) s_warp[warp] = inc;
   __syncthreads();
   uint32_t before = 0;
 #pragma unroll
-  for (int w = 0; w < kBlock / 32; ++w)
+  for (int w = 0; w < kRadix / 32; ++w)
     if (w < warp) before += s_warp[w];
   return before + inc - x;
 }
@@ -90,7 +96,7 @@ __device__ __forceinline__ uint32_t dig(K k, uint32_t shift, uint32_t mask) {
 }
 
 // Per-item key and in-warp rank.  16-bit keys share one register with their
-// rank (ranks stay below the tile size, 2^13); wider keys keep two.
+// rank (ranks stay below the tile size); wider keys keep two.
 template <typename K>
 struct Item {
   K key;
@@ -110,8 +116,10 @@ struct Item<uint16_t> {
 };
 
 template <typename K, bool kVals>
-__global__ void __launch_bounds__(kBlock, TileShape<K>::kMinBlocks) onesweep_kernel(const OnesweepArgs a) {
+__global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks)
+    onesweep_kernel(const OnesweepArgs a) {
   using L = SmemLayout<K, kVals>;
+  constexpr int kBlock = L::kBlock;
   constexpr int kIpt = L::kIpt;
   constexpr int kTile = L::kTile;
   constexpr int kWarps = L::kWarps;
@@ -139,7 +147,7 @@ __global__ void __launch_bounds__(kBlock, TileShape<K>::kMinBlocks) onesweep_ker
   }
   // The next pass uses the other look-back region: clear this block's slot of
   // it (one block per tile, so the slots cover every tile) and its counter.
-  if (a.next_lookback) a.next_lookback[uint64_t(blockIdx.x) * kRadix + tid] = 0;
+  if (a.next_lookback && tid < kRadix) a.next_lookback[uint64_t(blockIdx.x) * kRadix + tid] = 0;
   if (a.next_counter && blockIdx.x == 0 && tid == 0) *a.next_counter = 0;
   if (!active) return;
 
@@ -220,15 +228,18 @@ __global__ void __launch_bounds__(kBlock, TileShape<K>::kMinBlocks) onesweep_ker
   {
     const int d = tid;
     uint32_t run = 0;
+    if (d < kRadix) {
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const uint32_t c = s_wcnt[w * kRadix + d];
-      s_wcnt[w * kRadix + d] = run;
-      run += c;
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = s_wcnt[w * kRadix + d];
+        s_wcnt[w * kRadix + d] = run;
+        run += c;
+      }
+      s_cnt[d] = run;
+      st_relaxed_gpu(lb + d, (first_in_chunk ? kFlagPrefix : kFlagAggregate) | run);
     }
-    s_cnt[d] = run;
-    st_relaxed_gpu(lb + d, (first_in_chunk ? kFlagPrefix : kFlagAggregate) | run);
-    s_excl[d] = block_excl_scan_u32(run, s_scan);
+    const uint32_t ex = digit_excl_scan<kBlock>(run, s_scan);
+    if (d < kRadix) s_excl[d] = ex;
   }
   __syncthreads();
 
@@ -256,7 +267,7 @@ __global__ void __launch_bounds__(kBlock, TileShape<K>::kMinBlocks) onesweep_ker
   }
 
   // 5. decoupled look-back for digit d = tid, kWindow predecessors per round trip
-  {
+  if (tid < kRadix) {
     const int d = tid;
     const uint32_t cnt = s_cnt[d];
     uint32_t excl = 0;
@@ -357,12 +368,14 @@ cudaError_t launch_typed(const OnesweepArgs& a, cudaStream_t stream) {
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<K, kVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(L::kBytes));
+    if (e == cudaSuccess)  // all of the unified L1/shared capacity as shared memory
+      e = cudaFuncSetAttribute(onesweep_kernel<K, kVals>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const uint64_t tiles = (a.n + L::kTile - 1) / L::kTile;
   if (!tiles) return cudaSuccess;
-  onesweep_kernel<K, kVals><<<unsigned(tiles), kBlock, L::kBytes, stream>>>(a);
+  onesweep_kernel<K, kVals><<<unsigned(tiles), L::kBlock, L::kBytes, stream>>>(a);
   return cudaGetLastError();
 }
 
