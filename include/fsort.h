@@ -194,6 +194,38 @@ FSORT_API fsort_status fsort_plan_set_timing(fsort_plan* plan, int enable);
 FSORT_API fsort_status fsort_plan_timing_report(fsort_plan* plan, fsort_kernel_time* out, uint32_t capacity,
                                                 uint32_t* count);
 
+/* ---- allocation-free entry point --------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * call cudaMalloc where they sort: code running under another component's
+ * memory budget (a caching allocator that already holds nearly all device
+ * memory), latency-critical paths that must not take cudaMalloc's implicit
+ * device synchronisation, and hosts that forbid device allocation after start
+ * up.  Such callers cannot create a plan either, so this call needs none.
+ *
+ * fsort_scatter_pass_noalloc performs exactly what fsort_scatter_pass does
+ * (one stable scatter pass on raw key bits [shift, shift + width),
+ * 1 <= width <= 8, out of place, same argument rules) but keeps its scratch in
+ * a fixed array of FSORT_NOALLOC_SCRATCH_BYTES (about 4 MiB) that the library
+ * declares in device memory.  Every GPU that loads libfsort holds that array
+ * until the process exits.  The call allocates nothing: no cudaMalloc or
+ * cudaFree, no allocating library routine.
+ *   - n must not exceed FSORT_NOALLOC_MAX_KEYS; larger n returns
+ *     FSORT_ERR_INVALID_ARG without doing anything.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - The call is synchronous: it enqueues its kernels on `stream`, waits for
+ *     them, and returns FSORT_ERR_TIMEOUT if a device-side wait gave up.
+ *   - All calls share the one array and it keeps the last call's contents (the
+ *     call clears what must start at zero).  Calls that overlap on the GPU --
+ *     from several host threads, or alongside another call on another stream --
+ *     race on it and give wrong results; serialise them. */
+#define FSORT_NOALLOC_MAX_KEYS 16777216ull
+#define FSORT_NOALLOC_SCRATCH_BYTES 4199168ull
+FSORT_API fsort_status fsort_scatter_pass_noalloc(const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                                                  uint32_t* vals_out, uint64_t n, int key_bits, int shift, int width,
+                                                  void* stream);
+
 /* Raw device flag bits behind the last FSORT_ERR_TIMEOUT / FSORT_ERR_INTERNAL
  * this plan reported (0 if none): 1 look-back wait timed out, 2 bulk-copy wait
  * timed out, 4 tile id beyond the grid, 8 look-back walk found no prefix at its

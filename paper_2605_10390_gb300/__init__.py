@@ -29,6 +29,8 @@ from ._binding import (  # noqa: F401
     fsort_plan_sync,
     fsort_plan_timing_report,
     fsort_scatter_pass,
+    fsort_scatter_pass_noalloc,
+    FSORT_NOALLOC_MAX_KEYS,
     fsort_sort_pairs,
     fsort_sort_pairs_host,
     fsort_sort_pairs_out,

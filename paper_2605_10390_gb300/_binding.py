@@ -77,6 +77,7 @@ def load_library():
             "fsort_plan_timing_report": ([vp, ctypes.POINTER(FsortKernelTime), ctypes.c_uint32,
                                           ctypes.POINTER(ctypes.c_uint32)], st),
             "fsort_plan_device_flags": ([vp], ctypes.c_uint32),
+            "fsort_scatter_pass_noalloc": ([vp, vp, vp, vp, u64, i32, i32, i32, vp], st),
             "fsort_status_string": ([i32], ctypes.c_char_p),
             "fsort_version": ([], i32),
         }
@@ -220,6 +221,20 @@ def fsort_scatter_pass(plan, keys_in, vals_in, keys_out, vals_out, shift: int, w
     _check(load_library().fsort_scatter_pass(plan, _ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
                                              _numel(keys_in, n), kb, shift, width, _stream(stream)),
            "fsort_scatter_pass")
+
+
+FSORT_NOALLOC_MAX_KEYS = 1 << 24
+
+
+def fsort_scatter_pass_noalloc(keys_in, vals_in, keys_out, vals_out, shift: int, width: int, n=None, key_bits=None,
+                               stream=None) -> None:
+    """One stable scatter pass without any allocation: its scratch is a fixed
+    device array owned by the library (for callers that cannot cudaMalloc).
+    Synchronous; n <= FSORT_NOALLOC_MAX_KEYS; concurrent calls race."""
+    kb = _key_bits_of(keys_in, key_bits)
+    _check(load_library().fsort_scatter_pass_noalloc(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
+                                                     _numel(keys_in, n), kb, shift, width, _stream(stream)),
+           "fsort_scatter_pass_noalloc")
 
 
 def fsort_expand(plan, counts, keys_out, n=None, key_bits=16, stream=None) -> None:
