@@ -6,26 +6,27 @@
 //
 //  1. A bulk async copy (cp.async.bulk + mbarrier) stages the tile's keys and
 //     values in shared memory.
-//  2. The tile is stably sorted by the pass's 8-bit digit inside shared
-//     memory with two counting passes on 4-bit halves of the digit (low half
-//     first): each thread owns kIpt consecutive keys and counts them in sixteen
-//     4-bit fields of one 64-bit register, a block-wide exclusive scan over
-//     (nibble, thread) turns the counts into positions, and one scatter per
-//     half moves (key, source index) records.  No shared-memory atomics or warp
-//     votes are needed for stability: order within a thread is its key order,
-//     and threads are scanned in order.  The tile's digit counts are gathered
-//     on the way with shared-memory reductions.
-//  3. The digit counts are published at once to the decoupled look-back
-//     (2-bit flag | 30-bit count, the tapered counter width of Sec. III-D-1: a
-//     chunk never holds 2^30 keys), and scanned into tile-local digit starts.
-//  4. The look-back reads a window of predecessor tiles at a time (bounded
+//  2. Stable rank within each warp's strip of the tile: for every round of 32
+//     keys, each lane adds its lane bit to a warp-private shared word of its
+//     digit; the word then holds exactly the __match_any_sync peer mask of the
+//     lane (lanes with the same digit).  The lowest peer adds the group size to
+//     the warp's digit counter and broadcasts the old value; a lane's rank is
+//     that value plus its peers below it.  (The hardware match.any instruction
+//     computes the same mask but measured 5-6x slower on uniform 8-bit digits
+//     on GB300.)
+//  3. Warp counters -> per-warp exclusive prefixes and the tile's digit counts,
+//     published at once to the decoupled look-back (2-bit flag | 30-bit count,
+//     the tapered counter width of Sec. III-D-1: a chunk never holds 2^30 keys).
+//  4. Keys are permuted into digit order inside shared memory, each with its
+//     source position (values are gathered through it when written out).
+//  5. The look-back reads a window of predecessor tiles at a time (bounded
 //     wait) to find each digit's exclusive prefix among earlier tiles of the
 //     chunk, and publishes its inclusive prefix.  The 64-bit base of the chunk
 //     comes from the scan (chunk 0) or from the last tile of the previous chunk,
 //     which publishes the next chunk's bases (a 64-bit running total per digit)
 //     once its own prefix is known.
-//  5. The sorted tile is written out in digit runs, consecutive threads to
-//     consecutive addresses; values are gathered through the source index.
+//  6. The staged tile is written out in digit runs, consecutive threads to
+//     consecutive addresses.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -36,52 +37,34 @@ namespace fsort {
 namespace {
 
 constexpr int kRadix = 256;  // threads 0..255 own one digit each in the per-digit steps
-constexpr int kNib = 16;     // bins of one 4-bit counting step
 constexpr int kWindow = 16;  // predecessor tiles read per look-back round trip
 
-// Threads per CTA and keys per thread (<= 15: per-thread counts live in 4-bit
-// fields).  Two CTAs per SM.
+// Threads per CTA, keys per thread, and the CTAs per SM the register budget
+// is sized for.  Two 16-warp CTAs per SM keep 32 ranking chains of kIpt
+// items in flight per SM.
 template <typename K>
 struct TileShape;
 template <>
-struct TileShape<uint16_t> { static constexpr int kBlock = 512, kIpt = 15, kMinBlocks = 2; };
+struct TileShape<uint16_t> { static constexpr int kBlock = 512, kIpt = 16, kMinBlocks = 2; };
 template <>
-struct TileShape<uint32_t> { static constexpr int kBlock = 512, kIpt = 15, kMinBlocks = 2; };
+struct TileShape<uint32_t> { static constexpr int kBlock = 512, kIpt = 12, kMinBlocks = 2; };
 template <>
 struct TileShape<uint64_t> { static constexpr int kBlock = 512, kIpt = 8, kMinBlocks = 2; };
-
-// Sorted records: 16-bit keys travel packed with their 13-bit source index in
-// one 32-bit word; wider keys stay in the input buffer and only a 16-bit
-// source index moves.
-template <typename K>
-struct Rec {
-  using T = uint16_t;
-  static constexpr bool kPacked = false;
-};
-template <>
-struct Rec<uint16_t> {
-  using T = uint32_t;
-  static constexpr bool kPacked = true;
-};
 
 template <typename K, bool kVals>
 struct SmemLayout {
   static constexpr int kBlock = TileShape<K>::kBlock;
   static constexpr int kIpt = TileShape<K>::kIpt;
   static constexpr int kTile = kBlock * kIpt;
-  using R = typename Rec<K>::T;
-  static constexpr size_t align(size_t x) { return (x + 1023) / 1024 * 1024; }
-  // Packed records reuse the input-key region (the keys are in registers by
-  // the time the first scatter writes); otherwise records get their own.
+  static constexpr int kWarps = kBlock / 32;
   static constexpr size_t kKeys = 0;
-  static constexpr size_t kKeyBytes = Rec<K>::kPacked ? size_t(kTile) * sizeof(R) : size_t(kTile) * sizeof(K);
-  static constexpr size_t kRecs = Rec<K>::kPacked ? kKeys : align(kKeys + kKeyBytes);
-  static constexpr size_t kVals_ = align(Rec<K>::kPacked ? kKeys + kKeyBytes : kRecs + size_t(kTile) * sizeof(R));
-  static constexpr size_t kCnt16 = align(kVals_ + (kVals ? size_t(kTile) * 4 : 0));  // [16][kBlock] u16
-  static constexpr size_t kHist = align(kCnt16 + size_t(kNib) * kBlock * 2);          // [256] u32
-  static constexpr size_t kExcl = kHist + kRadix * 4;
-  static constexpr size_t kOff = kExcl + kRadix * 4;  // 8-byte aligned
-  static constexpr size_t kScan = kOff + kRadix * 8;  // 16 warp totals
+  static constexpr size_t kVals_ = kKeys + size_t(kTile) * sizeof(K);
+  static constexpr size_t kMask = kVals_ + (kVals ? size_t(kTile) * 4 : 0);
+  static constexpr size_t kWcnt = kMask + 2 * size_t(kWarps) * kRadix * 4;  // masks double-buffered
+  static constexpr size_t kExcl = kWcnt + size_t(kWarps) * kRadix * 4;
+  static constexpr size_t kCnt = kExcl + kRadix * 4;
+  static constexpr size_t kOff = kCnt + kRadix * 4;  // 8-byte aligned: all above are multiples of 1 KB
+  static constexpr size_t kScan = kOff + kRadix * 8;
   static constexpr size_t kBar = kScan + 16 * 4;
   static constexpr size_t kTileId = kBar + 8;
   static constexpr size_t kBytes = kTileId + 16;
@@ -89,6 +72,7 @@ struct SmemLayout {
 
 // Exclusive scan of x over threads 0..255 (the digits); every thread of the
 // block must call it (it contains a barrier).
+template <int kBlock>
 __device__ __forceinline__ uint32_t digit_excl_scan(uint32_t x, uint32_t* s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t inc = x;
@@ -106,76 +90,56 @@ __device__ __forceinline__ uint32_t digit_excl_scan(uint32_t x, uint32_t* s_warp
   return before + inc - x;
 }
 
-// In-place exclusive scan of the [16][kBlock] u16 count matrix in row-major
-// order (nibble-major, then thread), i.e. the stable counting-sort positions.
-// Thread t rakes the 16 consecutive entries [16t, 16t + 16).  Contains
-// barriers; every thread calls it.
-template <int kBlock>
-__device__ __forceinline__ void scan_counts(uint16_t* cnt, uint32_t* s_warp) {
-  static_assert(kNib * kBlock == 16 * kBlock, "one 16-entry segment per thread");
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint4* seg = reinterpret_cast<uint4*>(cnt + 16 * tid);
-  uint4 q0 = seg[0], q1 = seg[1];
-  uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-  uint32_t total = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) total += (w[i] & 0xFFFFu) + (w[i] >> 16);
-  uint32_t inc = total;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31) s_warp[warp] = inc;
-  __syncthreads();
-  uint32_t run = inc - total;
-#pragma unroll
-  for (int v = 0; v < kBlock / 32; ++v)
-    if (v < warp) run += s_warp[v];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const uint32_t lo = w[i] & 0xFFFFu, hi = w[i] >> 16;
-    w[i] = run | ((run + lo) << 16);
-    run += lo + hi;
-  }
-  seg[0] = make_uint4(w[0], w[1], w[2], w[3]);
-  seg[1] = make_uint4(w[4], w[5], w[6], w[7]);
-  __syncthreads();
-}
-
 template <typename K>
 __device__ __forceinline__ uint32_t dig(K k, uint32_t shift, uint32_t mask) {
   if (sizeof(K) <= 4) return (uint32_t(k) >> shift) & mask;
   return uint32_t(uint64_t(k) >> shift) & mask;
 }
 
-// 4-bit field of a 64-bit counter word.
-__device__ __forceinline__ uint32_t field4(uint64_t c, uint32_t v) { return uint32_t(c >> (4 * v)) & 15u; }
+// Per-item key and in-warp rank.  16-bit keys share one register with their
+// rank (ranks stay below the tile size); wider keys keep two.
+template <typename K>
+struct Item {
+  K key;
+  uint32_t rank;
+  __device__ __forceinline__ void set(K k, uint32_t r) { key = k; rank = r; }
+  __device__ __forceinline__ K k() const { return key; }
+  __device__ __forceinline__ uint32_t r() const { return rank; }
+  __device__ __forceinline__ void set_r(uint32_t r) { rank = r; }
+};
+template <>
+struct Item<uint16_t> {
+  uint32_t packed;
+  __device__ __forceinline__ void set(uint16_t k, uint32_t r) { packed = uint32_t(k) | (r << 16); }
+  __device__ __forceinline__ uint16_t k() const { return uint16_t(packed & 0xFFFFu); }
+  __device__ __forceinline__ uint32_t r() const { return packed >> 16; }
+  __device__ __forceinline__ void set_r(uint32_t r) { packed = (packed & 0xFFFFu) | (r << 16); }
+};
 
 template <typename K, bool kVals>
 __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks)
     onesweep_kernel(const OnesweepArgs a) {
   using L = SmemLayout<K, kVals>;
-  using R = typename L::R;
-  constexpr bool kPacked = Rec<K>::kPacked;
   constexpr int kBlock = L::kBlock;
   constexpr int kIpt = L::kIpt;
   constexpr int kTile = L::kTile;
-  static_assert(kIpt <= 15, "per-thread counts are 4-bit fields");
-  static_assert(kTile <= 8192, "packed records carry a 13-bit source index");
+  constexpr int kWarps = L::kWarps;
+  static_assert(kTile <= 65536, "in-warp ranks are kept in 16 bits");
+  static_assert(2 * kWarps * kRadix * 4 >= kTile * (sizeof(K) == 2 ? 4 : 2), "records fit the mask words");
+  static_assert(sizeof(K) != 2 || kTile <= 65536, "packed records carry a 16-bit source position");
   extern __shared__ __align__(1024) unsigned char smem[];
   K* s_keys = reinterpret_cast<K*>(smem + L::kKeys);
-  R* s_rec = reinterpret_cast<R*>(smem + L::kRecs);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + L::kVals_);
-  uint16_t* s_cnt16 = reinterpret_cast<uint16_t*>(smem + L::kCnt16);
-  uint32_t* s_hist = reinterpret_cast<uint32_t*>(smem + L::kHist);
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem + L::kMask);
+  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem + L::kWcnt);
   uint32_t* s_excl = reinterpret_cast<uint32_t*>(smem + L::kExcl);
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + L::kCnt);
   unsigned long long* s_off = reinterpret_cast<unsigned long long*>(smem + L::kOff);
   uint32_t* s_scan = reinterpret_cast<uint32_t*>(smem + L::kScan);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + L::kBar);
   uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::kTileId);
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   int src = kBufIn, dst = kBufOut, active = 1;
   if (a.sched) {
@@ -195,7 +159,8 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
     mbar_init(s_bar, 1);
     fence_mbar_init();
   }
-  if (tid < kRadix) s_hist[tid] = 0;
+  for (int i = tid; i < 2 * kWarps * kRadix; i += kBlock) s_mask[i] = 0;
+  for (int i = tid; i < kWarps * kRadix; i += kBlock) s_wcnt[i] = 0;
   __syncthreads();
 
   const uint32_t tile = *s_tile;
@@ -223,87 +188,94 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   if (!mbar_wait_bounded(s_bar, 0)) atomicOr(a.status, kDevTimeoutLoad);
   __syncthreads();
 
-  // 2. stable in-tile sort by the digit: two 4-bit counting steps.
+  // 2. stable in-warp ranks
   const uint32_t shift = a.shift, mask = a.mask;
-  const uint32_t first = uint32_t(tid) * kIpt;  // this thread's keys [first, first + kIpt)
-  R rec[kIpt];
-  uint64_t c = 0;
-  // Step A (low nibble), counting: key order within the thread is input order.
+  const uint32_t lt = lanemask_lt(), me = 1u << lane;
+  // Peer-mask words alternate between two buffers by item parity: a word
+  // cleared by its group leader in item i is reused at item i + 2, after the
+  // warp barriers of item i + 1 have ordered the clear before the reuse.
+  uint32_t* wmask0 = s_mask + warp * kRadix;
+  uint32_t* wmask1 = s_mask + (kWarps + warp) * kRadix;
+  uint32_t* wcnt = s_wcnt + warp * kRadix;
+  const int wbase = warp * 32 * kIpt;
+  Item<K> it[kIpt];
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
-    const uint32_t pos = first + i;
-    const bool valid = pos < tile_n;
+    const int pos = wbase + i * 32 + lane;
+    const bool valid = uint32_t(pos) < tile_n;
     const K k = valid ? s_keys[pos] : K(0);
     const uint32_t d = dig(k, shift, mask);
-    if (valid) atomicAdd(&s_hist[d], 1u);  // tile digit counts (same-address adds combine)
-    if (valid) c += 1ull << (4 * (d & 15u));
-    if (kPacked) rec[i] = R(uint32_t(k) | (pos << 16));
-    else rec[i] = R(pos);
-  }
-#pragma unroll
-  for (int v = 0; v < kNib; ++v) s_cnt16[v * kBlock + tid] = uint16_t(field4(c, v));
-  __syncthreads();
-  scan_counts<kBlock>(s_cnt16, s_scan);
-  // Scatter A.  For packed records this overwrites the input keys, all of
-  // which were read before the barriers inside scan_counts.  The counter is
-  // replayed to recover each key's rank within the thread.
-  c = 0;
-#pragma unroll
-  for (int i = 0; i < kIpt; ++i) {
-    if (first + i < tile_n) {
-      const K k = kPacked ? K(uint32_t(rec[i]) & 0xFFFFu) : s_keys[first + i];
-      const uint32_t v = dig(k, shift, mask) & 15u;
-      s_rec[s_cnt16[v * kBlock + tid] + field4(c, v)] = rec[i];
-      c += 1ull << (4 * v);
+    uint32_t* wmask = (i & 1) ? wmask1 : wmask0;
+    if (valid) atomicAdd(&wmask[d], me);
+    __syncwarp();
+    const uint32_t peers = valid ? wmask[d] : 0u;
+    const uint32_t below = __popc(peers & lt);
+    __syncwarp();
+    uint32_t base = 0;
+    if (valid && below == 0) {
+      base = atomicAdd(&wcnt[d], uint32_t(__popc(peers)));
+      wmask[d] = 0;
     }
+    base = __shfl_sync(0xffffffffu, base, valid ? (__ffs(peers) - 1) : lane);
+    it[i].set(k, base + below);
   }
   __syncthreads();
-  // Step B (high nibble) over the low-nibble order.
-  c = 0;
-#pragma unroll
-  for (int i = 0; i < kIpt; ++i) {
-    const uint32_t pos = first + i;
-    const bool valid = pos < tile_n;
-    const R r = valid ? s_rec[pos] : R(0);
-    rec[i] = r;
-    const K k = kPacked ? K(uint32_t(r) & 0xFFFFu) : s_keys[uint32_t(r)];
-    if (valid) c += 1ull << (4 * ((dig(k, shift, mask) >> 4) & 15u));
-  }
-#pragma unroll
-  for (int v = 0; v < kNib; ++v) s_cnt16[v * kBlock + tid] = uint16_t(field4(c, v));
-  __syncthreads();
-  scan_counts<kBlock>(s_cnt16, s_scan);
-  c = 0;
-#pragma unroll
-  for (int i = 0; i < kIpt; ++i) {
-    if (first + i < tile_n) {
-      const K k = kPacked ? K(uint32_t(rec[i]) & 0xFFFFu) : s_keys[uint32_t(rec[i])];
-      const uint32_t v = (dig(k, shift, mask) >> 4) & 15u;
-      s_rec[s_cnt16[v * kBlock + tid] + field4(c, v)] = rec[i];
-      c += 1ull << (4 * v);
-    }
-  }
 
-  // 3. per-digit: publish the tile's counts, tile-exclusive digit starts
+  // 3. per-digit: warp prefixes, tile count, publish, tile-exclusive prefix
   const uint32_t tpc = a.tiles_per_chunk;
   const uint32_t chunk = tile / tpc;
   const uint32_t chunk_first = chunk * tpc;
   const bool first_in_chunk = tile == chunk_first;
   const bool last_in_chunk = (tile - chunk_first == tpc - 1) && (tile + 1 < gridDim.x);
   uint32_t* lb = a.lookback + uint64_t(tile) * kRadix;
-  uint32_t cnt = 0;
-  if (tid < kRadix) {
-    cnt = s_hist[tid];
-    st_relaxed_gpu(lb + tid, (first_in_chunk ? kFlagPrefix : kFlagAggregate) | cnt);
-  }
   {
-    const uint32_t ex = digit_excl_scan(cnt, s_scan);
-    if (tid < kRadix) s_excl[tid] = ex;
+    const int d = tid;
+    uint32_t run = 0;
+    if (d < kRadix) {
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = s_wcnt[w * kRadix + d];
+        s_wcnt[w * kRadix + d] = run;
+        run += c;
+      }
+      s_cnt[d] = run;
+      st_relaxed_gpu(lb + d, (first_in_chunk ? kFlagPrefix : kFlagAggregate) | run);
+    }
+    const uint32_t ex = digit_excl_scan<kBlock>(run, s_scan);
+    if (d < kRadix) {
+      s_excl[d] = ex;
+      // warp offsets become tile positions: one lookup per key in the permute
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) s_wcnt[w * kRadix + d] += ex;
+    }
+  }
+  __syncthreads();
+
+  // 4. permute into digit order in shared memory.  The peer-mask words are
+  // dead now; their space holds the sorted records: 16-bit keys packed with
+  // their source position, wider keys in place plus a 16-bit source position.
+  // Values stay where they are and are gathered once, in the output loop.
+  uint32_t* s_rec32 = s_mask;
+  uint16_t* s_src16 = reinterpret_cast<uint16_t*>(s_mask);
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    const int pos = wbase + i * 32 + lane;
+    if (uint32_t(pos) < tile_n) {
+      const K k = it[i].k();
+      const uint32_t p = s_wcnt[warp * kRadix + dig(k, shift, mask)] + it[i].r();
+      if (sizeof(K) == 2) {
+        s_rec32[p] = uint32_t(k) | (uint32_t(pos) << 16);
+      } else {
+        s_keys[p] = k;
+        s_src16[p] = uint16_t(pos);
+      }
+    }
   }
 
-  // 4. decoupled look-back for digit d = tid, kWindow predecessors per round trip
+  // 5. decoupled look-back for digit d = tid, kWindow predecessors per round trip
   if (tid < kRadix) {
     const int d = tid;
+    const uint32_t cnt = s_cnt[d];
     uint32_t excl = 0;
     if (!first_in_chunk) {
       uint32_t t = tile;  // tiles [chunk_first, t) are still to the left
@@ -377,15 +349,22 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   __syncthreads();
   if (last_in_chunk && tid == 0) st_release_gpu(a.chunk_flag + chunk + 1, 1u);
 
-  // 5. write the sorted tile out in digit runs
+  // 6. write the staged tile out in digit runs
   K* kout = const_cast<K*>(static_cast<const K*>(a.keys[dst]));
   uint32_t* vout = const_cast<uint32_t*>(a.vals[dst]);
   bool out_of_range = false;
 #pragma unroll 4
   for (uint32_t s = tid; s < tile_n; s += kBlock) {
-    const R r = s_rec[s];
-    const uint32_t from = kPacked ? (uint32_t(r) >> 16) : uint32_t(r);
-    const K k = kPacked ? K(uint32_t(r) & 0xFFFFu) : s_keys[from];
+    K k;
+    uint32_t from;
+    if (sizeof(K) == 2) {
+      const uint32_t r = s_rec32[s];
+      k = K(r & 0xFFFFu);
+      from = r >> 16;
+    } else {
+      k = s_keys[s];
+      from = s_src16[s];
+    }
     const uint64_t o = s_off[dig(k, shift, mask)] + s;
     if (o >= a.n) {  // only reachable after a timed-out wait; never write outside the output
       out_of_range = true;
