@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--log2n", type=int, default=LOG2N, help="keys per sort (log2); the workload is 28")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 32 GB arbitrary-precision configurations")
     return ap.parse_args()
 
 
@@ -152,6 +153,61 @@ def cpu_baseline(seconds: float = 10.0, log2n: int = 24):
     return {"value": keys / el / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
             "sample": f"5 distributions x 2^{log2n} keys (uint16 + uint32 index, p=16), repeated for {el:.1f} s, "
                       f"single-threaded C LSD counting sort on {os.cpu_count()} host cores (1 used)"}
+
+
+def run_secondary(fs, workloads, torch, stream, peak, reps: int = 3):
+    """The 32 GB arbitrary-precision configurations, keys only, out of place:
+    2^34 uint16 keys at 16-bit precision (the expand path), and 2^32 uint64 keys
+    at 16, 32 and 64 bits, each uniform and Zipf s=1.1 on the top 16 bits."""
+    out = []
+    cases = [(16, 34, 16, d) for d in ("uniform", "zipf1.1")]
+    cases += [(64, 32, p, d) for p in (16, 32, 64) for d in ("uniform", "zipf1.1")]
+    dtypes = {16: torch.uint16, 64: torch.uint64}
+    cur = None
+    for kb, log2n, p, dist in cases:
+        n = 1 << log2n
+        if cur is None or cur[0] != (kb, log2n, dist):
+            cur = None
+            torch.cuda.empty_cache()
+            keys = torch.empty(n, dtype=dtypes[kb], device="cuda")
+            table = workloads.table_for(dist, kb)
+            tdev = torch.from_numpy(table).cuda() if table is not None else None
+            workloads.generate_device(dist, keys.data_ptr(), n, kb, seed=0, stream=7,
+                                      cuda_stream=stream.cuda_stream,
+                                      table_dev_ptr=tdev.data_ptr() if tdev is not None else None)
+            kout = torch.empty_like(keys)
+            torch.cuda.synchronize()
+            cur = ((kb, log2n, dist), keys, kout)
+        _, keys, kout = cur
+        plan = fs.Plan(n, kb, has_values=False)
+        info = plan.describe(n, p, False)
+        plan.sort_out(keys, None, kout, None, precision_bits=p)  # warm-up
+        plan.sync()
+        fs.fsort_plan_set_timing(plan.handle, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plan.sort_out(keys, None, kout, None, precision_bits=p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.sync()
+        ms = e0.elapsed_time(e1) / reps
+        recs = fs.fsort_plan_timing_report(plan.handle, 4096)
+        kernels = {}
+        for r in recs:
+            k = r["kind"] + ("" if r["active"] else "_skipped")
+            kernels.setdefault(k, 0.0)
+            kernels[k] += r["ms"] / reps
+        plan.close()
+        alg = info["algorithmic_bytes"]
+        out.append({"workload": f"2^{log2n} uint{kb} keys-only, {p}-bit precision, {dist}, out of place",
+                    "gkeys_per_s": n / ms / 1e6, "ms": ms, "algorithmic_bytes": alg,
+                    "achieved_gbs": alg / ms / 1e6, "frac": alg / ms / 1e6 / peak,
+                    "path": "expand" if info["expand_path"] else f"{info['passes']} scatter passes",
+                    "kernel_ms": kernels})
+    del cur
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args, rank: int):
@@ -324,7 +380,11 @@ def main():
             "clocks": clocks,
         }
     plan.close()
-    del inputs
+    del inputs, keys_out, vals_out
+    torch.cuda.empty_cache()
+
+    if rank == 0 and not args.no_extra:
+        result["secondary"] = run_secondary(fs, workloads, torch, stream, peak)
 
     # End to end through the public host-buffer entry point (rank-local).
     e2e = None

@@ -199,23 +199,38 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   uint32_t* wcnt = s_wcnt + warp * kRadix;
   const int wbase = warp * 32 * kIpt;
   Item<K> it[kIpt];
+  // Locally skewed strips (presorted runs, constant digits): same-address
+  // mask additions serialise, while the hardware match.any is fast when a
+  // round has few distinct digits.  The warp picks the method for its whole
+  // strip from its first round (a speed choice only; both give the same ranks).
+  bool use_match;
+  {
+    const bool v0 = uint32_t(wbase + lane) < tile_n;
+    const uint32_t d0 = v0 ? dig(s_keys[wbase + lane], shift, mask) : 0xFFFFFFFFu;
+    const uint32_t lead = __shfl_sync(0xffffffffu, d0, 0);
+    use_match = __popc(__ballot_sync(0xffffffffu, d0 == lead)) >= 16;
+  }
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
     const int pos = wbase + i * 32 + lane;
     const bool valid = uint32_t(pos) < tile_n;
     const K k = valid ? s_keys[pos] : K(0);
     const uint32_t d = dig(k, shift, mask);
-    uint32_t* wmask = (i & 1) ? wmask1 : wmask0;
-    if (valid) atomicAdd(&wmask[d], me);
-    __syncwarp();
-    const uint32_t peers = valid ? wmask[d] : 0u;
-    const uint32_t below = __popc(peers & lt);
-    __syncwarp();
-    uint32_t base = 0;
-    if (valid && below == 0) {
-      base = atomicAdd(&wcnt[d], uint32_t(__popc(peers)));
-      wmask[d] = 0;
+    uint32_t peers;
+    if (use_match) {
+      peers = __match_any_sync(0xffffffffu, valid ? d : (0x100u + lane));  // invalid lanes match nobody
+      if (!valid) peers = 0;
+    } else {
+      uint32_t* wmask = (i & 1) ? wmask1 : wmask0;
+      if (valid) atomicAdd(&wmask[d], me);
+      __syncwarp();
+      peers = valid ? wmask[d] : 0u;
+      __syncwarp();
+      if (valid && (peers & lt) == 0) wmask[d] = 0;
     }
+    const uint32_t below = __popc(peers & lt);
+    uint32_t base = 0;
+    if (valid && below == 0) base = atomicAdd(&wcnt[d], uint32_t(__popc(peers)));
     base = __shfl_sync(0xffffffffu, base, valid ? (__ffs(peers) - 1) : lane);
     it[i].set(k, base + below);
   }
