@@ -69,6 +69,7 @@ typedef enum fsort_status {
 
 /* fsort_plan_desc.flags */
 #define FSORT_FLAG_HOST_IO 0x4u /* also allocate device buffers of max_n keys (+values) for fsort_sort_pairs_host */
+#define FSORT_FLAG_GRAPH 0x2u   /* batched sorts replay a captured CUDA graph when the batch shape repeats */
 
 typedef struct fsort_plan fsort_plan;
 
@@ -78,6 +79,7 @@ typedef struct fsort_plan_desc {
   int32_t has_values; /* 1 if calls may carry uint32_t values, else 0 */
   int32_t digit_bits; /* radix digit width of the scatter passes: 0 = library default (8), or 8 */
   uint32_t flags;     /* FSORT_FLAG_* */
+  uint32_t max_segments; /* largest segment count of fsort_sort_batch (0: no batched sorts), <= 65535 */
 } fsort_plan_desc;
 
 /* What a call with these arguments will do (filled by fsort_plan_describe). */
@@ -131,6 +133,47 @@ FSORT_API fsort_status fsort_sort_pairs_out(fsort_plan* plan, const void* keys_i
  * asynchronous DMA; pageable memory works but is slower. */
 FSORT_API fsort_status fsort_sort_pairs_host(fsort_plan* plan, void* keys_host, uint32_t* vals_host, uint64_t n,
                                    int key_bits, int precision_bits, void* stream);
+
+/* ---- batched sorts ---------------------------------------------------------
+ * Many independent stable sorts in one call (the paper's batch stream
+ * sorting: batches processed without pre-processing, batch size tuned to the
+ * device, Sec. III-C and IV-D).  Each segment is sorted in place, exactly as
+ * fsort_sort_pairs would sort it alone.  Segments of at most
+ * small_capacity keys are sorted whole in shared memory by one persistent
+ * kernel; larger segments share one histogram launch, one scan launch and one
+ * scatter launch per pass.  The two groups run concurrently on the device.
+ * Requirements: a plan created with max_segments >= count; the sum of the
+ * large segments' lengths (each rounded up to a multiple of 8) <= max_n;
+ * each segment shorter than 2^31 keys; large segments' key/value pointers
+ * 16-byte aligned; either every segment has values or none. */
+typedef struct fsort_segment {
+  void* keys;     /* device pointer, key_bits-wide keys */
+  uint32_t* vals; /* device pointer or NULL */
+  uint64_t n;
+} fsort_segment;
+
+typedef struct fsort_batch_config {
+  int32_t small_capacity;    /* 0 (no on-chip path), 1024, 2048 or 4096 keys */
+  int32_t small_ctas_per_sm; /* CTAs per SM of the persistent small-segment kernel (1..8) */
+  int32_t reserved[2];
+} fsort_batch_config;
+
+FSORT_API fsort_status fsort_sort_batch(fsort_plan* plan, const fsort_segment* segments, uint32_t count, int key_bits,
+                                        int precision_bits, void* stream);
+
+/* Set / read the batched path's configuration (defaults: 4096 keys, the most
+ * CTAs per SM that shared memory allows). */
+FSORT_API fsort_status fsort_batch_set_config(fsort_plan* plan, const fsort_batch_config* config);
+FSORT_API fsort_status fsort_batch_get_config(const fsort_plan* plan, fsort_batch_config* config);
+
+/* Autotuner: time fsort_sort_batch on these segments under each candidate
+ * configuration (small-segment capacity x CTAs per SM), keep the fastest in
+ * the plan and return it (and its time in ms, if best_ms is not NULL).  The
+ * segments are sorted in place several times; the result is the sorted batch.
+ * Synchronous. */
+FSORT_API fsort_status fsort_batch_autotune(fsort_plan* plan, const fsort_segment* segments, uint32_t count,
+                                            int key_bits, int precision_bits, void* stream,
+                                            fsort_batch_config* best, float* best_ms);
 
 /* ---- the hot-path steps one at a time (same kernels as the full sort) ---- */
 

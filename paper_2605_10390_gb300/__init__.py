@@ -10,7 +10,14 @@ Low-level names mirror the C ABI (``fsort_plan_create``, ``fsort_sort_pairs``,
 ...).  :class:`Plan` is a small convenience wrapper for torch tensors.
 """
 from ._binding import (  # noqa: F401
+    FSORT_FLAG_GRAPH,
     FSORT_FLAG_HOST_IO,
+    FsortBatchConfig,
+    FsortSegment,
+    fsort_batch_autotune,
+    fsort_batch_get_config,
+    fsort_batch_set_config,
+    fsort_sort_batch,
     FsortError,
     FsortKernelTime,
     KERNEL_KINDS,

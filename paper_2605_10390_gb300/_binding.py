@@ -11,6 +11,7 @@ _lock = threading.Lock()
 _lib = None
 
 FSORT_FLAG_HOST_IO = 0x4
+FSORT_FLAG_GRAPH = 0x2
 
 STATUS = {
     0: "FSORT_OK", 1: "FSORT_ERR_INVALID_ARG", 2: "FSORT_ERR_OOM", 3: "FSORT_ERR_CUDA", 4: "FSORT_ERR_TIMEOUT",
@@ -26,7 +27,19 @@ class FsortError(RuntimeError):
 
 class FsortPlanDesc(ctypes.Structure):
     _fields_ = [("max_n", ctypes.c_uint64), ("key_bits", ctypes.c_int32), ("has_values", ctypes.c_int32),
-                ("digit_bits", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+                ("digit_bits", ctypes.c_int32), ("flags", ctypes.c_uint32), ("max_segments", ctypes.c_uint32)]
+
+
+class FsortSegment(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+
+
+class FsortBatchConfig(ctypes.Structure):
+    _fields_ = [("small_capacity", ctypes.c_int32), ("small_ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+    def as_dict(self) -> dict:
+        return {"small_capacity": self.small_capacity, "small_ctas_per_sm": self.small_ctas_per_sm}
 
 
 class FsortPlanInfo(ctypes.Structure):
@@ -78,6 +91,11 @@ def load_library():
                                           ctypes.POINTER(ctypes.c_uint32)], st),
             "fsort_plan_device_flags": ([vp], ctypes.c_uint32),
             "fsort_scatter_pass_noalloc": ([vp, vp, vp, vp, u64, i32, i32, i32, vp], st),
+            "fsort_sort_batch": ([vp, ctypes.POINTER(FsortSegment), ctypes.c_uint32, i32, i32, vp], st),
+            "fsort_batch_set_config": ([vp, ctypes.POINTER(FsortBatchConfig)], st),
+            "fsort_batch_get_config": ([vp, ctypes.POINTER(FsortBatchConfig)], st),
+            "fsort_batch_autotune": ([vp, ctypes.POINTER(FsortSegment), ctypes.c_uint32, i32, i32, vp,
+                                      ctypes.POINTER(FsortBatchConfig), ctypes.POINTER(ctypes.c_float)], st),
             "fsort_status_string": ([i32], ctypes.c_char_p),
             "fsort_version": ([], i32),
         }
@@ -148,10 +166,11 @@ def _numel(t, n):
 
 # ---- C ABI, same names -----------------------------------------------------------
 
-def fsort_plan_create(max_n: int, key_bits: int, has_values: bool = True, digit_bits: int = 0, flags: int = 0):
+def fsort_plan_create(max_n: int, key_bits: int, has_values: bool = True, digit_bits: int = 0, flags: int = 0,
+                      max_segments: int = 0):
     lib = load_library()
     desc = FsortPlanDesc(max_n=max_n, key_bits=key_bits, has_values=int(bool(has_values)), digit_bits=digit_bits,
-                         flags=flags)
+                         flags=flags, max_segments=max_segments)
     h = ctypes.c_void_p()
     _check(lib.fsort_plan_create(ctypes.byref(desc), ctypes.byref(h)), "fsort_plan_create")
     return h.value
@@ -257,6 +276,47 @@ def fsort_plan_timing_report(plan, capacity: int = 8192) -> list:
              "n": r.n, "ms": r.ms} for r in buf[:count.value]]
 
 
+def _segments(segments):
+    """List of (keys, vals, n) (tensors or device addresses; vals may be None;
+    n may be None for tensors) -> ctypes array."""
+    arr = (FsortSegment * max(1, len(segments)))()
+    for i, seg in enumerate(segments):
+        keys, vals = seg[0], seg[1]
+        n = seg[2] if len(seg) > 2 and seg[2] is not None else _numel(keys, None)
+        arr[i] = FsortSegment(_ptr(keys), _ptr(vals), n)
+    return arr
+
+
+def fsort_sort_batch(plan, segments, key_bits: int, precision_bits=None, stream=None) -> None:
+    arr = _segments(segments)
+    _check(load_library().fsort_sort_batch(plan, arr, len(segments), key_bits,
+                                           key_bits if precision_bits is None else precision_bits, _stream(stream)),
+           "fsort_sort_batch")
+
+
+def fsort_batch_set_config(plan, small_capacity: int, small_ctas_per_sm: int) -> None:
+    cfg = FsortBatchConfig(small_capacity=small_capacity, small_ctas_per_sm=small_ctas_per_sm)
+    _check(load_library().fsort_batch_set_config(plan, ctypes.byref(cfg)), "fsort_batch_set_config")
+
+
+def fsort_batch_get_config(plan) -> dict:
+    cfg = FsortBatchConfig()
+    _check(load_library().fsort_batch_get_config(plan, ctypes.byref(cfg)), "fsort_batch_get_config")
+    return cfg.as_dict()
+
+
+def fsort_batch_autotune(plan, segments, key_bits: int, precision_bits=None, stream=None):
+    """Returns (best config dict, its time in ms)."""
+    arr = _segments(segments)
+    cfg = FsortBatchConfig()
+    ms = ctypes.c_float()
+    _check(load_library().fsort_batch_autotune(plan, arr, len(segments), key_bits,
+                                               key_bits if precision_bits is None else precision_bits,
+                                               _stream(stream), ctypes.byref(cfg), ctypes.byref(ms)),
+           "fsort_batch_autotune")
+    return cfg.as_dict(), ms.value
+
+
 def fsort_status_string(status: int) -> str:
     return load_library().fsort_status_string(status).decode()
 
@@ -268,10 +328,11 @@ def fsort_version() -> int:
 class Plan:
     """Owns a libfsort plan; sorts torch tensors on the current CUDA stream."""
 
-    def __init__(self, max_n: int, key_bits: int, has_values: bool = True, digit_bits: int = 0, flags: int = 0):
+    def __init__(self, max_n: int, key_bits: int, has_values: bool = True, digit_bits: int = 0, flags: int = 0,
+                 max_segments: int = 0):
         self.key_bits = key_bits
         self.has_values = has_values
-        self.handle = fsort_plan_create(max_n, key_bits, has_values, digit_bits, flags)
+        self.handle = fsort_plan_create(max_n, key_bits, has_values, digit_bits, flags, max_segments)
 
     def close(self) -> None:
         if self.handle:
@@ -299,6 +360,9 @@ class Plan:
 
     def sync(self) -> None:
         fsort_plan_sync(self.handle)
+
+    def sort_batch(self, segments, precision_bits=None, stream=None) -> None:
+        fsort_sort_batch(self.handle, segments, self.key_bits, precision_bits, stream)
 
     def describe(self, n: int, precision_bits=None, has_values=None) -> dict:
         return fsort_plan_describe(self.handle, n, self.key_bits,

@@ -71,6 +71,25 @@ struct fsort_plan {
   bool pending = false;
   uint32_t last_device_flags = 0;  // raw bits of the last latched device error
 
+  // batched sorts (max_segments > 0)
+  uint32_t max_segments = 0;
+  uint64_t max_hist_chunks = 0;
+  SegDesc* d_seg_large = nullptr;
+  SegDesc* d_seg_small = nullptr;
+  HistChunk* d_chunks = nullptr;
+  uint32_t* d_tile_seg = nullptr;
+  uint64_t* d_bhist = nullptr;   // [max_segments][passes][256], zero between calls
+  uint64_t* d_bbases = nullptr;
+  uint32_t* d_small_counter = nullptr;
+  SegDesc* h_seg_large = nullptr;  // pinned staging
+  SegDesc* h_seg_small = nullptr;
+  HistChunk* h_chunks = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  fsort_batch_config bcfg{};
+  cudaGraphExec_t gexec = nullptr;  // last captured batch
+  uint64_t gkey[10] = {};
+
   Timing timing;
 };
 
@@ -78,6 +97,7 @@ namespace {
 
 constexpr int kRadix = 256;
 constexpr size_t kCounterBytes = 256;  // two counters, padded
+constexpr uint64_t kBatchHistChunk = 262144;  // keys per work item of the segmented histogram
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -248,16 +268,246 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
   return finish_call(p, s);
 }
 
+// Batched sorts: build the segment lists on the host (pinned staging), then
+// enqueue the small-segment kernel on a side stream and the large-segment
+// passes on `s`, joined at the end.  With FSORT_FLAG_GRAPH and a non-default
+// stream, the enqueued work is captured once per batch shape and replayed: the
+// kernels read the segment lists from plan memory, so one graph serves every
+// batch of the same shape.
+struct BatchShape {
+  uint32_t n_large = 0, n_small = 0, n_chunks = 0, total_tiles = 0;
+  uint64_t alt_total = 0;
+  bool has_vals = false;
+};
+
+fsort_status build_batch(fsort_plan* p, const fsort_segment* segs, uint32_t count, int key_bits, BatchShape* out) {
+  const int cap = p->bcfg.small_capacity;
+  const uint64_t tile = uint64_t(p->tile);
+  BatchShape b;
+  int vals_state = -1;  // -1 unknown, 0 none, 1 all
+  for (uint32_t i = 0; i < count; ++i) {
+    const fsort_segment& g = segs[i];
+    if (g.n == 0) continue;
+    if (!g.keys || g.n >= (1ull << 31)) return FSORT_ERR_INVALID_ARG;
+    const int hv = g.vals != nullptr;
+    if (vals_state < 0) vals_state = hv;
+    if (vals_state != hv) return FSORT_ERR_INVALID_ARG;
+    if (hv && !p->desc.has_values) return FSORT_ERR_INVALID_ARG;
+    const uintptr_t ka = reinterpret_cast<uintptr_t>(g.keys);
+    if (ka % uintptr_t(key_bits / 8)) return FSORT_ERR_INVALID_ARG;
+    if (hv && (reinterpret_cast<uintptr_t>(g.vals) & 3u)) return FSORT_ERR_INVALID_ARG;
+    SegDesc d{g.keys, g.vals, g.n, 0, 0, 0};
+    if (cap > 0 && g.n <= uint64_t(cap)) {
+      p->h_seg_small[b.n_small++] = d;
+      continue;
+    }
+    if (!aligned16(g.keys) || (hv && !aligned16(g.vals))) return FSORT_ERR_INVALID_ARG;
+    d.alt_off = b.alt_total;
+    d.first_tile = b.total_tiles;
+    b.alt_total += (g.n + 7) / 8 * 8;  // keeps every segment's scratch 16-byte aligned
+    if (b.alt_total > p->desc.max_n) return FSORT_ERR_INVALID_ARG;
+    const uint64_t tiles = (g.n + tile - 1) / tile;
+    if (uint64_t(b.total_tiles) + tiles > p->max_tiles) return FSORT_ERR_INVALID_ARG;
+    b.total_tiles += uint32_t(tiles);
+    for (uint64_t st = 0; st < g.n; st += kBatchHistChunk) {
+      if (b.n_chunks >= p->max_hist_chunks) return FSORT_ERR_INVALID_ARG;
+      const uint64_t len = (g.n - st < kBatchHistChunk) ? g.n - st : kBatchHistChunk;
+      p->h_chunks[b.n_chunks++] = HistChunk{b.n_large, uint32_t(len), st};
+    }
+    p->h_seg_large[b.n_large++] = d;
+  }
+  b.has_vals = vals_state == 1;
+  *out = b;
+  return FSORT_OK;
+}
+
+cudaError_t enqueue_batch(fsort_plan* p, const BatchShape& b, int key_bits, int precision_bits, cudaStream_t s) {
+  const DigitPlan plan = make_plan(key_bits, precision_bits, p->digit_bits);
+  cudaError_t e = cudaSuccess;
+  if (b.n_large) e = cudaMemcpyAsync(p->d_seg_large, p->h_seg_large, sizeof(SegDesc) * b.n_large,
+                                     cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && b.n_small)
+    e = cudaMemcpyAsync(p->d_seg_small, p->h_seg_small, sizeof(SegDesc) * b.n_small, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && b.n_chunks)
+    e = cudaMemcpyAsync(p->d_chunks, p->h_chunks, sizeof(HistChunk) * b.n_chunks, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && b.n_small) e = cudaMemsetAsync(p->d_small_counter, 0, 4, s);
+  if (e == cudaSuccess && b.n_small) {
+    e = cudaEventRecord(p->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+    if (e == cudaSuccess)
+      e = launch_small_sort(p->d_seg_small, b.n_small, key_bits, b.has_vals, p->bcfg.small_capacity, plan,
+                            p->d_small_counter, p->bcfg.small_ctas_per_sm * p->sms, p->side);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->side);
+  }
+  if (e == cudaSuccess && b.n_large) {
+    e = launch_fill_tile_seg(p->d_seg_large, b.n_large, p->tile, p->d_tile_seg, s);
+    if (e == cudaSuccess)
+      e = launch_seg_histogram(p->d_seg_large, p->d_chunks, b.n_chunks, key_bits, plan, p->d_bhist, p->counters,
+                               kCounterBytes / 4 + uint64_t(b.total_tiles) * kRadix, s);
+    if (e == cudaSuccess) e = launch_seg_scan(p->d_bhist, p->d_bbases, b.n_large, plan.passes, s);
+    for (int j = 0; j < plan.passes && e == cudaSuccess; ++j) {
+      OnesweepArgs a{};
+      a.keys[kBufAlt] = p->alt_keys;
+      a.vals[kBufAlt] = b.has_vals ? p->alt_vals : nullptr;
+      a.n = b.alt_total;
+      a.shift = plan.shift[j];
+      a.mask = plan.mask[j];
+      a.lookback = p->lookback[j & 1];
+      a.tile_counter = p->counters + (j & 1);
+      const bool last = (j + 1 == plan.passes);
+      a.next_lookback = last ? nullptr : p->lookback[(j + 1) & 1];
+      a.next_counter = last ? nullptr : p->counters + ((j + 1) & 1);
+      a.chunk_base = p->d_bbases;
+      a.chunk_flag = nullptr;
+      a.sched = nullptr;
+      a.pass = j;
+      a.tiles_per_chunk = 1;
+      a.status = p->status;
+      a.segs = p->d_seg_large;
+      a.tile_seg = p->d_tile_seg;
+      a.passes = uint32_t(plan.passes);
+      a.total_tiles = b.total_tiles;
+      e = launch_onesweep(a, key_bits, b.has_vals, s);
+    }
+    if (e == cudaSuccess && (plan.passes & 1))
+      e = launch_seg_copy_back(p->d_seg_large, b.n_large, p->alt_keys, b.has_vals ? p->alt_vals : nullptr, key_bits,
+                               p->sms, s);
+  }
+  if (e == cudaSuccess && b.n_small) e = cudaStreamWaitEvent(s, p->ev_join, 0);
+  return e;
+}
+
+fsort_status run_batch(fsort_plan* p, const fsort_segment* segs, uint32_t count, int key_bits, int precision_bits,
+                       cudaStream_t s, bool allow_graph) {
+  // The pinned staging is rewritten below: let the previous call finish with it.
+  if (p->pending && cudaEventSynchronize(p->done) != cudaSuccess) return FSORT_ERR_CUDA;
+  BatchShape b;
+  fsort_status st = build_batch(p, segs, count, key_bits, &b);
+  if (st != FSORT_OK) return st;
+  if (!b.n_large && !b.n_small) return FSORT_OK;
+  const bool graph = allow_graph && (p->desc.flags & FSORT_FLAG_GRAPH) && s != nullptr;
+  if (!graph) {
+    const cudaError_t e = enqueue_batch(p, b, key_bits, precision_bits, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return finish_call(p, s);
+  }
+  const uint64_t key[10] = {b.n_large, b.n_small, b.n_chunks, b.total_tiles, b.alt_total, uint64_t(b.has_vals),
+                            uint64_t(key_bits) << 8 | uint64_t(precision_bits), uint64_t(p->bcfg.small_capacity),
+                            uint64_t(p->bcfg.small_ctas_per_sm), reinterpret_cast<uint64_t>(s)};
+  if (!p->gexec || std::memcmp(key, p->gkey, sizeof(key)) != 0) {
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return from_cuda(e);
+    const cudaError_t ee = enqueue_batch(p, b, key_bits, precision_bits, s);
+    e = cudaStreamEndCapture(s, &g);
+    if (ee != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return FSORT_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&p->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      p->gexec = nullptr;
+      return from_cuda(e);
+    }
+    std::memcpy(p->gkey, key, sizeof(key));
+  }
+  const cudaError_t e = cudaGraphLaunch(p->gexec, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  return finish_call(p, s);
+}
+
 }  // namespace
 
 extern "C" {
+
+fsort_status fsort_sort_batch(fsort_plan* plan, const fsort_segment* segments, uint32_t count, int key_bits,
+                              int precision_bits, void* stream) {
+  if (!plan || !plan->max_segments) return FSORT_ERR_INVALID_ARG;
+  if (count > plan->max_segments || (count && !segments)) return FSORT_ERR_INVALID_ARG;
+  fsort_status st = check_call(plan, 0, key_bits, precision_bits, false);
+  if (st != FSORT_OK) return st;
+  if (count == 0) return FSORT_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = take_latched(plan, false, s);
+  if (st != FSORT_OK) return st;
+  return run_batch(plan, segments, count, key_bits, precision_bits, s, true);
+}
+
+fsort_status fsort_batch_set_config(fsort_plan* plan, const fsort_batch_config* config) {
+  if (!plan || !config || !plan->max_segments) return FSORT_ERR_INVALID_ARG;
+  const int c = config->small_capacity;
+  if (c != 0 && c != 1024 && c != 2048 && c != 4096) return FSORT_ERR_INVALID_ARG;
+  if (config->small_ctas_per_sm < 1 || config->small_ctas_per_sm > 8) return FSORT_ERR_INVALID_ARG;
+  if (c && config->small_ctas_per_sm > small_sort_ctas_per_sm(plan->desc.key_bits, plan->desc.has_values != 0, c))
+    return FSORT_ERR_INVALID_ARG;  // more CTAs than shared memory holds at once
+  plan->bcfg = *config;
+  return FSORT_OK;
+}
+
+fsort_status fsort_batch_get_config(const fsort_plan* plan, fsort_batch_config* config) {
+  if (!plan || !config || !plan->max_segments) return FSORT_ERR_INVALID_ARG;
+  *config = plan->bcfg;
+  return FSORT_OK;
+}
+
+fsort_status fsort_batch_autotune(fsort_plan* plan, const fsort_segment* segments, uint32_t count, int key_bits,
+                                  int precision_bits, void* stream, fsort_batch_config* best, float* best_ms) {
+  if (!plan || !plan->max_segments || !best) return FSORT_ERR_INVALID_ARG;
+  if (count > plan->max_segments || (count && !segments)) return FSORT_ERR_INVALID_ARG;
+  fsort_status st = check_call(plan, 0, key_bits, precision_bits, false);
+  if (st != FSORT_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = take_latched(plan, true, s);
+  if (st != FSORT_OK) return st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return FSORT_ERR_CUDA;
+  const fsort_batch_config saved = plan->bcfg;
+  fsort_batch_config winner = saved;
+  float winner_ms = -1.f;
+  const bool hv = plan->desc.has_values != 0;
+  for (int cap : {0, 1024, 2048, 4096}) {
+    const int most = cap ? small_sort_ctas_per_sm(key_bits, hv, cap) : 1;
+    for (int ctas : {most, (most + 1) / 2}) {
+      if (cap == 0 && ctas != most) continue;
+      plan->bcfg.small_capacity = cap;
+      plan->bcfg.small_ctas_per_sm = ctas;
+      st = run_batch(plan, segments, count, key_bits, precision_bits, s, false);  // warm-up
+      if (st == FSORT_OK && cudaEventRecord(e0, s) != cudaSuccess) st = FSORT_ERR_CUDA;
+      if (st == FSORT_OK) st = run_batch(plan, segments, count, key_bits, precision_bits, s, false);
+      if (st == FSORT_OK && cudaEventRecord(e1, s) != cudaSuccess) st = FSORT_ERR_CUDA;
+      if (st == FSORT_OK && cudaEventSynchronize(e1) != cudaSuccess) st = FSORT_ERR_CUDA;
+      float ms = 0.f;
+      if (st == FSORT_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = FSORT_ERR_CUDA;
+      if (st != FSORT_OK) break;
+      if (winner_ms < 0.f || ms < winner_ms) {
+        winner_ms = ms;
+        winner = plan->bcfg;
+      }
+    }
+    if (st != FSORT_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan->bcfg = (st == FSORT_OK) ? winner : saved;
+  if (st != FSORT_OK) return st;
+  *best = winner;
+  if (best_ms) *best_ms = winner_ms;
+  return take_latched(plan, true, s);
+}
+
 
 fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_plan) {
   if (!desc || !out_plan) return FSORT_ERR_INVALID_ARG;
   if (!valid_key_bits(desc->key_bits) || desc->max_n < 1) return FSORT_ERR_INVALID_ARG;
   if (desc->has_values != 0 && desc->has_values != 1) return FSORT_ERR_INVALID_ARG;
   if (desc->digit_bits != 0 && desc->digit_bits != 8) return FSORT_ERR_UNSUPPORTED;
-  if (desc->flags & ~FSORT_FLAG_HOST_IO) return FSORT_ERR_INVALID_ARG;
+  if (desc->flags & ~(FSORT_FLAG_HOST_IO | FSORT_FLAG_GRAPH)) return FSORT_ERR_INVALID_ARG;
   if (desc->max_n > (1ull << 36)) return FSORT_ERR_UNSUPPORTED;
 
   fsort_plan* p = new (std::nothrow) fsort_plan();
@@ -275,6 +525,10 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   p->chunk_keys = chunk_keys_for(desc->key_bits);
   p->max_tiles = (n + p->tile - 1) / p->tile;
   p->max_chunks = (n + p->chunk_keys - 1) / p->chunk_keys;
+  if (desc->max_segments > 0) {
+    p->max_segments = desc->max_segments;
+    p->max_tiles += desc->max_segments;  // every batch segment may add one partial tile
+  }
 
   // Carve the scratch out of one allocation.
   size_t off = 0;
@@ -294,6 +548,23 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   const size_t o_sched = take(sizeof(Schedule));
   const size_t o_status = take(sizeof(uint32_t));
   size_t o_lpart = 0, o_lspill = 0, o_lcnt = 0, o_loff = 0;
+  const bool batch = desc->max_segments > 0;
+  if (desc->max_segments > 65535) {
+    delete p;
+    return FSORT_ERR_INVALID_ARG;
+  }
+  const int pmax = desc->key_bits / 8;
+  size_t o_bsl = 0, o_bss = 0, o_bch = 0, o_bts = 0, o_bh = 0, o_bb = 0, o_bctr = 0;
+  if (batch) {
+    p->max_hist_chunks = n / kBatchHistChunk + desc->max_segments + 1;
+    o_bsl = take(size_t(desc->max_segments) * sizeof(SegDesc));
+    o_bss = take(size_t(desc->max_segments) * sizeof(SegDesc));
+    o_bch = take(size_t(p->max_hist_chunks) * sizeof(HistChunk));
+    o_bts = take(size_t(p->max_tiles) * 4);
+    o_bh = take(size_t(desc->max_segments) * pmax * kRadix * 8);
+    o_bb = take(size_t(desc->max_segments) * pmax * kRadix * 8);
+    o_bctr = take(4);
+  }
   const bool leaf = desc->key_bits == 16;
   if (leaf) {
     o_lpart = take(size_t(leaf_hist_grid(p->sms)) * 32768 * 4);
@@ -325,6 +596,15 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   p->chunk_flag = reinterpret_cast<uint32_t*>(w + o_cflag);
   p->sched = reinterpret_cast<Schedule*>(w + o_sched);
   p->status = reinterpret_cast<uint32_t*>(w + o_status);
+  if (batch) {
+    p->d_seg_large = reinterpret_cast<SegDesc*>(w + o_bsl);
+    p->d_seg_small = reinterpret_cast<SegDesc*>(w + o_bss);
+    p->d_chunks = reinterpret_cast<HistChunk*>(w + o_bch);
+    p->d_tile_seg = reinterpret_cast<uint32_t*>(w + o_bts);
+    p->d_bhist = reinterpret_cast<uint64_t*>(w + o_bh);
+    p->d_bbases = reinterpret_cast<uint64_t*>(w + o_bb);
+    p->d_small_counter = reinterpret_cast<uint32_t*>(w + o_bctr);
+  }
   if (leaf) {
     p->leaf_part = reinterpret_cast<uint32_t*>(w + o_lpart);
     p->leaf_spill = reinterpret_cast<uint64_t*>(w + o_lspill);
@@ -339,18 +619,29 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   e = cudaMemset(p->hist, 0, hist_bytes);
   if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(p->counters, 0, kCounterBytes);
+  if (e == cudaSuccess && batch) e = cudaMemset(p->d_bhist, 0, size_t(desc->max_segments) * pmax * kRadix * 8);
+  if (e == cudaSuccess && batch)
+    e = cudaMallocHost(reinterpret_cast<void**>(&p->h_seg_large), sizeof(SegDesc) * desc->max_segments);
+  if (e == cudaSuccess && batch)
+    e = cudaMallocHost(reinterpret_cast<void**>(&p->h_seg_small), sizeof(SegDesc) * desc->max_segments);
+  if (e == cudaSuccess && batch)
+    e = cudaMallocHost(reinterpret_cast<void**>(&p->h_chunks), sizeof(HistChunk) * p->max_hist_chunks);
+  if (e == cudaSuccess && batch) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess && batch) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && batch) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&p->h_status), sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     cudaGetLastError();
-    if (p->h_status) cudaFreeHost(p->h_status);
-    if (p->done) cudaEventDestroy(p->done);
-    cudaFree(p->ws);
-    delete p;
+    fsort_plan_destroy(p);
     return FSORT_ERR_CUDA;
   }
   *p->h_status = 0;
+  if (batch) {
+    p->bcfg.small_capacity = 4096;
+    p->bcfg.small_ctas_per_sm = small_sort_ctas_per_sm(desc->key_bits, desc->has_values != 0, 4096);
+  }
   *out_plan = p;
   return FSORT_OK;
 }
@@ -359,6 +650,14 @@ fsort_status fsort_plan_destroy(fsort_plan* plan) {
   if (!plan) return FSORT_OK;
   fsort_status st = FSORT_OK;
   if (plan->pending && cudaEventSynchronize(plan->done) != cudaSuccess) st = FSORT_ERR_CUDA;
+  if (plan->side) cudaStreamSynchronize(plan->side);
+  if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
+  if (plan->side) cudaStreamDestroy(plan->side);
+  if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+  if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+  if (plan->h_seg_large) cudaFreeHost(plan->h_seg_large);
+  if (plan->h_seg_small) cudaFreeHost(plan->h_seg_small);
+  if (plan->h_chunks) cudaFreeHost(plan->h_chunks);
   if (plan->done) cudaEventDestroy(plan->done);
   if (plan->h_status) cudaFreeHost(plan->h_status);
   fsort_plan_set_timing(plan, 0);

@@ -258,19 +258,30 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
   extern __shared__ uint32_t hw[];
   for (int i = threadIdx.x; i < kLeafWords; i += blockDim.x) hw[i] = 0;
   __syncthreads();
-  // Rounds are dealt to CTAs round-robin over the whole input.
+  // Rounds are dealt to CTAs round-robin over the whole input; the next
+  // round's keys are loaded into registers before this round's drain, so the
+  // loads overlap the drain and its barriers.
   const uint64_t rounds = (n + kLeafRound - 1) / kLeafRound;
   auto add = [&](uint32_t k) { atomicAdd(&hw[k >> 1], 1u << ((k & 1) * 16)); };
-  for (uint64_t r = blockIdx.x; r < rounds; r += gridDim.x) {
-    const uint64_t base = r * kLeafRound;
-    if (base + kLeafRound <= n) {
-      uint4 q[kLeafVecPerThread];
+  auto full = [&](uint64_t r) { return (r + 1) * kLeafRound <= n; };
+  uint4 q[kLeafVecPerThread];
+  auto load = [&](uint64_t r) {
 #pragma unroll
-      for (int u = 0; u < kLeafVecPerThread; ++u)
-        q[u] = __ldg(reinterpret_cast<const uint4*>(keys + base) + u * kLeafThreads + threadIdx.x);
+    for (int u = 0; u < kLeafVecPerThread; ++u)
+      q[u] = __ldg(reinterpret_cast<const uint4*>(keys + r * kLeafRound) + u * kLeafThreads + threadIdx.x);
+  };
+  uint64_t r = blockIdx.x;
+  if (r < rounds && full(r)) load(r);
+  for (; r < rounds; r += gridDim.x) {
+    const uint64_t next = r + gridDim.x;
+    if (full(r)) {
+      uint4 cur[kLeafVecPerThread];
+#pragma unroll
+      for (int u = 0; u < kLeafVecPerThread; ++u) cur[u] = q[u];
+      if (next < rounds && full(next)) load(next);
 #pragma unroll
       for (int u = 0; u < kLeafVecPerThread; ++u) {
-        const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+        const uint32_t w[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           add(w[e] & 0xFFFFu);
@@ -278,7 +289,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
         }
       }
     } else {
-      for (uint64_t i = base + threadIdx.x; i < n; i += blockDim.x) add(keys[i]);
+      for (uint64_t i = r * kLeafRound + threadIdx.x; i < n; i += blockDim.x) add(keys[i]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kLeafWords; i += blockDim.x) {
@@ -315,13 +326,14 @@ __global__ void leaf_reduce_kernel(const uint32_t* __restrict__ partials, const 
 }
 
 // ---------------------------------------------------------------- K4 -------
-// Output-centric: each CTA covers kExpandPerCta consecutive output positions.
-// Thread 0 finds the bins of the first and last position by binary search
-// over the 65,537 bin boundaries; each thread then writes 8 consecutive keys
-// (one 16-byte store) after locating its first key's bin inside that range.
+// Output-centric and persistent: CTA c writes one contiguous stretch of the
+// output.  Thread 0 finds the bins of the stretch's first and last position by
+// binary search over the 65,536 bin starts; each thread then writes 8
+// consecutive keys per step (one 16-byte store, the warp's stores contiguous)
+// and follows the bin boundary forward as its positions advance.
 constexpr int kExpandThreads = 256;
 constexpr int kExpandPerThread = 8;
-constexpr int kExpandPerCta = kExpandThreads * kExpandPerThread * 4;
+constexpr uint64_t kExpandStep = uint64_t(kExpandThreads) * kExpandPerThread;  // keys per CTA step
 
 __device__ __forceinline__ uint32_t bin_of(const uint64_t* off, uint32_t lo, uint32_t hi, uint64_t pos) {
   // largest v in [lo, hi] with off[v] <= pos (off ascending, off[lo] <= pos)
@@ -333,43 +345,51 @@ __device__ __forceinline__ uint32_t bin_of(const uint64_t* off, uint32_t lo, uin
 }
 
 __global__ void __launch_bounds__(kExpandThreads) expand_kernel(const uint64_t* __restrict__ offsets,
-                                                                uint16_t* __restrict__ out, uint64_t n) {
+                                                                uint16_t* __restrict__ out, uint64_t n,
+                                                                uint64_t per_cta) {
   __shared__ uint32_t s_range[2];
-  const uint64_t c0 = uint64_t(blockIdx.x) * kExpandPerCta;
-  const uint64_t c1 = (c0 + kExpandPerCta < n) ? c0 + kExpandPerCta : n;
+  const uint64_t c0 = uint64_t(blockIdx.x) * per_cta;
+  if (c0 >= n) return;
+  const uint64_t c1 = (c0 + per_cta < n) ? c0 + per_cta : n;
   if (threadIdx.x == 0) {
     s_range[0] = bin_of(offsets, 0, 65535, c0);
     s_range[1] = bin_of(offsets, s_range[0], 65535, c1 - 1);
   }
   __syncthreads();
   const uint32_t b_lo = s_range[0], b_hi = s_range[1];
-  for (uint64_t p0 = c0 + uint64_t(threadIdx.x) * kExpandPerThread; p0 < c1;
-       p0 += uint64_t(kExpandThreads) * kExpandPerThread) {
-    uint32_t b = bin_of(offsets, b_lo, b_hi, p0);
-    uint64_t next = (b < 65535) ? offsets[b + 1] : n;
-    if (p0 + kExpandPerThread <= c1) {
+  uint64_t p0 = c0 + uint64_t(threadIdx.x) * kExpandPerThread;
+  if (p0 >= c1) return;
+  uint32_t b = bin_of(offsets, b_lo, b_hi, p0);
+  uint64_t next = (b < 65535) ? offsets[b + 1] : n;
+  for (; p0 < c1; p0 += kExpandStep) {
+    while (p0 >= next) {  // positions only move forward: walk to the bin holding p0
+      ++b;
+      next = (b < 65535) ? offsets[b + 1] : n;
+    }
+    if (p0 + kExpandPerThread <= c1 && p0 + kExpandPerThread <= next) {
+      const uint32_t v2 = uint32_t(b) | (uint32_t(b) << 16);  // all 8 keys in one bin
+      *reinterpret_cast<uint4*>(out + p0) = make_uint4(v2, v2, v2, v2);
+    } else {
       uint16_t v[kExpandPerThread];
+      uint32_t bb = b;
+      uint64_t nx = next;
 #pragma unroll
       for (int e = 0; e < kExpandPerThread; ++e) {
-        while (p0 + e >= next) {
-          ++b;
-          next = (b < 65535) ? offsets[b + 1] : n;
+        while (p0 + e >= nx && bb < 65535) {
+          ++bb;
+          nx = (bb < 65535) ? offsets[bb + 1] : n;
         }
-        v[e] = uint16_t(b);
+        v[e] = uint16_t(bb);
       }
-      uint4 q;
-      q.x = uint32_t(v[0]) | (uint32_t(v[1]) << 16);
-      q.y = uint32_t(v[2]) | (uint32_t(v[3]) << 16);
-      q.z = uint32_t(v[4]) | (uint32_t(v[5]) << 16);
-      q.w = uint32_t(v[6]) | (uint32_t(v[7]) << 16);
-      *reinterpret_cast<uint4*>(out + p0) = q;
-    } else {
-      for (uint64_t p = p0; p < c1; ++p) {
-        while (p >= next) {
-          ++b;
-          next = (b < 65535) ? offsets[b + 1] : n;
-        }
-        out[p] = uint16_t(b);
+      if (p0 + kExpandPerThread <= c1) {
+        uint4 qv;
+        qv.x = uint32_t(v[0]) | (uint32_t(v[1]) << 16);
+        qv.y = uint32_t(v[2]) | (uint32_t(v[3]) << 16);
+        qv.z = uint32_t(v[4]) | (uint32_t(v[5]) << 16);
+        qv.w = uint32_t(v[6]) | (uint32_t(v[7]) << 16);
+        *reinterpret_cast<uint4*>(out + p0) = qv;
+      } else {
+        for (int e = 0; e < kExpandPerThread && p0 + e < c1; ++e) out[p0 + e] = v[e];
       }
     }
   }
@@ -495,8 +515,16 @@ cudaError_t launch_leaf_reduce(const uint32_t* partials, const uint64_t* spill, 
 
 cudaError_t launch_expand(const uint64_t* offsets, uint16_t* keys_out, uint64_t n, cudaStream_t stream) {
   if (!n) return cudaSuccess;
-  const uint64_t grid = (n + kExpandPerCta - 1) / kExpandPerCta;
-  expand_kernel<<<unsigned(grid), kExpandThreads, 0, stream>>>(offsets, keys_out, n);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  // Eight CTAs per SM, each a stretch that is a whole number of 16-byte steps.
+  const uint64_t want = uint64_t(sms) * 8;
+  uint64_t per = (n + want - 1) / want;
+  per = (per + kExpandStep - 1) / kExpandStep * kExpandStep;
+  const uint64_t grid = (n + per - 1) / per;
+  expand_kernel<<<unsigned(grid), kExpandThreads, 0, stream>>>(offsets, keys_out, n, per);
   return cudaGetLastError();
 }
 

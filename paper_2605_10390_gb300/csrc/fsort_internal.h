@@ -40,6 +40,16 @@ cudaError_t launch_scan_schedule(uint64_t* hist, uint64_t* chunk_base, uint32_t*
 // Row-wise exclusive scan, one CTA per row (bins <= 65536).
 cudaError_t launch_scan_rows(const uint64_t* in, uint64_t* out, uint64_t rows, uint64_t bins, cudaStream_t stream);
 
+// One segment of a batched sort (segmented scatter mode of K3).
+struct SegDesc {
+  void* keys;           // the caller's keys (sorted in place)
+  uint32_t* vals;       // the caller's values, or null
+  uint64_t n;           // keys in the segment
+  uint64_t alt_off;     // element offset of the segment's ping-pong space in the plan scratch
+  uint32_t first_tile;  // global index of the segment's first scatter tile
+  uint32_t pad;
+};
+
 // K3: one stable scatter pass.
 struct OnesweepArgs {
   const void* keys[3];     // by BufSel: input, plan scratch, output
@@ -58,6 +68,14 @@ struct OnesweepArgs {
   int32_t pass;
   uint32_t tiles_per_chunk;
   uint32_t* status;
+  // Segmented mode (segs != null): global tiles of many independent segments;
+  // tile t belongs to segment tile_seg[t]; even passes read the segment's own
+  // buffers and write its scratch space, odd passes the reverse; the segment's
+  // 64-bit digit bases are chunk_base[seg * passes * 256 + pass * 256 + d].
+  const SegDesc* segs;
+  const uint32_t* tile_seg;
+  uint32_t passes;
+  uint32_t total_tiles;  // segmented mode: tiles over all segments (the grid)
 };
 cudaError_t launch_onesweep(const OnesweepArgs& args, int key_bits, bool has_vals, cudaStream_t stream);
 
@@ -76,5 +94,34 @@ cudaError_t launch_leaf_reduce(const uint32_t* partials, const uint64_t* spill, 
                                cudaStream_t stream);
 // K4: keys_out[offsets[v] .. offsets[v] + counts[v]) = v.
 cudaError_t launch_expand(const uint64_t* offsets, uint16_t* keys_out, uint64_t n, cudaStream_t stream);
+
+// ---- batched sorts (fsort_batch.cu) ----
+// Small segments sorted entirely in shared memory by one CTA each.
+// capacity: 1024, 2048 or 4096 keys.  segs[0..count) all have n <= capacity.
+// counter: a device word, zero on entry (work distribution).
+cudaError_t launch_small_sort(const SegDesc* segs, uint32_t count, int key_bits, bool has_vals, int capacity,
+                              const DigitPlan& plan, uint32_t* counter, int ctas, cudaStream_t stream);
+int small_sort_ctas_per_sm(int key_bits, bool has_vals, int capacity);
+
+// One entry of the segmented histogram's work list.
+struct HistChunk {
+  uint32_t seg;
+  uint32_t len;
+  uint64_t start;
+};
+// Per-segment per-pass digit histograms: hist[(seg * passes + j) * 256 + d]
+// (accumulated; zero on entry).  Also zeroes clear_words words at `clear`.
+cudaError_t launch_seg_histogram(const SegDesc* segs, const HistChunk* chunks, uint32_t nchunks, int key_bits,
+                                 const DigitPlan& plan, uint64_t* hist, uint32_t* clear, uint64_t clear_words,
+                                 cudaStream_t stream);
+// Per segment and pass: exclusive scan of the histogram into 64-bit bases
+// (same layout); leaves hist zero.
+cudaError_t launch_seg_scan(uint64_t* hist, uint64_t* bases, uint32_t nsegs, int passes, cudaStream_t stream);
+// tile_seg[t] = segment of global tile t.
+cudaError_t launch_fill_tile_seg(const SegDesc* segs, uint32_t nsegs, int tile_keys, uint32_t* tile_seg,
+                                 cudaStream_t stream);
+// Copy each segment's scratch space back to its own buffers (odd pass count).
+cudaError_t launch_seg_copy_back(const SegDesc* segs, uint32_t nsegs, const void* alt_keys,
+                                 const uint32_t* alt_vals, int key_bits, int sms, cudaStream_t stream);
 
 }  // namespace fsort

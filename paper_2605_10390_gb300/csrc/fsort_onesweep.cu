@@ -32,6 +32,7 @@
 
 #include "fsort_dev.cuh"
 #include "fsort_internal.h"
+#include "fsort_rank.cuh"
 
 namespace fsort {
 namespace {
@@ -68,52 +69,6 @@ struct SmemLayout {
   static constexpr size_t kBar = kScan + 16 * 4;
   static constexpr size_t kTileId = kBar + 8;
   static constexpr size_t kBytes = kTileId + 16;
-};
-
-// Exclusive scan of x over threads 0..255 (the digits); every thread of the
-// block must call it (it contains a barrier).
-template <int kBlock>
-__device__ __forceinline__ uint32_t digit_excl_scan(uint32_t x, uint32_t* s_warp) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t inc = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31 && warp < kRadix / 32) s_warp[warp] = inc;
-  __syncthreads();
-  uint32_t before = 0;
-#pragma unroll
-  for (int w = 0; w < kRadix / 32; ++w)
-    if (w < warp) before += s_warp[w];
-  return before + inc - x;
-}
-
-template <typename K>
-__device__ __forceinline__ uint32_t dig(K k, uint32_t shift, uint32_t mask) {
-  if (sizeof(K) <= 4) return (uint32_t(k) >> shift) & mask;
-  return uint32_t(uint64_t(k) >> shift) & mask;
-}
-
-// Per-item key and in-warp rank.  16-bit keys share one register with their
-// rank (ranks stay below the tile size); wider keys keep two.
-template <typename K>
-struct Item {
-  K key;
-  uint32_t rank;
-  __device__ __forceinline__ void set(K k, uint32_t r) { key = k; rank = r; }
-  __device__ __forceinline__ K k() const { return key; }
-  __device__ __forceinline__ uint32_t r() const { return rank; }
-  __device__ __forceinline__ void set_r(uint32_t r) { rank = r; }
-};
-template <>
-struct Item<uint16_t> {
-  uint32_t packed;
-  __device__ __forceinline__ void set(uint16_t k, uint32_t r) { packed = uint32_t(k) | (r << 16); }
-  __device__ __forceinline__ uint16_t k() const { return uint16_t(packed & 0xFFFFu); }
-  __device__ __forceinline__ uint32_t r() const { return packed >> 16; }
-  __device__ __forceinline__ void set_r(uint32_t r) { packed = (packed & 0xFFFFu) | (r << 16); }
 };
 
 template <typename K, bool kVals>
@@ -168,10 +123,45 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
     if (tid == 0) atomicOr(a.status, kDevBadTile);
     return;
   }
-  const uint64_t t0 = uint64_t(tile) * kTile;
-  const uint32_t tile_n = uint32_t((a.n - t0 < uint64_t(kTile)) ? (a.n - t0) : uint64_t(kTile));
-  const K* kin = static_cast<const K*>(a.keys[src]);
-  const uint32_t* vin = a.vals[src];
+  // Where this tile's keys live, where they go, and its look-back chunk.
+  const K* kin;
+  const uint32_t* vin;
+  K* kout;
+  uint32_t* vout;
+  uint64_t t0, n_bound;
+  uint32_t chunk, chunk_first;
+  bool last_in_chunk;
+  const unsigned long long* base_row;  // 64-bit digit bases of this tile's chunk, if already known
+  if (a.segs) {
+    const uint32_t seg = a.tile_seg[tile];
+    const SegDesc sd = a.segs[seg];
+    K* user_k = static_cast<K*>(sd.keys);
+    K* alt_k = const_cast<K*>(static_cast<const K*>(a.keys[kBufAlt])) + sd.alt_off;
+    uint32_t* alt_v = kVals ? const_cast<uint32_t*>(a.vals[kBufAlt]) + sd.alt_off : nullptr;
+    const bool even = (a.pass & 1) == 0;
+    kin = even ? user_k : alt_k;
+    vin = even ? sd.vals : alt_v;
+    kout = even ? alt_k : user_k;
+    vout = even ? alt_v : sd.vals;
+    t0 = uint64_t(tile - sd.first_tile) * kTile;
+    n_bound = sd.n;
+    chunk = seg;
+    chunk_first = sd.first_tile;
+    last_in_chunk = false;  // a segment is one chunk (< 2^30 keys)
+    base_row = reinterpret_cast<const unsigned long long*>(a.chunk_base) + (uint64_t(seg) * a.passes + a.pass) * kRadix;
+  } else {
+    kin = static_cast<const K*>(a.keys[src]);
+    vin = a.vals[src];
+    kout = const_cast<K*>(static_cast<const K*>(a.keys[dst]));
+    vout = const_cast<uint32_t*>(a.vals[dst]);
+    t0 = uint64_t(tile) * kTile;
+    n_bound = a.n;
+    chunk = tile / a.tiles_per_chunk;
+    chunk_first = chunk * a.tiles_per_chunk;
+    last_in_chunk = (tile - chunk_first == a.tiles_per_chunk - 1) && (tile + 1 < gridDim.x);
+    base_row = chunk == 0 ? reinterpret_cast<const unsigned long long*>(a.chunk_base) : nullptr;
+  }
+  const uint32_t tile_n = uint32_t((n_bound - t0 < uint64_t(kTile)) ? (n_bound - t0) : uint64_t(kTile));
 
   // 1. stage the tile: bulk copies for the 16-byte-aligned body, plain loads
   // for a ragged end.
@@ -190,7 +180,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
 
   // 2. stable in-warp ranks
   const uint32_t shift = a.shift, mask = a.mask;
-  const uint32_t lt = lanemask_lt(), me = 1u << lane;
+  (void)lane;
   // Peer-mask words alternate between two buffers by item parity: a word
   // cleared by its group leader in item i is reused at item i + 2, after the
   // warp barriers of item i + 1 have ordered the clear before the reuse.
@@ -199,49 +189,11 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   uint32_t* wcnt = s_wcnt + warp * kRadix;
   const int wbase = warp * 32 * kIpt;
   Item<K> it[kIpt];
-  // Locally skewed strips (presorted runs, constant digits): same-address
-  // mask additions serialise, while the hardware match.any is fast when a
-  // round has few distinct digits.  The warp picks the method for its whole
-  // strip from its first round (a speed choice only; both give the same ranks).
-  bool use_match;
-  {
-    const bool v0 = uint32_t(wbase + lane) < tile_n;
-    const uint32_t d0 = v0 ? dig(s_keys[wbase + lane], shift, mask) : 0xFFFFFFFFu;
-    const uint32_t lead = __shfl_sync(0xffffffffu, d0, 0);
-    use_match = __popc(__ballot_sync(0xffffffffu, d0 == lead)) >= 16;
-  }
-#pragma unroll
-  for (int i = 0; i < kIpt; ++i) {
-    const int pos = wbase + i * 32 + lane;
-    const bool valid = uint32_t(pos) < tile_n;
-    const K k = valid ? s_keys[pos] : K(0);
-    const uint32_t d = dig(k, shift, mask);
-    uint32_t peers;
-    if (use_match) {
-      peers = __match_any_sync(0xffffffffu, valid ? d : (0x100u + lane));  // invalid lanes match nobody
-      if (!valid) peers = 0;
-    } else {
-      uint32_t* wmask = (i & 1) ? wmask1 : wmask0;
-      if (valid) atomicAdd(&wmask[d], me);
-      __syncwarp();
-      peers = valid ? wmask[d] : 0u;
-      __syncwarp();
-      if (valid && (peers & lt) == 0) wmask[d] = 0;
-    }
-    const uint32_t below = __popc(peers & lt);
-    uint32_t base = 0;
-    if (valid && below == 0) base = atomicAdd(&wcnt[d], uint32_t(__popc(peers)));
-    base = __shfl_sync(0xffffffffu, base, valid ? (__ffs(peers) - 1) : lane);
-    it[i].set(k, base + below);
-  }
+  rank_strip<K, kIpt>(s_keys, tile_n, wbase, shift, mask, wmask0, wmask1, wcnt, it);
   __syncthreads();
 
   // 3. per-digit: warp prefixes, tile count, publish, tile-exclusive prefix
-  const uint32_t tpc = a.tiles_per_chunk;
-  const uint32_t chunk = tile / tpc;
-  const uint32_t chunk_first = chunk * tpc;
   const bool first_in_chunk = tile == chunk_first;
-  const bool last_in_chunk = (tile - chunk_first == tpc - 1) && (tile + 1 < gridDim.x);
   uint32_t* lb = a.lookback + uint64_t(tile) * kRadix;
   {
     const int d = tid;
@@ -339,8 +291,8 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
     }
     // 64-bit base of this digit in this chunk.
     unsigned long long base;
-    if (chunk == 0) {
-      base = a.chunk_base[d];
+    if (base_row) {
+      base = base_row[d];
     } else {
       const uint32_t* flag = a.chunk_flag + chunk;
       if (!ld_acquire_gpu(flag)) {
@@ -365,8 +317,6 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   if (last_in_chunk && tid == 0) st_release_gpu(a.chunk_flag + chunk + 1, 1u);
 
   // 6. write the staged tile out in digit runs
-  K* kout = const_cast<K*>(static_cast<const K*>(a.keys[dst]));
-  uint32_t* vout = const_cast<uint32_t*>(a.vals[dst]);
   bool out_of_range = false;
 #pragma unroll 4
   for (uint32_t s = tid; s < tile_n; s += kBlock) {
@@ -381,7 +331,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
       from = s_src16[s];
     }
     const uint64_t o = s_off[dig(k, shift, mask)] + s;
-    if (o >= a.n) {  // only reachable after a timed-out wait; never write outside the output
+    if (o >= n_bound) {  // only reachable after a timed-out wait; never write outside the output
       out_of_range = true;
       continue;
     }
@@ -403,7 +353,7 @@ cudaError_t launch_typed(const OnesweepArgs& a, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const uint64_t tiles = (a.n + L::kTile - 1) / L::kTile;
+  const uint64_t tiles = a.segs ? uint64_t(a.total_tiles) : (a.n + L::kTile - 1) / L::kTile;
   if (!tiles) return cudaSuccess;
   onesweep_kernel<K, kVals><<<unsigned(tiles), L::kBlock, L::kBytes, stream>>>(a);
   return cudaGetLastError();
