@@ -210,6 +210,89 @@ def run_secondary(fs, workloads, torch, stream, peak, reps: int = 3):
     return out
 
 
+def batch_sizes(count: int = 4096, lo: int = 10, hi: int = 24, seed: int = 0):
+    """Segment lengths log-uniform in [2^lo, 2^hi] (seeded)."""
+    import numpy as np
+    u = np.random.default_rng(seed).random(count)
+    return [int(2 ** (lo + (hi - lo) * x)) for x in u]
+
+
+def run_batched(fs, workloads, torch, stream, peak, reps: int = 2):
+    """4096 independent uint32 key + uint32 value sorts (32-bit precision),
+    lengths log-uniform 1K-16M, each segment's distribution drawn from
+    uniform / Zipf s=1.1 / Gaussian: the batched path (one call, CUDA graph
+    replay, autotuned) against the plain path (one fsort_sort_pairs per
+    segment), same data, same exact output."""
+    import numpy as np
+    sizes = batch_sizes()
+    dists = ["uniform", "zipf1.1", "gauss"]
+    pick = np.random.default_rng(1).integers(0, 3, len(sizes))
+    total = sum(sizes)
+    tables = {d: (torch.from_numpy(workloads.table_for(d, 32)).cuda() if workloads.table_for(d, 32) is not None
+                  else None) for d in dists}
+    # every segment starts 16-byte aligned in one allocation
+    starts, at = [], 0
+    for n in sizes:
+        starts.append(at)
+        at += (n + 3) // 4 * 4
+    need = at
+    keys = torch.empty(need, dtype=torch.uint32, device="cuda")
+    vals = torch.empty(need, dtype=torch.uint32, device="cuda")
+
+    def regenerate():
+        for i, (st, n) in enumerate(zip(starts, sizes)):
+            d = dists[pick[i]]
+            t = tables[d]
+            workloads.generate_device(d, keys.data_ptr() + 4 * st, n, 32, seed=0, stream=i,
+                                      cuda_stream=stream.cuda_stream, table_dev_ptr=t.data_ptr() if t is not None else None)
+        workloads.iota_device(vals.data_ptr(), need, cuda_stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+
+    segs = [(keys.data_ptr() + 4 * st, vals.data_ptr() + 4 * st, n) for st, n in zip(starts, sizes)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"{len(sizes)} uint32 key + uint32 value sorts, 32-bit precision, lengths log-uniform "
+                       f"2^10..2^24 (total {total} keys), uniform/zipf1.1/gauss per segment",
+           "total_keys": total}
+    # batched: autotune once on this batch, then time graph replays on fresh data
+    side = torch.cuda.Stream()
+    bplan = fs.Plan(need + 8 * len(sizes), 32, has_values=True, flags=fs.FSORT_FLAG_GRAPH, max_segments=len(sizes))
+    regenerate()
+    cfg, _ = fs.fsort_batch_autotune(bplan.handle, segs, 32, 32, stream=side)
+    times = []
+    for _ in range(reps + 1):
+        regenerate()
+        with torch.cuda.stream(side):
+            e0.record(side)
+            bplan.sort_batch(segs, precision_bits=32, stream=side)
+            e1.record(side)
+        side.synchronize()
+        times.append(e0.elapsed_time(e1))
+    bplan.sync()
+    bplan.close()
+    bms = float(np.median(times[1:]))
+    # plain: one sort per segment
+    pplan = fs.Plan(max(sizes), 32, has_values=True)
+    times = []
+    for _ in range(reps + 1):
+        regenerate()
+        e0.record(stream)
+        for kp, vp, n in segs:
+            fs.fsort_sort_pairs(pplan.handle, kp, vp, n=n, key_bits=32, precision_bits=32, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    pplan.sync()
+    pplan.close()
+    pms = float(np.median(times[1:]))
+    alg = sum(4 * n + 4 * 2 * 8 * n for n in sizes)  # plain path's bytes: key read + 4 passes of keys+values
+    out.update({"batched_ms": bms, "batched_gkeys_per_s": total / bms / 1e6, "plain_ms": pms,
+                "plain_gkeys_per_s": total / pms / 1e6, "speedup": pms / bms, "autotuned": cfg,
+                "plain_path_algorithmic_bytes": alg, "plain_path_frac": alg / pms / 1e6 / peak})
+    del keys, vals
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, rank: int):
     """Reference arm: the CPU oracle, timed per step on a bounded sample."""
     if rank != 0:
@@ -385,6 +468,7 @@ def main():
 
     if rank == 0 and not args.no_extra:
         result["secondary"] = run_secondary(fs, workloads, torch, stream, peak)
+        result["batched"] = run_batched(fs, workloads, torch, stream, peak)
 
     # End to end through the public host-buffer entry point (rank-local).
     e2e = None

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kSmallBlock) small_sort_kernel(const SegDesc* 
           if (kVals) vals_buf[cur ^ 1][p] = vals_buf[cur][pos];
         }
       }
+      __syncthreads();  // every warp has read its offsets before the next pass clears them
       cur ^= 1;
     }
     __syncthreads();
