@@ -44,7 +44,8 @@ PRECISION = 16
 WORKLOAD = ("512 MB: 2^28 uint16 keys + uint32 index values, stable, 16-bit precision, out of place; "
             "5 distributions per step (uniform, zipf s=1.1, gauss mu=32768 sigma=1024, 90% presorted, all-equal)")
 METRIC = "Gkeys/s (16-bit keys + 32-bit values, 512 MB per sort, 5 distributions)"
-SCATTER_SRC = [os.path.join(ROOT, "paper_2605_10390_gb300", "csrc", f) for f in ("fsort_onesweep.cu", "fsort_dev.cuh")]
+SCATTER_SRC = [os.path.join(ROOT, "paper_2605_10390_gb300", "csrc", f)
+               for f in ("fsort_onesweep.cu", "fsort_dev.cuh", "fsort_rank.cuh")]
 
 
 def parse_args():

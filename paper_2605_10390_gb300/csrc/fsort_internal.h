@@ -124,4 +124,18 @@ cudaError_t launch_fill_tile_seg(const SegDesc* segs, uint32_t nsegs, int tile_k
 cudaError_t launch_seg_copy_back(const SegDesc* segs, uint32_t nsegs, const void* alt_keys,
                                  const uint32_t* alt_vals, int key_bits, int sms, cudaStream_t stream);
 
+// ---- learned CDF model (fsort_learned.cu) ----
+constexpr int kMlpHidden = 64;
+constexpr int kMlpParams = 1 * kMlpHidden + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden + kMlpHidden + 1;
+// grads += gradient of the mean squared error of sigmoid(mlp(x)) against y.
+cudaError_t launch_mlp_grad(const void* w_bf16, const float* x, const float* y, uint32_t m, float* grads, float* loss,
+                            cudaStream_t stream);
+// One Adam step (step >= 1): master/m1/m2 FP32, grads zeroed, BF16 copy refreshed.
+cudaError_t launch_mlp_adam(float* master, float* grads, float* m1, float* m2, void* w_bf16, float lr, int step,
+                            cudaStream_t stream);
+cudaError_t launch_mlp_eval(const void* w_bf16, const float* x, uint32_t m, float* out, cudaStream_t stream);
+cudaError_t launch_to_bf16(const float* src, void* dst, int count, cudaStream_t stream);
+cudaError_t launch_mlp_invert(const void* w_bf16, float center, float half, uint64_t lo_key, uint64_t hi_key,
+                              uint32_t buckets, uint64_t* splitters, cudaStream_t stream);
+
 }  // namespace fsort
