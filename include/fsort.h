@@ -70,6 +70,7 @@ typedef enum fsort_status {
 /* fsort_plan_desc.flags */
 #define FSORT_FLAG_HOST_IO 0x4u /* also allocate device buffers of max_n keys (+values) for fsort_sort_pairs_host */
 #define FSORT_FLAG_GRAPH 0x2u   /* batched sorts replay a captured CUDA graph when the batch shape repeats */
+#define FSORT_FLAG_LEARNED 0x8u /* allocate the learned bucket mapping (64-bit keys only); see fsort_learned_fit */
 
 typedef struct fsort_plan fsort_plan;
 
@@ -175,6 +176,98 @@ FSORT_API fsort_status fsort_batch_autotune(fsort_plan* plan, const fsort_segmen
                                             int key_bits, int precision_bits, void* stream,
                                             fsort_batch_config* best, float* best_ms);
 
+/* ---- learned bucket mapping -----------------------------------------------
+ * The paper has no learned component; this extends it where it leaves skewed
+ * inputs open (Sec. IV-A).  A small CDF model (a 1-64-64-1 ReLU perceptron with
+ * a sigmoid output, BF16 weights, FP32 sums) is trained on the GPU by this
+ * library's own forward and backward kernels on a stratified sample that the
+ * plain sort has sorted.  Its CDF is tabulated into a monotone bucket map;
+ * keys frequent in the sample get buckets of their own.  A keys-only sort of
+ * 64-bit keys at precision 64 on a plan with a fitted model then:
+ *   1. counts every bucket exactly (the plain path's histogram, Sec. III, used
+ *      as the judge of the model's error),
+ *   2. accepts the map iff the largest bucket of non-frequent keys holds at
+ *      most tau * n / B keys (tau = 8, B = the power of two >= n / 1024; one
+ *      CTA sorts up to 8,192 keys on chip), else runs the plain path (the
+ *      fallback),
+ *   3. partitions the keys into their buckets, fills the frequent-key buckets
+ *      and sorts every other bucket on chip.
+ * The result is the sorted multiset, identical to the plain path's.  The
+ * judge's decision is read back by the host: such a call synchronises with
+ * `stream` once, midway, and cannot be captured into a CUDA graph.  Calls
+ * with values, precision < 64 or n >= 2^32 always take the plain path. */
+typedef struct fsort_learned_opts {
+  uint32_t sample_keys; /* keys sampled from the input: 0 = min(n, 4,194,304); at most that */
+  uint32_t steps;       /* Adam steps: 0 = 4000; at most 16384 */
+  uint32_t batch;       /* minibatch (stratified over the sorted sample): 0 = 65536; at most 1,048,576 */
+  float lr;             /* peak learning rate (cosine decay to a tenth): 0 = 0.01 */
+  uint64_t seed;        /* sample, initial weights and minibatches */
+} fsort_learned_opts;
+
+typedef struct fsort_learned_stats {
+  int32_t fitted;        /* a model has been fitted on this plan */
+  int32_t used;          /* last eligible sort: 1 learned path, 0 fallback, -1 none yet */
+  uint32_t buckets;      /* B of the last judged sort (frequent keys add 2 ids each) */
+  uint32_t heavy_keys;   /* keys with buckets of their own */
+  uint32_t max_bucket;   /* largest bucket of non-frequent keys in the last judged sort */
+  uint32_t limit;        /* floor(tau * n / B) of that sort */
+  double imbalance;      /* max_bucket / (n / B) */
+  double tau;            /* threshold on imbalance (8) */
+  uint32_t sample_keys;  /* keys sampled by the last fit */
+  uint32_t train_keys;   /* non-frequent sample keys the model was trained on */
+  uint32_t steps;        /* Adam steps of the last fit */
+  uint32_t reserved;
+  float loss_first;      /* training loss (mean of 0.5 (F(x) - rank/count)^2) of the first step */
+  float loss_last;       /* and of the last step */
+} fsort_learned_stats;
+
+/* Number of MLP parameters and their order in a flat array: W1[64], b1[64],
+ * W2[64][64] (row j feeds hidden unit j of layer 2), b2[64], W3[64], b3. */
+#define FSORT_MLP_PARAMS 4353
+#define FSORT_LEARN_CELLS 56320
+
+/* Fit the plan's model to keys[0..n) (64-bit keys, n <= max_n): sample, sort
+ * the sample with the plain path, find the frequent keys, train, tabulate the
+ * map.  Stream-ordered (no host synchronisation); requires FSORT_FLAG_LEARNED. */
+FSORT_API fsort_status fsort_learned_fit(fsort_plan* plan, const void* keys, uint64_t n,
+                                         const fsort_learned_opts* opts, void* stream);
+
+/* Statistics of the last fit and the last judged sort.  Waits for the device. */
+FSORT_API fsort_status fsort_learned_get_stats(fsort_plan* plan, fsort_learned_stats* out);
+
+/* Copy of the fitted model (waits for the device): params_host[FSORT_MLP_PARAMS]
+ * FP32 master weights (the sorts use their BF16 rounding); cells_host
+ * [2 * (FSORT_LEARN_CELLS + 1)] the map table (G_i, H_i) pairs; heavy_host
+ * [8192] the frequent keys ascending, *heavy_count of them; norm[2] = (center,
+ * half) of the feature.  Any pointer may be NULL. */
+FSORT_API fsort_status fsort_learned_get_model(fsort_plan* plan, float* params_host, uint32_t* cells_host,
+                                               uint64_t* heavy_host, uint32_t* heavy_count, float* norm);
+
+/* Install a model instead of fitting one (synchronous; host pointers).
+ * heavy_host[heavy_count] ascending distinct frequent keys (heavy_count <=
+ * 8192, NULL if 0); norm[2] = (center, half > 0).  If cells_host is NULL the
+ * map table is built on the GPU from params_host exactly as a fit builds it;
+ * otherwise cells_host[2 * (FSORT_LEARN_CELLS + 1)] is used as the table: G
+ * non-decreasing with G[FSORT_LEARN_CELLS] = 0xFFFFFFFF, H_i = frequent keys
+ * below the start of cell i (checked; FSORT_ERR_INVALID_ARG otherwise), and
+ * params_host may be NULL. */
+FSORT_API fsort_status fsort_learned_set_model(fsort_plan* plan, const float* params_host, const uint32_t* cells_host,
+                                               const uint64_t* heavy_host, uint32_t heavy_count, const float* norm,
+                                               void* stream);
+
+/* ids[i] = bucket id of keys[i] under the fitted map, with the B that a sort
+ * of n keys uses (device pointers; uint32_t ids). */
+FSORT_API fsort_status fsort_learned_bucket_ids(fsort_plan* plan, const void* keys, uint64_t n, uint32_t* ids,
+                                                void* stream);
+
+/* The model's kernels on caller data (device pointers), for checking them:
+ * out[i] = sigmoid(mlp(x[i])) with BF16 weights w_bf16[FSORT_MLP_PARAMS];
+ * grads[FSORT_MLP_PARAMS] += gradient of L = 1/(2m) sum_i (out_i - y_i)^2 and
+ * *loss += L (loss may be NULL).  1 <= m. */
+FSORT_API fsort_status fsort_mlp_forward(const void* w_bf16, const float* x, uint32_t m, float* out, void* stream);
+FSORT_API fsort_status fsort_mlp_grad(const void* w_bf16, const float* x, const float* y, uint32_t m, float* grads,
+                                      float* loss, void* stream);
+
 /* ---- the hot-path steps one at a time (same kernels as the full sort) ---- */
 
 /* Step 2: per-pass digit histograms of keys[0..n).  counts_out (device, uint64_t)
@@ -215,6 +308,13 @@ FSORT_API fsort_status fsort_expand(fsort_plan* plan, const uint64_t* counts, vo
 #define FSORT_KERNEL_LEAF_REDUCE 6 /* expand path: sum of per-CTA partial counts */
 #define FSORT_KERNEL_LEAF_SCAN 7   /* expand path: exclusive scan of 65,536 bins */
 #define FSORT_KERNEL_EXPAND 8      /* step 5 */
+#define FSORT_KERNEL_LEARN_COUNT1 9    /* learned path: per-chunk super-bucket counts, heavy counts */
+#define FSORT_KERNEL_LEARN_SCATTER1 10 /* learned path: scan + keys grouped by super-bucket */
+#define FSORT_KERNEL_LEARN_COUNT2 11   /* learned path: per-bucket counts */
+#define FSORT_KERNEL_LEARN_JUDGE 12    /* learned path: the judge, with the host read-back */
+#define FSORT_KERNEL_LEARN_SCATTER2 13 /* learned path: scan + keys to their buckets */
+#define FSORT_KERNEL_LEARN_FILL 14     /* learned path: heavy buckets */
+#define FSORT_KERNEL_LEARN_BUCKETS 15  /* learned path: on-chip sort of every bucket */
 
 typedef struct fsort_kernel_time {
   int32_t kind;   /* FSORT_KERNEL_* */

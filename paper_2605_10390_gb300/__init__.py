@@ -12,6 +12,19 @@ Low-level names mirror the C ABI (``fsort_plan_create``, ``fsort_sort_pairs``,
 from ._binding import (  # noqa: F401
     FSORT_FLAG_GRAPH,
     FSORT_FLAG_HOST_IO,
+    FSORT_FLAG_LEARNED,
+    FSORT_LEARN_CELLS,
+    FSORT_LEARN_MAX_HEAVY,
+    FSORT_MLP_PARAMS,
+    FsortLearnedOpts,
+    FsortLearnedStats,
+    fsort_learned_bucket_ids,
+    fsort_learned_fit,
+    fsort_learned_get_model,
+    fsort_learned_get_stats,
+    fsort_learned_set_model,
+    fsort_mlp_forward,
+    fsort_mlp_grad,
     FsortBatchConfig,
     FsortSegment,
     fsort_batch_autotune,

@@ -12,6 +12,10 @@ _lib = None
 
 FSORT_FLAG_HOST_IO = 0x4
 FSORT_FLAG_GRAPH = 0x2
+FSORT_FLAG_LEARNED = 0x8
+FSORT_MLP_PARAMS = 4353
+FSORT_LEARN_CELLS = 56320
+FSORT_LEARN_MAX_HEAVY = 8192
 
 STATUS = {
     0: "FSORT_OK", 1: "FSORT_ERR_INVALID_ARG", 2: "FSORT_ERR_OOM", 3: "FSORT_ERR_CUDA", 4: "FSORT_ERR_TIMEOUT",
@@ -56,8 +60,25 @@ class FsortKernelTime(ctypes.Structure):
                 ("call", ctypes.c_int32), ("n", ctypes.c_uint64), ("ms", ctypes.c_float), ("reserved", ctypes.c_float)]
 
 
+class FsortLearnedOpts(ctypes.Structure):
+    _fields_ = [("sample_keys", ctypes.c_uint32), ("steps", ctypes.c_uint32), ("batch", ctypes.c_uint32),
+                ("lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class FsortLearnedStats(ctypes.Structure):
+    _fields_ = [("fitted", ctypes.c_int32), ("used", ctypes.c_int32), ("buckets", ctypes.c_uint32),
+                ("heavy_keys", ctypes.c_uint32), ("max_bucket", ctypes.c_uint32), ("limit", ctypes.c_uint32),
+                ("imbalance", ctypes.c_double), ("tau", ctypes.c_double), ("sample_keys", ctypes.c_uint32),
+                ("train_keys", ctypes.c_uint32), ("steps", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 KERNEL_KINDS = {1: "histogram", 2: "scan", 3: "scatter", 4: "copy", 5: "leaf_hist", 6: "leaf_reduce",
-                7: "leaf_scan", 8: "expand"}
+                7: "leaf_scan", 8: "expand", 9: "learn_count1", 10: "learn_scatter1", 11: "learn_count2",
+                12: "learn_judge", 13: "learn_scatter2", 14: "learn_fill", 15: "learn_buckets"}
 
 
 def lib_path() -> str:
@@ -96,6 +117,13 @@ def load_library():
             "fsort_batch_get_config": ([vp, ctypes.POINTER(FsortBatchConfig)], st),
             "fsort_batch_autotune": ([vp, ctypes.POINTER(FsortSegment), ctypes.c_uint32, i32, i32, vp,
                                       ctypes.POINTER(FsortBatchConfig), ctypes.POINTER(ctypes.c_float)], st),
+            "fsort_learned_fit": ([vp, vp, u64, ctypes.POINTER(FsortLearnedOpts), vp], st),
+            "fsort_learned_get_stats": ([vp, ctypes.POINTER(FsortLearnedStats)], st),
+            "fsort_learned_get_model": ([vp, vp, vp, vp, ctypes.POINTER(ctypes.c_uint32), vp], st),
+            "fsort_learned_bucket_ids": ([vp, vp, u64, vp, vp], st),
+            "fsort_learned_set_model": ([vp, vp, vp, vp, ctypes.c_uint32, vp, vp], st),
+            "fsort_mlp_forward": ([vp, vp, ctypes.c_uint32, vp, vp], st),
+            "fsort_mlp_grad": ([vp, vp, vp, ctypes.c_uint32, vp, vp, vp], st),
             "fsort_status_string": ([i32], ctypes.c_char_p),
             "fsort_version": ([], i32),
         }
@@ -317,6 +345,64 @@ def fsort_batch_autotune(plan, segments, key_bits: int, precision_bits=None, str
     return cfg.as_dict(), ms.value
 
 
+def fsort_learned_fit(plan, keys, n=None, sample_keys: int = 0, steps: int = 0, batch: int = 0, lr: float = 0.0,
+                      seed: int = 0, stream=None) -> None:
+    o = FsortLearnedOpts(sample_keys, steps, batch, lr, seed)
+    _check(load_library().fsort_learned_fit(plan, _ptr(keys), _numel(keys, n), ctypes.byref(o), _stream(stream)),
+           "fsort_learned_fit")
+
+
+def fsort_learned_get_stats(plan) -> dict:
+    out = FsortLearnedStats()
+    _check(load_library().fsort_learned_get_stats(plan, ctypes.byref(out)), "fsort_learned_get_stats")
+    return out.as_dict()
+
+
+def fsort_learned_get_model(plan) -> dict:
+    """The fitted model as numpy arrays: params (FP32), cells (G, H) pairs,
+    frequent keys, and the feature normalisation (center, half)."""
+    import numpy as np
+    params = np.zeros(FSORT_MLP_PARAMS, np.float32)
+    cells = np.zeros((FSORT_LEARN_CELLS + 1, 2), np.uint32)
+    heavy = np.zeros(FSORT_LEARN_MAX_HEAVY, np.uint64)
+    norm = np.zeros(2, np.float32)
+    m = ctypes.c_uint32(0)
+    _check(load_library().fsort_learned_get_model(plan, params.ctypes.data, cells.ctypes.data, heavy.ctypes.data,
+                                                  ctypes.byref(m), norm.ctypes.data), "fsort_learned_get_model")
+    return {"params": params, "cells": cells, "heavy": heavy[:m.value].copy(), "center": float(norm[0]),
+            "half": float(norm[1])}
+
+
+def fsort_learned_set_model(plan, params=None, cells=None, heavy=None, center: float = 0.0, half: float = 1.0,
+                            stream=None) -> None:
+    """Install a model: numpy float32 params[4353] and/or uint32 cells[(56321, 2)],
+    uint64 heavy keys ascending, and the feature normalisation."""
+    import numpy as np
+    p = None if params is None else np.ascontiguousarray(params, np.float32)
+    c = None if cells is None else np.ascontiguousarray(cells, np.uint32)
+    h = np.ascontiguousarray(np.zeros(0, np.uint64) if heavy is None else heavy, np.uint64)
+    norm = np.array([center, half], np.float32)
+    _check(load_library().fsort_learned_set_model(plan, None if p is None else p.ctypes.data,
+                                                  None if c is None else c.ctypes.data,
+                                                  h.ctypes.data if h.size else None, h.size, norm.ctypes.data,
+                                                  _stream(stream)), "fsort_learned_set_model")
+
+
+def fsort_learned_bucket_ids(plan, keys, ids, n=None, stream=None) -> None:
+    _check(load_library().fsort_learned_bucket_ids(plan, _ptr(keys), _numel(keys, n), _ptr(ids), _stream(stream)),
+           "fsort_learned_bucket_ids")
+
+
+def fsort_mlp_forward(w_bf16, x, out, m=None, stream=None) -> None:
+    _check(load_library().fsort_mlp_forward(_ptr(w_bf16), _ptr(x), _numel(x, m), _ptr(out), _stream(stream)),
+           "fsort_mlp_forward")
+
+
+def fsort_mlp_grad(w_bf16, x, y, grads, loss=None, m=None, stream=None) -> None:
+    _check(load_library().fsort_mlp_grad(_ptr(w_bf16), _ptr(x), _ptr(y), _numel(x, m), _ptr(grads), _ptr(loss),
+                                         _stream(stream)), "fsort_mlp_grad")
+
+
 def fsort_status_string(status: int) -> str:
     return load_library().fsort_status_string(status).decode()
 
@@ -363,6 +449,12 @@ class Plan:
 
     def sort_batch(self, segments, precision_bits=None, stream=None) -> None:
         fsort_sort_batch(self.handle, segments, self.key_bits, precision_bits, stream)
+
+    def learned_fit(self, keys, n=None, **opts) -> None:
+        fsort_learned_fit(self.handle, keys, n, **opts)
+
+    def learned_stats(self) -> dict:
+        return fsort_learned_get_stats(self.handle)
 
     def describe(self, n: int, precision_bits=None, has_values=None) -> dict:
         return fsort_plan_describe(self.handle, n, self.key_bits,

@@ -4,6 +4,7 @@
 // validates, enqueues and reports.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -34,6 +35,35 @@ struct Timing {
   int next_slot = 0;
   int calls = 0;
   std::vector<TimingRec> recs;
+};
+
+// Learned bucket mapping (FSORT_FLAG_LEARNED): device buffers carved from
+// the plan's allocation, and the host view of the last fit and judge.
+struct LearnedWs {
+  static constexpr uint32_t kMaxSample = 1u << 22;
+  static constexpr uint32_t kMaxSteps = 16384;
+  uint32_t sample_max = 0;
+  uint32_t nids_max = 0;
+  uint64_t l1_max = 0;
+  uint64_t* sample = nullptr;
+  uint64_t* train = nullptr;
+  uint32_t *flag_nh = nullptr, *flag_hv = nullptr, *pos_nh = nullptr, *pos_hv = nullptr;
+  uint32_t* sums = nullptr;
+  uint64_t* heavy = nullptr;
+  uint32_t *hid = nullptr, *large = nullptr;
+  uint2* cells = nullptr;
+  float* fval = nullptr;
+  uint32_t *counts1 = nullptr, *off1 = nullptr;   // level 1: [nsuper][nch] + 1
+  uint32_t *counts = nullptr, *offsets = nullptr;  // every bucket id (+ 1)
+  uint32_t *hcount = nullptr, *bitmap = nullptr;
+  void* w_bf16 = nullptr;
+  float *master = nullptr, *m1 = nullptr, *m2 = nullptr, *grads = nullptr, *loss_log = nullptr;
+  fsort::LearnedState* st = nullptr;
+  fsort::LearnedState* h_st = nullptr;  // pinned
+  bool fitted = false;
+  int32_t used = -1;
+  uint32_t steps = 0, last_b = 0, last_limit = 0, last_max = 0, last_heavy = 0;
+  double last_imbalance = 0.0;
 };
 
 }  // namespace
@@ -91,6 +121,7 @@ struct fsort_plan {
   uint64_t gkey[10] = {};
 
   Timing timing;
+  LearnedWs* learn = nullptr;  // FSORT_FLAG_LEARNED
 };
 
 namespace {
@@ -109,6 +140,21 @@ fsort_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return FSORT_OK;
   if (e == cudaErrorMemoryAllocation) return FSORT_ERR_OOM;
   return FSORT_ERR_CUDA;
+}
+
+// B for a learned sort of n keys: the smallest power of two >= n / 1024,
+// clamped to [2^8, 2^22].
+uint32_t learned_buckets(uint64_t n) {
+  const uint64_t want = (n + kLearnKeysPerBucket - 1) / kLearnKeysPerBucket;
+  uint32_t b = 256;
+  while (b < want && b < (1u << 22)) b <<= 1;
+  return b;
+}
+
+uint32_t log2u(uint32_t v) {
+  uint32_t l = 0;
+  while ((1u << l) < v) ++l;
+  return l;
 }
 
 DigitPlan make_plan(int key_bits, int precision_bits, int d) {
@@ -266,6 +312,105 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
   tm.finish();
   if (e != cudaSuccess) return from_cuda(e);
   return finish_call(p, s);
+}
+
+// ---- learned bucket mapping ----
+bool learned_eligible(const fsort_plan* p, const uint32_t* vals, uint64_t n, int key_bits, int precision_bits) {
+  return p->learn && p->learn->fitted && !vals && key_bits == 64 && precision_bits == 64 && n > 0 &&
+         n < (1ull << 32);
+}
+
+LearnedMap learned_map(const LearnedWs& L, uint64_t n) {
+  return LearnedMap{L.cells, L.heavy, 32u - log2u(learned_buckets(n))};
+}
+
+// Level-1 and level-2 counts, the judge (host read-back); on acceptance the
+// scatters, the heavy fill and the bucket sorts, else the plain path on the
+// untouched input.  keys_in == keys_out: in place.
+fsort_status enqueue_learned(fsort_plan* p, const void* keys_in, void* keys_out, uint64_t n, cudaStream_t s) {
+  LearnedWs& L = *p->learn;
+  const uint32_t B = learned_buckets(n);
+  const LearnedGeom g = learned_geometry(n, B);
+  const LearnedMap mp = learned_map(L, n);
+  const uint64_t* kin = static_cast<const uint64_t*>(keys_in);
+  uint64_t* kout = static_cast<uint64_t*>(keys_out);
+  uint64_t* alt = static_cast<uint64_t*>(p->alt_keys);
+  const uint64_t l1n = uint64_t(g.nsuper) * g.nch;
+  CallTimer tm(p, n, s, false);
+  cudaError_t e = cudaMemsetAsync(L.hcount, 0, size_t(kLearnMaxHeavy) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.bitmap, 0, size_t(g.nids / 32 + 1) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.counts1 + l1n, 0, 4, s);
+  if (e == cudaSuccess) e = launch_learn_heavy_ids(mp, L.st, L.hid, L.bitmap, s);
+  if (e == cudaSuccess) e = launch_learn_l1(kin, n, g, mp, L.st, L.counts1, L.hcount, s);
+  tm.mark(FSORT_KERNEL_LEARN_COUNT1, -1);
+  if (e == cudaSuccess) e = launch_scan_u32(L.counts1, l1n + 1, L.off1, nullptr, L.sums, s);
+  if (e == cudaSuccess) e = launch_learn_l1_scatter(kin, n, g, mp, L.off1, alt, s);
+  tm.mark(FSORT_KERNEL_LEARN_SCATTER1, -1);
+  if (e == cudaSuccess) e = launch_learn_l2_count(alt, g, mp, L.off1, L.counts, s);
+  tm.mark(FSORT_KERNEL_LEARN_COUNT2, -1);
+  if (e == cudaSuccess) e = launch_learn_judge(L.counts, g, L.bitmap, L.hid, L.hcount, L.st, L.large, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(L.h_st, L.st, sizeof(LearnedState), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  tm.mark(FSORT_KERNEL_LEARN_JUDGE, -1);
+  if (e != cudaSuccess) return from_cuda(e);
+  const uint64_t limit = uint64_t(kLearnTau) * n / B;
+  const uint32_t mx = L.h_st->max_nonheavy;
+  const bool accept = mx <= limit && mx <= uint32_t(kLearnBucketCap);
+  L.used = accept ? 1 : 0;
+  L.last_b = B;
+  L.last_limit = uint32_t(limit);
+  L.last_max = mx;
+  L.last_heavy = L.h_st->heavy_count;
+  L.last_imbalance = double(mx) * double(B) / double(n);
+  if (!accept) return enqueue_sort(p, keys_in, nullptr, keys_out, nullptr, n, 64, 64, s);
+  e = launch_scan_u32(L.counts, g.nids, L.offsets, nullptr, L.sums, s);
+  if (e == cudaSuccess) e = launch_learn_l2_scatter(alt, g, mp, L.off1, L.offsets, kout, s);
+  tm.mark(FSORT_KERNEL_LEARN_SCATTER2, -1);
+  if (e == cudaSuccess) e = launch_learn_fill(mp, L.st, L.hid, L.large, L.offsets, L.counts, kout, p->sms, s);
+  tm.mark(FSORT_KERNEL_LEARN_FILL, -1);
+  if (e == cudaSuccess)
+    e = launch_learn_bucket_sort(kout, L.counts, L.offsets, L.bitmap, g.nids, L.cells, p->status, p->sms, s);
+  tm.mark(FSORT_KERNEL_LEARN_BUCKETS, -1);
+  if (e != cudaSuccess) return from_cuda(e);
+  return finish_call(p, s);
+}
+
+// Every sort entry point: the learned path where it applies, else the plain one.
+fsort_status enqueue_any(fsort_plan* p, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                         uint32_t* vals_out, uint64_t n, int key_bits, int precision_bits, cudaStream_t s) {
+  if (learned_eligible(p, vals_in, n, key_bits, precision_bits)) return enqueue_learned(p, keys_in, keys_out, n, s);
+  return enqueue_sort(p, keys_in, vals_in, keys_out, vals_out, n, key_bits, precision_bits, s);
+}
+
+// Seeded initial weights: first-layer kinks spread evenly over the feature
+// range [-1, 1], He-scaled hidden layer, small output layer.
+void learned_init_params(std::vector<float>& w, uint64_t seed) {
+  w.assign(kMlpParams, 0.f);
+  uint64_t z = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  auto next = [&]() {  // splitmix64 (Steele, Lea and Flood, 2014) -> uniform [0, 1)
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t x = z;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return double(x >> 11) * (1.0 / 9007199254740992.0);
+  };
+  auto normal = [&]() {  // Box-Muller
+    const double u1 = next() + 1e-300, u2 = next();
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  };
+  const int H = kMlpHidden;
+  for (int i = 0; i < H; ++i) {
+    const double slope = (2.0 + 6.0 * next()) * ((i & 1) ? -1.0 : 1.0);
+    const double kink = -1.0 + 2.0 * (i + 0.5) / H;
+    w[i] = float(slope);                 // W1
+    w[H + i] = float(-slope * kink);     // b1
+  }
+  const int w2 = 2 * H, b2 = w2 + H * H, w3 = b2 + H;
+  for (int i = 0; i < H * H; ++i) w[w2 + i] = float(normal() * std::sqrt(2.0 / H));
+  for (int i = 0; i < H; ++i) w[b2 + i] = 0.f;
+  for (int i = 0; i < H; ++i) w[w3 + i] = float(normal() * std::sqrt(1.0 / H));
+  w[w3 + H] = 0.f;  // b3
 }
 
 // Batched sorts: build the segment lists on the host (pinned staging), then
@@ -507,7 +652,8 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   if (!valid_key_bits(desc->key_bits) || desc->max_n < 1) return FSORT_ERR_INVALID_ARG;
   if (desc->has_values != 0 && desc->has_values != 1) return FSORT_ERR_INVALID_ARG;
   if (desc->digit_bits != 0 && desc->digit_bits != 8) return FSORT_ERR_UNSUPPORTED;
-  if (desc->flags & ~(FSORT_FLAG_HOST_IO | FSORT_FLAG_GRAPH)) return FSORT_ERR_INVALID_ARG;
+  if (desc->flags & ~(FSORT_FLAG_HOST_IO | FSORT_FLAG_GRAPH | FSORT_FLAG_LEARNED)) return FSORT_ERR_INVALID_ARG;
+  if ((desc->flags & FSORT_FLAG_LEARNED) && desc->key_bits != 64) return FSORT_ERR_UNSUPPORTED;
   if (desc->max_n > (1ull << 36)) return FSORT_ERR_UNSUPPORTED;
 
   fsort_plan* p = new (std::nothrow) fsort_plan();
@@ -578,6 +724,43 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     o_iok = take(n * kb);
     if (desc->has_values) o_iov = take(n * 4);
   }
+  const bool learned = (desc->flags & FSORT_FLAG_LEARNED) != 0;
+  LearnedWs lw;
+  size_t o_l[25] = {};
+  if (learned) {
+    lw.sample_max = uint32_t(n < LearnedWs::kMaxSample ? n : LearnedWs::kMaxSample);
+    const LearnedGeom gm = learned_geometry(n, learned_buckets(n));
+    lw.nids_max = gm.nids;
+    lw.l1_max = uint64_t(gm.nsuper) * kLearnL1Chunks + 1;
+    const size_t sm = lw.sample_max, nb = lw.nids_max + 1, l1 = lw.l1_max;
+    const size_t big = sm > nb ? (sm > l1 ? sm : l1) : (nb > l1 ? nb : l1);
+    const size_t scan_words = big / 4096 + 2;
+    o_l[0] = take(sm * 8);
+    o_l[1] = take(sm * 8);
+    o_l[2] = take(sm * 4);
+    o_l[3] = take(sm * 4);
+    o_l[4] = take(sm * 4);
+    o_l[5] = take(sm * 4);
+    o_l[6] = take(scan_words * 4);
+    o_l[7] = take(size_t(kLearnMaxHeavy) * 8);
+    o_l[8] = take(size_t(kLearnMaxHeavy) * 4);
+    o_l[9] = take(size_t(kLearnMaxHeavy) * 4);
+    o_l[10] = take(size_t(kLearnCells + 1) * 8);
+    o_l[11] = take(size_t(kLearnCells + 1) * 4);
+    o_l[12] = take(nb * 4);
+    o_l[13] = take(nb * 4);
+    o_l[14] = take(size_t(kLearnMaxHeavy) * 4);
+    o_l[15] = take((nb / 32 + 1) * 4);
+    o_l[23] = take(l1 * 4);
+    o_l[24] = take(l1 * 4);
+    o_l[16] = take(size_t(kMlpParams) * 2);
+    o_l[17] = take(size_t(kMlpParams) * 4);
+    o_l[18] = take(size_t(kMlpParams) * 4);
+    o_l[19] = take(size_t(kMlpParams) * 4);
+    o_l[20] = take(size_t(kMlpParams) * 4);
+    o_l[21] = take(size_t(LearnedWs::kMaxSteps) * 4);
+    o_l[22] = take(sizeof(LearnedState));
+  }
   p->ws_bytes = off;
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->ws), p->ws_bytes);
   if (e != cudaSuccess) {
@@ -614,6 +797,48 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   if (hio) {
     p->io_keys = w + o_iok;
     p->io_vals = desc->has_values ? reinterpret_cast<uint32_t*>(w + o_iov) : nullptr;
+  }
+  if (learned) {
+    p->learn = new (std::nothrow) LearnedWs(lw);
+    if (!p->learn) {
+      fsort_plan_destroy(p);
+      return FSORT_ERR_OOM;
+    }
+    LearnedWs& L = *p->learn;
+    L.sample = reinterpret_cast<uint64_t*>(w + o_l[0]);
+    L.train = reinterpret_cast<uint64_t*>(w + o_l[1]);
+    L.flag_nh = reinterpret_cast<uint32_t*>(w + o_l[2]);
+    L.flag_hv = reinterpret_cast<uint32_t*>(w + o_l[3]);
+    L.pos_nh = reinterpret_cast<uint32_t*>(w + o_l[4]);
+    L.pos_hv = reinterpret_cast<uint32_t*>(w + o_l[5]);
+    L.sums = reinterpret_cast<uint32_t*>(w + o_l[6]);
+    L.heavy = reinterpret_cast<uint64_t*>(w + o_l[7]);
+    L.hid = reinterpret_cast<uint32_t*>(w + o_l[8]);
+    L.large = reinterpret_cast<uint32_t*>(w + o_l[9]);
+    L.cells = reinterpret_cast<uint2*>(w + o_l[10]);
+    L.fval = reinterpret_cast<float*>(w + o_l[11]);
+    L.counts = reinterpret_cast<uint32_t*>(w + o_l[12]);
+    L.offsets = reinterpret_cast<uint32_t*>(w + o_l[13]);
+    L.hcount = reinterpret_cast<uint32_t*>(w + o_l[14]);
+    L.bitmap = reinterpret_cast<uint32_t*>(w + o_l[15]);
+    L.counts1 = reinterpret_cast<uint32_t*>(w + o_l[23]);
+    L.off1 = reinterpret_cast<uint32_t*>(w + o_l[24]);
+    L.w_bf16 = w + o_l[16];
+    L.master = reinterpret_cast<float*>(w + o_l[17]);
+    L.m1 = reinterpret_cast<float*>(w + o_l[18]);
+    L.m2 = reinterpret_cast<float*>(w + o_l[19]);
+    L.grads = reinterpret_cast<float*>(w + o_l[20]);
+    L.loss_log = reinterpret_cast<float*>(w + o_l[21]);
+    L.st = reinterpret_cast<LearnedState*>(w + o_l[22]);
+    e = cudaMallocHost(reinterpret_cast<void**>(&L.h_st), sizeof(LearnedState));
+    if (e == cudaSuccess) e = cudaMemset(L.st, 0, sizeof(LearnedState));
+    if (e == cudaSuccess) e = cudaMemset(L.heavy, 0, size_t(kLearnMaxHeavy) * 8);
+    if (e != cudaSuccess) {
+      L.h_st = nullptr;
+      cudaGetLastError();
+      fsort_plan_destroy(p);
+      return FSORT_ERR_OOM;
+    }
   }
   // Zero what must start at zero: histogram accumulators, status, counters.
   e = cudaMemset(p->hist, 0, hist_bytes);
@@ -661,6 +886,10 @@ fsort_status fsort_plan_destroy(fsort_plan* plan) {
   if (plan->done) cudaEventDestroy(plan->done);
   if (plan->h_status) cudaFreeHost(plan->h_status);
   fsort_plan_set_timing(plan, 0);
+  if (plan->learn) {
+    if (plan->learn->h_st) cudaFreeHost(plan->learn->h_st);
+    delete plan->learn;
+  }
   if (plan->ws && cudaFree(plan->ws) != cudaSuccess) st = FSORT_ERR_CUDA;
   delete plan;
   return st;
@@ -705,7 +934,7 @@ fsort_status fsort_sort_pairs(fsort_plan* plan, void* keys, uint32_t* vals, uint
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   st = take_latched(plan, false, s);
   if (st != FSORT_OK) return st;
-  return enqueue_sort(plan, keys, vals, keys, vals, n, key_bits, precision_bits, s);
+  return enqueue_any(plan, keys, vals, keys, vals, n, key_bits, precision_bits, s);
 }
 
 fsort_status fsort_sort_pairs_out(fsort_plan* plan, const void* keys_in, const uint32_t* vals_in, void* keys_out,
@@ -724,7 +953,7 @@ fsort_status fsort_sort_pairs_out(fsort_plan* plan, const void* keys_in, const u
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   st = take_latched(plan, false, s);
   if (st != FSORT_OK) return st;
-  return enqueue_sort(plan, keys_in, vals_in, keys_out, vals_out, n, key_bits, precision_bits, s);
+  return enqueue_any(plan, keys_in, vals_in, keys_out, vals_out, n, key_bits, precision_bits, s);
 }
 
 fsort_status fsort_sort_pairs_host(fsort_plan* plan, void* keys_host, uint32_t* vals_host, uint64_t n, int key_bits,
@@ -741,8 +970,8 @@ fsort_status fsort_sort_pairs_host(fsort_plan* plan, void* keys_host, uint32_t* 
   cudaError_t e = cudaMemcpyAsync(plan->io_keys, keys_host, kbytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && vals_host) e = cudaMemcpyAsync(plan->io_vals, vals_host, n * 4, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return from_cuda(e);
-  st = enqueue_sort(plan, plan->io_keys, vals_host ? plan->io_vals : nullptr, plan->io_keys,
-                    vals_host ? plan->io_vals : nullptr, n, key_bits, precision_bits, s);
+  st = enqueue_any(plan, plan->io_keys, vals_host ? plan->io_vals : nullptr, plan->io_keys,
+                   vals_host ? plan->io_vals : nullptr, n, key_bits, precision_bits, s);
   if (st != FSORT_OK) return st;
   e = cudaMemcpyAsync(keys_host, plan->io_keys, kbytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && vals_host) e = cudaMemcpyAsync(vals_host, plan->io_vals, n * 4, cudaMemcpyDeviceToHost, s);
@@ -855,6 +1084,186 @@ fsort_status fsort_expand(fsort_plan* plan, const uint64_t* counts, void* keys_o
   if (e == cudaSuccess) e = launch_expand(plan->leaf_off, static_cast<uint16_t*>(keys_out), n, s);
   if (e != cudaSuccess) return from_cuda(e);
   return finish_call(plan, s);
+}
+
+fsort_status fsort_learned_fit(fsort_plan* plan, const void* keys, uint64_t n, const fsort_learned_opts* opts,
+                               void* stream) {
+  if (!plan || !plan->learn) return FSORT_ERR_INVALID_ARG;
+  if (!keys || !aligned16(keys) || n < 1 || n > plan->desc.max_n) return FSORT_ERR_INVALID_ARG;
+  fsort_learned_opts o{};
+  if (opts) o = *opts;
+  LearnedWs& L = *plan->learn;
+  uint32_t S = o.sample_keys ? o.sample_keys : LearnedWs::kMaxSample;
+  if (S > L.sample_max) S = L.sample_max;
+  if (uint64_t(S) > n) S = uint32_t(n);
+  const uint32_t steps = o.steps ? o.steps : 4000u;
+  const uint32_t batch = o.batch ? o.batch : 65536u;
+  const float lr = o.lr > 0.f ? o.lr : 0.01f;
+  if (steps > LearnedWs::kMaxSteps || batch > (1u << 20) || !(lr < 1.f)) return FSORT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  fsort_status st = take_latched(plan, false, s);
+  if (st != FSORT_OK) return st;
+  L.fitted = false;
+  std::vector<float> init;
+  learned_init_params(init, o.seed);
+  cudaError_t e = cudaMemcpyAsync(L.master, init.data(), size_t(kMlpParams) * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // `init` is pageable and about to go away
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.m1, 0, size_t(kMlpParams) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.m2, 0, size_t(kMlpParams) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.grads, 0, size_t(kMlpParams) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.loss_log, 0, size_t(LearnedWs::kMaxSteps) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.st, 0, sizeof(LearnedState), s);
+  if (e == cudaSuccess) e = launch_to_bf16(L.master, L.w_bf16, kMlpParams, s);
+  // the sample, sorted by the plain path
+  if (e == cudaSuccess) e = launch_learn_sample(static_cast<const uint64_t*>(keys), n, S, o.seed, L.sample, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  st = enqueue_sort(plan, L.sample, nullptr, L.sample, nullptr, S, 64, 64, s);
+  if (st != FSORT_OK) return st;
+  // frequent keys: at least 1024 copies expected among the n keys
+  uint64_t hmin = (uint64_t(S) * 1024 + n - 1) / n;
+  if (hmin < 2) hmin = 2;
+  e = launch_learn_split(L.sample, S, uint32_t(hmin), L.flag_nh, L.flag_hv, s);
+  if (e == cudaSuccess) e = launch_scan_u32(L.flag_nh, S, L.pos_nh, nullptr, L.sums, s);
+  if (e == cudaSuccess) e = launch_scan_u32(L.flag_hv, S, L.pos_hv, nullptr, L.sums, s);
+  if (e == cudaSuccess)
+    e = launch_learn_compact(L.sample, S, L.flag_nh, L.pos_nh, L.flag_hv, L.pos_hv, L.train, L.heavy, L.st, s);
+  if (e == cudaSuccess) e = launch_learn_init_kinks(L.train, L.st, L.master, s);
+  if (e == cudaSuccess) e = launch_to_bf16(L.master, L.w_bf16, kMlpParams, s);
+  // training: Adam on stratified minibatches, cosine decay to lr / 10
+  for (uint32_t t = 1; t <= steps && e == cudaSuccess; ++t) {
+    const double c = 0.5 * (1.0 + std::cos(3.141592653589793 * double(t - 1) / double(steps)));
+    const float lr_t = float(lr * (0.1 + 0.9 * c));
+    e = launch_mlp_grad_sample(L.w_bf16, L.train, L.st, batch, t, o.seed, L.grads, s);
+    if (e == cudaSuccess)
+      e = launch_mlp_adam(L.master, L.grads, L.m1, L.m2, L.w_bf16, lr_t, int(t), L.st, L.loss_log + (t - 1), s);
+  }
+  if (e == cudaSuccess) e = launch_learn_cells(L.w_bf16, L.st, L.heavy, L.fval, L.cells, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  L.fitted = true;
+  L.steps = steps;
+  L.used = -1;
+  return finish_call(plan, s);
+}
+
+fsort_status fsort_learned_get_stats(fsort_plan* plan, fsort_learned_stats* out) {
+  if (!plan || !plan->learn || !out) return FSORT_ERR_INVALID_ARG;
+  LearnedWs& L = *plan->learn;
+  std::memset(out, 0, sizeof(*out));
+  if (cudaDeviceSynchronize() != cudaSuccess) return FSORT_ERR_CUDA;
+  out->fitted = L.fitted ? 1 : 0;
+  out->used = L.used;
+  out->buckets = L.last_b;
+  out->max_bucket = L.last_max;
+  out->limit = L.last_limit;
+  out->imbalance = L.last_imbalance;
+  out->tau = double(kLearnTau);
+  out->steps = L.steps;
+  if (L.fitted) {
+    LearnedState h{};
+    if (cudaMemcpy(&h, L.st, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return FSORT_ERR_CUDA;
+    out->heavy_keys = h.heavy_count;
+    out->sample_keys = h.sample_count;
+    out->train_keys = h.train_count;
+    if (L.steps) {
+      if (cudaMemcpy(&out->loss_first, L.loss_log, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(&out->loss_last, L.loss_log + (L.steps - 1), 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FSORT_ERR_CUDA;
+    }
+  }
+  return FSORT_OK;
+}
+
+fsort_status fsort_learned_get_model(fsort_plan* plan, float* params_host, uint32_t* cells_host, uint64_t* heavy_host,
+                                     uint32_t* heavy_count, float* norm) {
+  if (!plan || !plan->learn) return FSORT_ERR_INVALID_ARG;
+  LearnedWs& L = *plan->learn;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FSORT_ERR_CUDA;
+  LearnedState h{};
+  cudaError_t e = cudaMemcpy(&h, L.st, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && params_host)
+    e = cudaMemcpy(params_host, L.master, size_t(kMlpParams) * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && cells_host)
+    e = cudaMemcpy(cells_host, L.cells, size_t(kLearnCells + 1) * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && heavy_host)
+    e = cudaMemcpy(heavy_host, L.heavy, size_t(kLearnMaxHeavy) * 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return FSORT_ERR_CUDA;
+  if (heavy_count) *heavy_count = h.heavy_count;
+  if (norm) {
+    norm[0] = h.center;
+    norm[1] = h.half;
+  }
+  return FSORT_OK;
+}
+
+fsort_status fsort_learned_set_model(fsort_plan* plan, const float* params_host, const uint32_t* cells_host,
+                                     const uint64_t* heavy_host, uint32_t heavy_count, const float* norm,
+                                     void* stream) {
+  if (!plan || !plan->learn || !norm || !(norm[1] > 0.f)) return FSORT_ERR_INVALID_ARG;
+  if (heavy_count > uint32_t(kLearnMaxHeavy) || (heavy_count && !heavy_host)) return FSORT_ERR_INVALID_ARG;
+  if (!cells_host && !params_host) return FSORT_ERR_INVALID_ARG;
+  for (uint32_t t = 1; t < heavy_count; ++t)
+    if (heavy_host[t - 1] >= heavy_host[t]) return FSORT_ERR_INVALID_ARG;
+  if (cells_host) {  // G non-decreasing, last = all ones, H = frequent keys below each cell start
+    if (cells_host[2 * kLearnCells] != 0xFFFFFFFFu || cells_host[2 * kLearnCells + 1] != heavy_count)
+      return FSORT_ERR_INVALID_ARG;
+    uint32_t below = 0;
+    for (int i = 0; i < kLearnCells; ++i) {
+      if (cells_host[2 * i] > cells_host[2 * i + 2]) return FSORT_ERR_INVALID_ARG;
+      const uint64_t c = i < 2048 ? uint64_t(i) : uint64_t(1024 + (i & 1023)) << ((i >> 10) - 1);
+      while (below < heavy_count && heavy_host[below] < c) ++below;
+      if (cells_host[2 * i + 1] != below) return FSORT_ERR_INVALID_ARG;
+    }
+  }
+  LearnedWs& L = *plan->learn;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  fsort_status st = take_latched(plan, true, s);
+  if (st != FSORT_OK) return st;
+  LearnedState h{};
+  h.center = norm[0];
+  h.half = norm[1];
+  h.heavy_count = heavy_count;
+  L.fitted = false;
+  cudaError_t e = cudaMemcpyAsync(L.st, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.heavy, 0, size_t(kLearnMaxHeavy) * 8, s);
+  if (e == cudaSuccess && heavy_count)
+    e = cudaMemcpyAsync(L.heavy, heavy_host, size_t(heavy_count) * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && params_host) {
+    e = cudaMemcpyAsync(L.master, params_host, size_t(kMlpParams) * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_to_bf16(L.master, L.w_bf16, kMlpParams, s);
+  }
+  if (e == cudaSuccess) {
+    if (cells_host)
+      e = cudaMemcpyAsync(L.cells, cells_host, size_t(kLearnCells + 1) * 8, cudaMemcpyHostToDevice, s);
+    else
+      e = launch_learn_cells(L.w_bf16, L.st, L.heavy, L.fval, L.cells, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  L.fitted = true;
+  L.steps = 0;
+  L.used = -1;
+  return FSORT_OK;
+}
+
+fsort_status fsort_learned_bucket_ids(fsort_plan* plan, const void* keys, uint64_t n, uint32_t* ids, void* stream) {
+  if (!plan || !plan->learn || !plan->learn->fitted) return FSORT_ERR_INVALID_ARG;
+  if (n == 0) return FSORT_OK;
+  if (!keys || !ids || n >= (1ull << 32)) return FSORT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cudaError_t e = launch_learn_bucket_ids(static_cast<const uint64_t*>(keys), n,
+                                                learned_map(*plan->learn, n), ids, s);
+  return from_cuda(e);
+}
+
+fsort_status fsort_mlp_forward(const void* w_bf16, const float* x, uint32_t m, float* out, void* stream) {
+  if (!w_bf16 || !x || !out || m < 1) return FSORT_ERR_INVALID_ARG;
+  return from_cuda(launch_mlp_eval(w_bf16, x, m, out, static_cast<cudaStream_t>(stream)));
+}
+
+fsort_status fsort_mlp_grad(const void* w_bf16, const float* x, const float* y, uint32_t m, float* grads, float* loss,
+                            void* stream) {
+  if (!w_bf16 || !x || !y || !grads || m < 1) return FSORT_ERR_INVALID_ARG;
+  return from_cuda(launch_mlp_grad(w_bf16, x, y, m, grads, loss, static_cast<cudaStream_t>(stream)));
 }
 
 fsort_status fsort_plan_set_timing(fsort_plan* plan, int enable) {

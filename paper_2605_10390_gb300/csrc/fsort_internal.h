@@ -124,18 +124,102 @@ cudaError_t launch_fill_tile_seg(const SegDesc* segs, uint32_t nsegs, int tile_k
 cudaError_t launch_seg_copy_back(const SegDesc* segs, uint32_t nsegs, const void* alt_keys,
                                  const uint32_t* alt_vals, int key_bits, int sms, cudaStream_t stream);
 
-// ---- learned CDF model (fsort_learned.cu) ----
+// ---- learned bucket mapping (fsort_learned.cu) ----
 constexpr int kMlpHidden = 64;
 constexpr int kMlpParams = 1 * kMlpHidden + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden + kMlpHidden + 1;
-// grads += gradient of the mean squared error of sigmoid(mlp(x)) against y.
+constexpr int kLearnCells = 56320;        // cells of the 11-significant-bit grid over 64-bit keys
+constexpr int kLearnMaxHeavy = 8192;      // keys that get a bucket of their own
+constexpr int kLearnBucketCap = 8192;     // keys one CTA sorts on chip
+constexpr int kLearnKeysPerBucket = 1024; // B = smallest power of two >= n / 1024 (mean load in (512, 1024])
+constexpr int kLearnTau = 8;              // judge: accept iff max non-heavy bucket <= tau * n / B (<= capacity)
+constexpr float kLearnEps = 1.0f / 16.0f; // weight of the uniform-in-feature floor mixed into the model's CDF
+
+// Device-resident model and judge state.
+struct LearnedState {
+  float center, half;          // feature normalisation: x = (log2(k + 1) / 64 - center) / half
+  uint32_t heavy_count;        // m (<= kLearnMaxHeavy)
+  uint32_t train_count;        // non-heavy sample keys the model is trained on
+  uint32_t sample_count;
+  uint32_t max_nonheavy;       // judge: largest non-heavy bucket of the last histogram
+  uint32_t large_heavy;        // judge: heavy buckets above the fill split (listed in large_list)
+  uint32_t pad;
+  float loss;                  // accumulated by the gradient kernel, moved to the loss log by Adam
+  float pad2[3];
+};
+
+// The bucket map: cells[i] = (G_i, H_i) for i in [0, kLearnCells]: G = model
+// CDF at cell start (u32 fixed point, non-decreasing), H = heavy keys below
+// the cell start; heavy[] ascending; id = (PLA(k) >> shift) + 2 c(k) + e(k).
+struct LearnedMap {
+  const uint2* cells;
+  const uint64_t* heavy;
+  uint32_t shift;  // 32 - log2(B)
+};
+
+// grads += gradient of the mean (over m) of 0.5 (sigmoid(mlp(x)) - y)^2; loss += that mean.
 cudaError_t launch_mlp_grad(const void* w_bf16, const float* x, const float* y, uint32_t m, float* grads, float* loss,
                             cudaStream_t stream);
-// One Adam step (step >= 1): master/m1/m2 FP32, grads zeroed, BF16 copy refreshed.
+// Same on a stratified minibatch of m keys of the sorted training sample (step selects the draw).
+cudaError_t launch_mlp_grad_sample(const void* w_bf16, const uint64_t* train, const LearnedState* st, uint32_t m,
+                                   uint32_t step, uint64_t seed, float* grads, cudaStream_t stream);
+// One Adam step (step >= 1): master/m1/m2 FP32, grads zeroed, BF16 copy
+// refreshed; if loss_log: loss_log[0] = st->loss, st->loss = 0.
 cudaError_t launch_mlp_adam(float* master, float* grads, float* m1, float* m2, void* w_bf16, float lr, int step,
-                            cudaStream_t stream);
+                            LearnedState* st, float* loss_log, cudaStream_t stream);
 cudaError_t launch_mlp_eval(const void* w_bf16, const float* x, uint32_t m, float* out, cudaStream_t stream);
 cudaError_t launch_to_bf16(const float* src, void* dst, int count, cudaStream_t stream);
-cudaError_t launch_mlp_invert(const void* w_bf16, float center, float half, uint64_t lo_key, uint64_t hi_key,
-                              uint32_t buckets, uint64_t* splitters, cudaStream_t stream);
+
+// Fitting: stratified sample of s keys; heavy/non-heavy split of the sorted
+// sample; compaction; the tabulated map.
+cudaError_t launch_learn_sample(const uint64_t* keys, uint64_t n, uint32_t s, uint64_t seed, uint64_t* out,
+                                cudaStream_t stream);
+cudaError_t launch_learn_split(const uint64_t* sorted, uint32_t s, uint32_t hmin, uint32_t* flag_nh,
+                               uint32_t* flag_hv, cudaStream_t stream);
+cudaError_t launch_learn_compact(const uint64_t* sorted, uint32_t s, const uint32_t* flag_nh, const uint32_t* pos_nh,
+                                 const uint32_t* flag_hv, const uint32_t* pos_hv, uint64_t* train, uint64_t* heavy,
+                                 LearnedState* st, cudaStream_t stream);
+// Move the first-layer kinks to quantiles of the training sample (FP32 master weights).
+cudaError_t launch_learn_init_kinks(const uint64_t* train, const LearnedState* st, float* master,
+                                    cudaStream_t stream);
+cudaError_t launch_learn_cells(const void* w_bf16, LearnedState* st, const uint64_t* heavy, float* fval, uint2* cells,
+                               cudaStream_t stream);
+
+// Exclusive scan of count u32 words (count <= 2^24): out (and out2 if not
+// null); sums: scratch of >= count / 4096 + 1 words.
+cudaError_t launch_scan_u32(const uint32_t* in, uint64_t count, uint32_t* out, uint32_t* out2, uint32_t* sums,
+                            cudaStream_t stream);
+
+// Sorting with the map: two-level partition geometry for a sort of n keys.
+constexpr uint32_t kLearnL1Chunks = 4096;  // most level-1 chunks (input ranges owned by one CTA)
+struct LearnedGeom {
+  uint32_t nb;      // bucket ids in use: B + 2 * kLearnMaxHeavy
+  uint32_t nsuper;  // super-buckets (id >> 10)
+  uint32_t nids;    // nsuper * 1024 (ids beyond nb are empty)
+  uint32_t nch;     // level-1 chunks
+  uint64_t chunk;   // keys per level-1 chunk
+};
+LearnedGeom learned_geometry(uint64_t n, uint32_t buckets);
+cudaError_t launch_learn_heavy_ids(const LearnedMap& mp, LearnedState* st, uint32_t* hid, uint32_t* bitmap,
+                                   cudaStream_t stream);
+// counts1[nsuper * nch] (super-bucket major), hcount[kLearnMaxHeavy] accumulated.
+cudaError_t launch_learn_l1(const uint64_t* keys, uint64_t n, const LearnedGeom& g, const LearnedMap& mp,
+                            const LearnedState* st, uint32_t* counts1, uint32_t* hcount, cudaStream_t stream);
+// off1: exclusive scan of counts1 with one extra entry (the total).
+cudaError_t launch_learn_l1_scatter(const uint64_t* keys, uint64_t n, const LearnedGeom& g, const LearnedMap& mp,
+                                    const uint32_t* off1, uint64_t* alt, cudaStream_t stream);
+cudaError_t launch_learn_l2_count(const uint64_t* alt, const LearnedGeom& g, const LearnedMap& mp,
+                                  const uint32_t* off1, uint32_t* counts, cudaStream_t stream);
+cudaError_t launch_learn_judge(uint32_t* counts, const LearnedGeom& g, const uint32_t* bitmap, const uint32_t* hid,
+                               const uint32_t* hcount, LearnedState* st, uint32_t* large_list, cudaStream_t stream);
+cudaError_t launch_learn_l2_scatter(const uint64_t* alt, const LearnedGeom& g, const LearnedMap& mp,
+                                    const uint32_t* off1, const uint32_t* off2, uint64_t* dst, cudaStream_t stream);
+cudaError_t launch_learn_fill(const LearnedMap& mp, const LearnedState* st, const uint32_t* hid,
+                              const uint32_t* large_list, const uint32_t* offsets, const uint32_t* counts,
+                              uint64_t* dst, int sms, cudaStream_t stream);
+cudaError_t launch_learn_bucket_sort(uint64_t* keys, const uint32_t* counts, const uint32_t* offsets,
+                                     const uint32_t* bitmap, uint32_t nb, const uint2* cells, uint32_t* status,
+                                     int sms, cudaStream_t stream);
+cudaError_t launch_learn_bucket_ids(const uint64_t* keys, uint64_t n, const LearnedMap& mp, uint32_t* ids,
+                                    cudaStream_t stream);
 
 }  // namespace fsort

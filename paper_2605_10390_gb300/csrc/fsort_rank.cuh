@@ -75,9 +75,13 @@ struct Item<uint16_t> {
 // same-address additions, while the hardware match.any is fast when a round
 // has few distinct digits: the warp picks the method for its whole strip from
 // its first round (a speed choice only; both give the same ranks).
-template <typename K, int kIpt>
+//
+// kDyn: the strip has only `rounds` (<= kIpt) rounds (a warp-uniform bound);
+// items of later rounds are left untouched.
+template <typename K, int kIpt, bool kDyn = false>
 __device__ __forceinline__ void rank_strip(const K* s_keys, uint32_t tile_n, int wbase, uint32_t shift, uint32_t mask,
-                                           uint32_t* wmask0, uint32_t* wmask1, uint32_t* wcnt, Item<K> (&it)[kIpt]) {
+                                           uint32_t* wmask0, uint32_t* wmask1, uint32_t* wcnt, Item<K> (&it)[kIpt],
+                                           int rounds = kIpt) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = lanemask_lt(), me = 1u << lane;
   // Locally skewed strips (presorted runs, constant digits): same-address
@@ -93,6 +97,7 @@ __device__ __forceinline__ void rank_strip(const K* s_keys, uint32_t tile_n, int
   }
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
+    if (kDyn && i >= rounds) break;
     const int pos = wbase + i * 32 + lane;
     const bool valid = uint32_t(pos) < tile_n;
     const K k = valid ? s_keys[pos] : K(0);

@@ -20,6 +20,9 @@ Named distributions (16-bit top part; wider keys get uniform low bits):
   presorted  ascending ramp on the top 16 bits with 10 % of elements replaced
              by uniform draws
   equal      every key 0xA5A5...
+  mixture    (64-bit keys) 90 % from 8 lognormal clusters (ln-means U[20,40], ln-sigmas
+             U[0.1,1], Dirichlet(1) weights) through a 65,537-point piecewise-linear
+             inverse CDF, 10 % Zipf s=1.3 over 65,536 hot values drawn from the mixture
 """
 from __future__ import annotations
 
@@ -155,15 +158,71 @@ def table_for(name: str, key_bits: int):
     return _table_cache[key]
 
 
+_MIX_CACHE: dict = {}
+
+
+def lognormal_mixture(seed: int = 0, clusters: int = 8):
+    """Mixture of `clusters` lognormal clusters: ln-means ~ U[20, 40], ln-sigmas
+    ~ U[0.1, 1], weights ~ Dirichlet(1), all from `seed`.  Returns (mu, sigma, w)."""
+    rng = np.random.default_rng(1000 + seed)
+    mu = rng.uniform(20.0, 40.0, clusters)
+    sigma = rng.uniform(0.1, 1.0, clusters)
+    w = rng.dirichlet(np.ones(clusters))
+    return mu, sigma, w
+
+
+def _mixture_cdf(logx: np.ndarray, mu, sigma, w) -> np.ndarray:
+    z = (logx[:, None] - mu[None, :]) / (sigma[None, :] * math.sqrt(2.0))
+    erf = np.vectorize(math.erf)
+    return (w[None, :] * 0.5 * (1.0 + erf(z))).sum(axis=1)
+
+
+def mixture_tables(seed: int = 0):
+    """Plain data for the learned-sort workload: 65,537 ascending u64 quantile
+    points of the lognormal mixture (piecewise-linear inverse CDF), 65,536
+    hot values drawn from the mixture, and the Zipf s=1.3 threshold table over
+    their ranks.  Computed in float64 by bisection on ln(key)."""
+    if seed in _MIX_CACHE:
+        return _MIX_CACHE[seed]
+    mu, sigma, w = lognormal_mixture(seed)
+    probs = np.arange(65537, dtype=np.float64) / 65536.0
+    probs[0], probs[-1] = 1e-9, 1.0 - 1e-9
+    lo = np.full(probs.shape, float((mu - 8 * sigma).min()))
+    hi = np.full(probs.shape, min(float((mu + 8 * sigma).max()), 44.0))
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        below = _mixture_cdf(mid, mu, sigma, w) < probs
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    keys = np.minimum(np.exp(hi), 2.0 ** 64 - 4096.0)
+    quant = np.maximum.accumulate(keys.astype(np.uint64))
+    rng = np.random.default_rng(2000 + seed)
+    u = rng.random(65536)
+    idx = np.minimum((u * 65536).astype(np.int64), 65535)
+    frac = u * 65536 - idx
+    hot = (quant[idx] + (quant[idx + 1] - quant[idx]) * frac).astype(np.uint64)
+    table = thresholds_from_pmf(zipf_pmf(1.3))
+    _MIX_CACHE[seed] = (quant, hot, table)
+    return _MIX_CACHE[seed]
+
+
+MIXTURE_HOT_PROB = int(0.1 * 2 ** 32)
+
+
 def params_for(name: str, n_total: int, key_bits: int, seed: int, stream: int):
     """(WlParams, table) for a named distribution; the table (or None) must be
     kept alive, and for device use copied to the device and its pointer set."""
     if key_bits not in _KEY_DTYPES:
         raise ValueError("key_bits must be 16, 32 or 64")
+    if name == "mixture":
+        quant, hot, table = mixture_tables(0)
+        p = WlParams(seed=seed, stream=stream, n_total=n_total, dist=WL_HOTSET, key_bits=key_bits,
+                     hot_prob=MIXTURE_HOT_PROB, pad=0, table=None, quant=None, hot=None)
+        return p, (table, quant, hot)
     dist = {"uniform": WL_UNIFORM, "zipf1.1": WL_TABLE, "gauss": WL_TABLE, "presorted": WL_PRESORTED,
             "equal": WL_CONSTANT}.get(name)
     if dist is None:
-        raise ValueError(f"unknown distribution {name!r}; known: {DISTRIBUTIONS}")
+        raise ValueError(f"unknown distribution {name!r}; known: {DISTRIBUTIONS + ('mixture',)}")
     table = table_for(name, key_bits)
     p = WlParams(seed=seed, stream=stream, n_total=n_total, dist=dist, key_bits=key_bits, hot_prob=0, pad=0,
                  table=None, quant=None, hot=None)
@@ -175,7 +234,9 @@ def generate(name: str, n: int, key_bits: int = 16, seed: int = 0, stream: int =
     """Keys start..start+n-1 of a workload of n_total (default n) keys, on the host."""
     lib = _host_lib()
     p, table = params_for(name, n if n_total is None else n_total, key_bits, seed, stream)
-    if table is not None:
+    if isinstance(table, tuple):
+        p.table, p.quant, p.hot = (t.ctypes.data_as(ctypes.c_void_p).value for t in table)
+    elif table is not None:
         p.table = table.ctypes.data_as(ctypes.c_void_p).value
     out = np.empty(n, dtype=_KEY_DTYPES[key_bits])
     rc = lib.wl_fill(out.ctypes.data_as(ctypes.c_void_p), start, n, ctypes.byref(p))
@@ -190,7 +251,11 @@ def generate_device(name: str, out_ptr: int, n: int, key_bits: int, seed: int = 
     distributions, table_dev_ptr must point at a device copy of table_for()."""
     lib = _dev_lib()
     p, table = params_for(name, n if n_total is None else n_total, key_bits, seed, stream)
-    if table is not None:
+    if isinstance(table, tuple):
+        if not isinstance(table_dev_ptr, (tuple, list)) or len(table_dev_ptr) != 3:
+            raise ValueError("the mixture needs (table, quantiles, hot values) device pointers")
+        p.table, p.quant, p.hot = table_dev_ptr
+    elif table is not None:
         if table_dev_ptr is None:
             raise ValueError("table distribution needs table_dev_ptr")
         p.table = table_dev_ptr
