@@ -262,8 +262,8 @@ def test_learned_beats_plain_on_the_mixture():
     """What the trained network gains: on 2^28 keys of the lognormal mixture
     the judged learned path is faster than the plain radix path, with the
     identical output (the learned path's parity with the oracle is covered
-    above; here the two GPU paths must agree bit for bit, and a strided sample
-    of the output is checked against the oracle's sort of the same keys)."""
+    above; here the two GPU paths must agree bit for bit, and sampled output
+    positions are checked against the definition of the sorted order)."""
     n = 1 << 28
     d = mixture_device(n)
     with learned_plan(n) as lp, fs.Plan(n, 64, has_values=False) as pp:
@@ -273,11 +273,14 @@ def test_learned_beats_plain_on_the_mixture():
         assert st["used"] == 1, st
         t_plain, out_p = _time_sorts(pp, d)
     assert torch.equal(out_l, out_p)
-    # ranks by counting: out[i] is the key of rank i in the oracle's sorted order
+    # sampled positions against the definition of the sorted multiset:
+    # out[i] = v iff #{keys < v} <= i < #{keys <= v}
     keys = d.cpu().numpy()
-    want = oracle.sort(keys[:: 1 << 8].copy(), None, 64, 64)[0]
-    got = out_l[:: 1 << 8].cpu().numpy()
-    assert np.all(np.diff(got.astype(np.float64)) >= 0) and got.size == want.size
+    out = out_l.cpu().numpy()
+    for i in np.random.default_rng(5).integers(0, n, 12).tolist() + [0, n - 1]:
+        v = out[i]
+        below = int(np.count_nonzero(keys < v))
+        assert below <= i < below + int(np.count_nonzero(keys == v)), i
     print(f"learned {t_learned:.2f} ms  plain {t_plain:.2f} ms  ({t_plain / t_learned:.2f}x) imbalance "
           f"{st['imbalance']:.2f}")
     assert t_learned < t_plain
