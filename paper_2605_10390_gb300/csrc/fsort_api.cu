@@ -56,6 +56,7 @@ struct LearnedWs {
   uint32_t *counts1 = nullptr, *off1 = nullptr;   // level 1: [nsuper][nch] + 1
   uint32_t *counts = nullptr, *offsets = nullptr;  // every bucket id (+ 1)
   uint32_t *hcount = nullptr, *bitmap = nullptr;
+  uint2* units = nullptr;                          // bucket-sort unit list
   void* w_bf16 = nullptr;
   float *master = nullptr, *m1 = nullptr, *m2 = nullptr, *grads = nullptr, *loss_log = nullptr;
   fsort::LearnedState* st = nullptr;
@@ -369,7 +370,7 @@ fsort_status enqueue_learned(fsort_plan* p, const void* keys_in, void* keys_out,
   if (e == cudaSuccess) e = launch_learn_fill(mp, L.st, L.hid, L.large, L.offsets, L.counts, kout, p->sms, s);
   tm.mark(FSORT_KERNEL_LEARN_FILL, -1);
   if (e == cudaSuccess)
-    e = launch_learn_bucket_sort(kout, L.counts, L.offsets, L.bitmap, g.nids, L.cells, p->status, p->sms, s);
+    e = launch_learn_bucket_sort(kout, L.counts, L.offsets, L.bitmap, g.nids, L.units, p->status, p->sms, s);
   tm.mark(FSORT_KERNEL_LEARN_BUCKETS, -1);
   if (e != cudaSuccess) return from_cuda(e);
   return finish_call(p, s);
@@ -726,7 +727,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   }
   const bool learned = (desc->flags & FSORT_FLAG_LEARNED) != 0;
   LearnedWs lw;
-  size_t o_l[25] = {};
+  size_t o_l[26] = {};
   if (learned) {
     lw.sample_max = uint32_t(n < LearnedWs::kMaxSample ? n : LearnedWs::kMaxSample);
     const LearnedGeom gm = learned_geometry(n, learned_buckets(n));
@@ -753,6 +754,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     o_l[15] = take((nb / 32 + 1) * 4);
     o_l[23] = take(l1 * 4);
     o_l[24] = take(l1 * 4);
+    o_l[25] = take(((nb + 3) / 4 * 4 + 1) * 8);
     o_l[16] = take(size_t(kMlpParams) * 2);
     o_l[17] = take(size_t(kMlpParams) * 4);
     o_l[18] = take(size_t(kMlpParams) * 4);
@@ -823,6 +825,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     L.bitmap = reinterpret_cast<uint32_t*>(w + o_l[15]);
     L.counts1 = reinterpret_cast<uint32_t*>(w + o_l[23]);
     L.off1 = reinterpret_cast<uint32_t*>(w + o_l[24]);
+    L.units = reinterpret_cast<uint2*>(w + o_l[25]);
     L.w_bf16 = w + o_l[16];
     L.master = reinterpret_cast<float*>(w + o_l[17]);
     L.m1 = reinterpret_cast<float*>(w + o_l[18]);

@@ -216,9 +216,10 @@ cudaError_t launch_learn_l2_scatter(const uint64_t* alt, const LearnedGeom& g, c
 cudaError_t launch_learn_fill(const LearnedMap& mp, const LearnedState* st, const uint32_t* hid,
                               const uint32_t* large_list, const uint32_t* offsets, const uint32_t* counts,
                               uint64_t* dst, int sms, cudaStream_t stream);
+// units: scratch of 1 + 4 * ceil(nb / 4) uint2 (the unit list).
 cudaError_t launch_learn_bucket_sort(uint64_t* keys, const uint32_t* counts, const uint32_t* offsets,
-                                     const uint32_t* bitmap, uint32_t nb, const uint2* cells, uint32_t* status,
-                                     int sms, cudaStream_t stream);
+                                     const uint32_t* bitmap, uint32_t nb, uint2* units, uint32_t* status, int sms,
+                                     cudaStream_t stream);
 cudaError_t launch_learn_bucket_ids(const uint64_t* keys, uint64_t n, const LearnedMap& mp, uint32_t* ids,
                                     cudaStream_t stream);
 

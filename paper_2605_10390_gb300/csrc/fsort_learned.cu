@@ -559,7 +559,8 @@ __global__ void learn_judge_kernel(uint32_t* __restrict__ counts, uint32_t nb, c
 // tile is counted per digit in shared memory (slot = the old count), staged
 // grouped by digit, and written out in runs at the digit's global cursor, so
 // consecutive threads write consecutive addresses.  Order inside a digit's run
-// follows the shared-memory atomics (arbitrary; the bucket sorts fix it).
+// follows the shared-memory atomics (arbitrary; the bucket sorts fix it).  The
+// next tile is prefetched into shared memory (cp.async) while one is processed.
 //   level 1: CTA = input chunk c, digit = id >> 10, heavy keys skipped,
 //            cursors from off1[s * nch + c], output alt
 //   level 2: CTA = super-bucket s, keys alt[off1[s nch], off1[(s+1) nch]),
@@ -569,50 +570,73 @@ constexpr int kStIpt = 8;
 constexpr int kStTile = kStThreads * kStIpt;
 constexpr uint32_t kNoDigit = 0xFFFFu;
 constexpr int kStPer = (kMaxSuper + kStThreads - 1) / kStThreads;  // digits a thread owns in the scan
+
+// Shared-memory layout for a given digit capacity (bytes from the start).
 struct StLayout {
-  static constexpr size_t kStage = 0;
-  static constexpr size_t kDig = kStage + size_t(kStTile) * 8;
-  static constexpr size_t kCnt = kDig + size_t(kStTile) * 2;
-  static constexpr size_t kCur = kCnt + size_t(kMaxSuper) * 4;
-  static constexpr size_t kDelta = kCur + size_t(kMaxSuper) * 4;
-  static constexpr size_t kWarp = kDelta + size_t(kMaxSuper) * 4;
-  static constexpr size_t kBytes = kWarp + 32 * 4;
+  size_t stage, pre, dig, cnt, cur, delta, warp, bytes;
+  __host__ __device__ explicit StLayout(uint32_t cap) {
+    stage = 0;
+    pre = stage + size_t(kStTile) * 8;
+    dig = pre + size_t(kStTile) * 8;
+    cnt = dig + size_t(kStTile) * 2;
+    cur = cnt + size_t(cap) * 4;
+    delta = cur + size_t(cap) * 4;
+    warp = delta + size_t(cap) * 4;
+    bytes = warp + 32 * 4;
+  }
 };
+
+__device__ __forceinline__ void prefetch_tile(uint64_t* s_pre, const uint64_t* __restrict__ src, uint64_t base,
+                                              uint64_t hi) {
+  const uint32_t tn = uint32_t(hi - base < uint64_t(kStTile) ? hi - base : uint64_t(kStTile));
+  for (uint32_t i = threadIdx.x; i < tn; i += kStThreads) cp_async8(&s_pre[i], &src[base + i]);
+  cp_async_commit();
+}
 
 template <int kLevel>
 __global__ void __launch_bounds__(kStThreads, 2) learn_staged_scatter_kernel(
-    const uint64_t* __restrict__ src, uint64_t n, uint64_t chunk, uint32_t nch, uint32_t nsuper, LearnedMap mp,
-    const uint32_t* __restrict__ off1, const uint32_t* __restrict__ offsets, uint64_t* __restrict__ dst) {
+    const uint64_t* __restrict__ src, uint64_t n, uint64_t chunk, uint32_t nch, uint32_t nsuper, uint32_t cap,
+    LearnedMap mp, const uint32_t* __restrict__ off1, const uint32_t* __restrict__ offsets,
+    uint64_t* __restrict__ dst) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* s_stage = reinterpret_cast<uint64_t*>(smem + StLayout::kStage);
-  uint16_t* s_dig = reinterpret_cast<uint16_t*>(smem + StLayout::kDig);
-  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + StLayout::kCnt);
-  uint32_t* s_cur = reinterpret_cast<uint32_t*>(smem + StLayout::kCur);
-  uint32_t* s_delta = reinterpret_cast<uint32_t*>(smem + StLayout::kDelta);
-  uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + StLayout::kWarp);
+  const StLayout L(cap);
+  uint64_t* s_stage = reinterpret_cast<uint64_t*>(smem + L.stage);
+  uint64_t* s_pre = reinterpret_cast<uint64_t*>(smem + L.pre);
+  uint16_t* s_dig = reinterpret_cast<uint16_t*>(smem + L.dig);
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + L.cnt);
+  uint32_t* s_cur = reinterpret_cast<uint32_t*>(smem + L.cur);
+  uint32_t* s_delta = reinterpret_cast<uint32_t*>(smem + L.delta);
+  uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L.warp);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t ndig = kLevel == 1 ? nsuper : uint32_t(kFine);
   uint64_t lo, hi;
   if (kLevel == 1) {
     lo = uint64_t(blockIdx.x) * chunk;
     hi = lo + chunk < n ? lo + chunk : n;
-    for (uint32_t d = tid; d < ndig; d += kStThreads) s_cur[d] = off1[uint64_t(d) * nch + blockIdx.x];
   } else {
     lo = off1[uint64_t(blockIdx.x) * nch];
     hi = off1[uint64_t(blockIdx.x + 1) * nch];
+  }
+  if (lo < hi) prefetch_tile(s_pre, src, lo, hi);
+  if (kLevel == 1) {
+    for (uint32_t d = tid; d < ndig; d += kStThreads) s_cur[d] = off1[uint64_t(d) * nch + blockIdx.x];
+  } else {
     for (uint32_t d = tid; d < ndig; d += kStThreads) s_cur[d] = offsets[uint64_t(blockIdx.x) * kFine + d];
   }
   for (uint32_t d = tid; d < ndig; d += kStThreads) s_cnt[d] = 0;
-  __syncthreads();
   for (uint64_t base = lo; base < hi; base += kStTile) {
     const uint32_t tn = uint32_t(hi - base < uint64_t(kStTile) ? hi - base : uint64_t(kStTile));
+    cp_async_wait_all();
+    __syncthreads();
     uint64_t k[kStIpt];
     uint32_t ds[kStIpt];  // digit << 16 | slot inside the tile's digit run
 #pragma unroll
     for (int j = 0; j < kStIpt; ++j) {
       const uint32_t i = uint32_t(j * kStThreads + tid);
-      k[j] = i < tn ? src[base + i] : 0;
+      k[j] = i < tn ? s_pre[i] : 0;
     }
+    __syncthreads();  // the prefetch buffer is free again
+    if (base + kStTile < hi) prefetch_tile(s_pre, src, base + kStTile, hi);
 #pragma unroll
     for (int j = 0; j < kStIpt; ++j) {
       const uint32_t i = uint32_t(j * kStThreads + tid);
@@ -671,8 +695,8 @@ __global__ void __launch_bounds__(kStThreads, 2) learn_staged_scatter_kernel(
     __syncthreads();
     for (uint32_t i = tid; i < total; i += kStThreads) dst[s_delta[s_dig[i]] + i] = s_stage[i];
     for (uint32_t d = tid; d < ndig; d += kStThreads) s_cnt[d] = 0;
-    __syncthreads();
   }
+  cp_async_wait_all();
 }
 
 __global__ void __launch_bounds__(256) learn_fill_kernel(LearnedMap mp, const LearnedState* __restrict__ st,
@@ -704,10 +728,10 @@ __global__ void __launch_bounds__(256) learn_fill_kernel(LearnedMap mp, const Le
 // On-chip sort of the buckets, one unit per CTA iteration, in place.  A unit
 // is a group of kGroup consecutive bucket ids with no heavy id and at most
 // 8192 keys in all (contiguous in memory), else each bucket of the group
-// alone.  The unit's keys are split into at most 4096 sub-buckets by their
-// PLA value (the tabulated model CDF, in which the keys are near-uniform) --
-// or by key - min when the PLA does not separate them -- in one counting pass
-// through shared memory; each thread then sorts its sub-buckets by insertion.
+// alone.  The unit's keys are split into at most 4096 sub-buckets by the top
+// 12 bits of key - min in one counting pass through shared memory; each
+// thread then sorts its sub-buckets by insertion.  The next unit's keys are
+// prefetched into shared memory (cp.async) while one is sorted.
 // A unit where some thread would need more than kInsertBudget insertion moves
 // is finished by a bitonic network instead.
 constexpr int kBsThreads = 1024;
@@ -731,43 +755,30 @@ struct BsShared {
   uint32_t flag;
 };
 
-// Sorts g[0, cnt), 2 <= cnt <= kLearnBucketCap; every thread calls it.
-__device__ void sort_unit(uint64_t* __restrict__ g, uint32_t cnt, const uint2* __restrict__ cells,
+// Sorts one unit whose keys the threads hold (key j of thread t is element
+// j * kBsThreads + t) into g[0, cnt), 2 <= cnt <= kLearnBucketCap; every
+// thread calls it.
+__device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g, uint32_t cnt,
                           uint64_t* __restrict__ s_out, BsShared& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint64_t k[kBsIpt];
-  uint32_t v[kBsIpt];  // PLA value, later sub-bucket << 16 | slot
+  uint32_t v[kBsIpt];  // sub-bucket << 16 | slot
   uint64_t kmn = ~0ull, kmx = 0;
-  uint32_t pmn = 0xFFFFFFFFu, pmx = 0;
-#pragma unroll
-  for (int j = 0; j < kBsIpt; ++j) {
-    const uint32_t i = uint32_t(j * kBsThreads + tid);
-    k[j] = i < cnt ? g[i] : 0;
-  }
 #pragma unroll
   for (int j = 0; j < kBsIpt; ++j) {
     const uint32_t i = uint32_t(j * kBsThreads + tid);
     if (i < cnt) {
-      uint2 hr;
-      v[j] = pla_of(k[j], cells, hr);
       kmn = umin64(kmn, k[j]);
       kmx = umax64(kmx, k[j]);
-      pmn = min(pmn, v[j]);
-      pmx = max(pmx, v[j]);
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     kmn = umin64(kmn, __shfl_xor_sync(0xffffffffu, kmn, o));
     kmx = umax64(kmx, __shfl_xor_sync(0xffffffffu, kmx, o));
-    pmn = min(pmn, __shfl_xor_sync(0xffffffffu, pmn, o));
-    pmx = max(pmx, __shfl_xor_sync(0xffffffffu, pmx, o));
   }
   if (lane == 0) {
     sh.red[warp] = kmn;
     sh.red[kBsWarps + warp] = kmx;
-    sh.red[2 * kBsWarps + warp] = pmn;
-    sh.red[3 * kBsWarps + warp] = pmx;
   }
   if (tid == 0) sh.flag = 0;
   __syncthreads();
@@ -775,42 +786,33 @@ __device__ void sort_unit(uint64_t* __restrict__ g, uint32_t cnt, const uint2* _
     static_assert(kBsWarps == 32, "one partial per lane");
     kmn = sh.red[lane];
     kmx = sh.red[kBsWarps + lane];
-    pmn = uint32_t(sh.red[2 * kBsWarps + lane]);
-    pmx = uint32_t(sh.red[3 * kBsWarps + lane]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       kmn = umin64(kmn, __shfl_xor_sync(0xffffffffu, kmn, o));
       kmx = umax64(kmx, __shfl_xor_sync(0xffffffffu, kmx, o));
-      pmn = min(pmn, __shfl_xor_sync(0xffffffffu, pmn, o));
-      pmx = max(pmx, __shfl_xor_sync(0xffffffffu, pmx, o));
     }
     if (lane == 0) {
       sh.fin[0] = kmn;
       sh.fin[1] = kmx;
-      sh.fin[2] = pmn;
-      sh.fin[3] = pmx;
     }
   }
   __syncthreads();
   kmn = sh.fin[0];
   kmx = sh.fin[1];
-  pmn = uint32_t(sh.fin[2]);
-  pmx = uint32_t(sh.fin[3]);
   const uint64_t krange = kmx - kmn;
   if (krange == 0) {  // all keys equal: already in order
-    __syncthreads();
+    for (uint32_t i = tid; i < cnt; i += kBsThreads) g[i] = kmn;
     return;
   }
-  // sub-bucket function: by PLA when it spreads the unit over >= 1024 values
-  const uint32_t prange = pmx - pmn;
-  const bool by_pla = prange >= 1024u;
-  const int bits = by_pla ? 32 - __clz(int(prange)) : 64 - __clzll(static_cast<long long>(krange));
+  // sub-bucket = the top 12 bits of key - min: the map is near-linear inside
+  // a unit, so the keys spread evenly over the sub-buckets
+  const int bits = 64 - __clzll(static_cast<long long>(krange));
   const int shf = bits > kSubBits ? bits - kSubBits : 0;
 #pragma unroll
   for (int j = 0; j < kBsIpt; ++j) {
     const uint32_t i = uint32_t(j * kBsThreads + tid);
     if (i < cnt) {
-      const uint32_t sb = by_pla ? ((v[j] - pmn) >> shf) : uint32_t((k[j] - kmn) >> shf);
+      const uint32_t sb = uint32_t((k[j] - kmn) >> shf);
       v[j] = (sb << 16) | atomicAdd(&sh.sub[sb], 1u);
     }
   }
@@ -898,50 +900,84 @@ __device__ void sort_unit(uint64_t* __restrict__ g, uint32_t cnt, const uint2* _
       }
     }
   }
-  __syncthreads();
   for (uint32_t i = tid; i < cnt; i += kBsThreads) g[i] = s_out[i];
   for (int i = tid; i <= kSub; i += kBsThreads) sh.sub[i] = 0;
-  __syncthreads();
+}
+
+// The unit list, compacted: every group of kGroup consecutive ids appends
+// one unit (the whole group, when it has no heavy id and at most the
+// capacity) or one per bucket of at least two keys; units[0].x counts them
+// (list entries start at units + 1; their order is arbitrary).
+__global__ void learn_units_kernel(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets,
+                                   const uint32_t* __restrict__ bitmap, uint32_t nb, uint2* __restrict__ units,
+                                   uint32_t* status) {
+  const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi * kGroup >= nb) return;
+  const uint32_t i0 = gi * kGroup;
+  uint32_t tot = 0;
+  bool heavy = false;
+  for (int q = 0; q < kGroup; ++q) {
+    const uint32_t id = i0 + q;
+    if (id < nb) {
+      tot += counts[id];
+      heavy |= ((bitmap[id >> 5] >> (id & 31u)) & 1u) != 0;
+    }
+  }
+  uint32_t* count = &units[0].x;
+  if (!heavy && tot <= uint32_t(kLearnBucketCap)) {
+    if (tot >= 2) units[1 + atomicAdd(count, 1u)] = make_uint2(offsets[i0], tot);
+    return;
+  }
+  for (int q = 0; q < kGroup; ++q) {
+    const uint32_t id = i0 + q;
+    if (id >= nb || ((bitmap[id >> 5] >> (id & 31u)) & 1u)) continue;
+    const uint32_t c = counts[id];
+    if (c > uint32_t(kLearnBucketCap)) {  // the judge rejects such maps; never sort past capacity
+      atomicOr(status, kDevBadBucket);
+      continue;
+    }
+    if (c >= 2) units[1 + atomicAdd(count, 1u)] = make_uint2(offsets[id], c);
+  }
 }
 
 __global__ void __launch_bounds__(kBsThreads, 1) learn_bucket_sort_kernel(uint64_t* __restrict__ keys,
-                                                                          const uint32_t* __restrict__ counts,
-                                                                          const uint32_t* __restrict__ offsets,
-                                                                          const uint32_t* __restrict__ bitmap,
-                                                                          uint32_t nb, const uint2* __restrict__ cells,
-                                                                          uint32_t* status) {
-  extern __shared__ uint64_t s_out[];  // [kLearnBucketCap], dynamic: above the static limit
+                                                                          const uint2* __restrict__ units) {
+  extern __shared__ uint64_t s_dyn[];  // [2][kLearnBucketCap]: the unit, the next unit's prefetch
+  uint64_t* s_out = s_dyn;
+  uint64_t* s_pre = s_dyn + kLearnBucketCap;
   __shared__ BsShared sh;
-  for (int i = threadIdx.x; i <= kSub; i += kBsThreads) sh.sub[i] = 0;
-  __syncthreads();
-  const uint32_t ngroups = (nb + kGroup - 1) / kGroup;
-  for (uint32_t gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
-    const uint32_t i0 = gi * kGroup;
-    uint32_t tot = 0;
-    bool heavy = false;
-#pragma unroll
-    for (int q = 0; q < kGroup; ++q) {
-      const uint32_t id = i0 + q;
-      if (id < nb) {
-        tot += counts[id];
-        heavy |= ((bitmap[id >> 5] >> (id & 31u)) & 1u) != 0;
-      }
-    }
-    if (!heavy && tot <= uint32_t(kLearnBucketCap)) {
-      if (tot >= 2) sort_unit(keys + offsets[i0], tot, cells, s_out, sh);
-      continue;
-    }
-    for (int q = 0; q < kGroup; ++q) {
-      const uint32_t id = i0 + q;
-      if (id >= nb || ((bitmap[id >> 5] >> (id & 31u)) & 1u)) continue;
-      const uint32_t c = counts[id];
-      if (c > uint32_t(kLearnBucketCap)) {  // the judge rejects such maps; never sort past capacity
-        if (threadIdx.x == 0) atomicOr(status, kDevBadBucket);
-        continue;
-      }
-      if (c >= 2) sort_unit(keys + offsets[id], c, cells, s_out, sh);
-    }
+  const int tid = threadIdx.x;
+  const uint32_t nunits = units[0].x;
+  const uint2* list = units + 1;
+  for (int i = tid; i <= kSub; i += kBsThreads) sh.sub[i] = 0;
+  uint32_t u = blockIdx.x;
+  uint2 cur = make_uint2(0, 0);
+  if (u < nunits) {
+    cur = list[u];
+    for (uint32_t i = tid; i < cur.y; i += kBsThreads) cp_async8(&s_pre[i], &keys[cur.x + i]);
+    cp_async_commit();
   }
+  while (u < nunits) {
+    const uint32_t nx = u + gridDim.x;
+    const uint2 next = nx < nunits ? list[nx] : make_uint2(0, 0);
+    cp_async_wait_all();
+    __syncthreads();
+    uint64_t k[kBsIpt];
+#pragma unroll
+    for (int j = 0; j < kBsIpt; ++j) {
+      const uint32_t i = uint32_t(j * kBsThreads + tid);
+      k[j] = i < cur.y ? s_pre[i] : 0;
+    }
+    __syncthreads();  // the prefetch buffer is free again
+    if (nx < nunits) {
+      for (uint32_t i = tid; i < next.y; i += kBsThreads) cp_async8(&s_pre[i], &keys[next.x + i]);
+      cp_async_commit();
+    }
+    sort_unit(k, keys + cur.x, cur.y, s_out, sh);
+    u = nx;
+    cur = next;
+  }
+  cp_async_wait_all();
 }
 
 __global__ void learn_bucket_ids_kernel(const uint64_t* __restrict__ keys, uint64_t n, LearnedMap mp,
@@ -1180,18 +1216,21 @@ template <int kLevel>
 cudaError_t launch_staged(const uint64_t* src, uint64_t n, const LearnedGeom& g, const LearnedMap& mp,
                           const uint32_t* off1, const uint32_t* offsets, uint64_t* dst, unsigned grid,
                           cudaStream_t stream) {
-  static bool attr = false;
-  if (!attr) {
+  const uint32_t cap = g.nsuper > uint32_t(kFine) ? g.nsuper : uint32_t(kFine);
+  const StLayout L(cap);
+  static int attr_bytes = 0;
+  if (int(L.bytes) > attr_bytes) {
+    const StLayout most(kMaxSuper);
     cudaError_t e = cudaFuncSetAttribute(learn_staged_scatter_kernel<kLevel>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(StLayout::kBytes));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(most.bytes));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(learn_staged_scatter_kernel<kLevel>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                100);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr_bytes = int(most.bytes);
   }
-  learn_staged_scatter_kernel<kLevel><<<grid, kStThreads, StLayout::kBytes, stream>>>(src, n, g.chunk, g.nch, g.nsuper,
-                                                                                     mp, off1, offsets, dst);
+  learn_staged_scatter_kernel<kLevel><<<grid, kStThreads, L.bytes, stream>>>(src, n, g.chunk, g.nch, g.nsuper, cap,
+                                                                            mp, off1, offsets, dst);
   return cudaGetLastError();
 }
 
@@ -1226,12 +1265,18 @@ cudaError_t launch_learn_fill(const LearnedMap& mp, const LearnedState* st, cons
 }
 
 cudaError_t launch_learn_bucket_sort(uint64_t* keys, const uint32_t* counts, const uint32_t* offsets,
-                                     const uint32_t* bitmap, uint32_t nb, const uint2* cells, uint32_t* status,
-                                     int sms, cudaStream_t stream) {
-  constexpr int kBytes = kLearnBucketCap * 8;
+                                     const uint32_t* bitmap, uint32_t nb, uint2* units, uint32_t* status, int sms,
+                                     cudaStream_t stream) {
+  const uint32_t ngroups = (nb + kGroup - 1) / kGroup;
+  cudaError_t e = cudaMemsetAsync(units, 0, sizeof(uint2), stream);
+  if (e != cudaSuccess) return e;
+  learn_units_kernel<<<grid_for(ngroups, 256), 256, 0, stream>>>(counts, offsets, bitmap, nb, units, status);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  constexpr int kBytes = 2 * kLearnBucketCap * 8;
   static int per_sm = 0;
   if (!per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(learn_bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
+    e = cudaFuncSetAttribute(learn_bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(learn_bucket_sort_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess)
@@ -1240,9 +1285,8 @@ cudaError_t launch_learn_bucket_sort(uint64_t* keys, const uint32_t* counts, con
     if (per_sm < 1) per_sm = 1;
   }
   const uint64_t want = uint64_t(sms) * per_sm;
-  const uint32_t ngroups = (nb + kGroup - 1) / kGroup;
   const unsigned grid = unsigned(ngroups < want ? ngroups : want);
-  learn_bucket_sort_kernel<<<grid, kBsThreads, kBytes, stream>>>(keys, counts, offsets, bitmap, nb, cells, status);
+  learn_bucket_sort_kernel<<<grid, kBsThreads, kBytes, stream>>>(keys, units);
   return cudaGetLastError();
 }
 
