@@ -268,6 +268,80 @@ FSORT_API fsort_status fsort_mlp_forward(const void* w_bf16, const float* x, uin
 FSORT_API fsort_status fsort_mlp_grad(const void* w_bf16, const float* x, const float* y, uint32_t m, float* grads,
                                       float* loss, void* stream);
 
+/* ---- serving: a request loop with continuous batching --------------------
+ * A server runs `lanes` workers, each with its own CUDA stream and plan.
+ * Requests (host buffers) wait in a FIFO queue; a free worker takes the head
+ * request as soon as its device buffers fit into the server's memory arena
+ * (admission by free HBM), copies it in, sorts it, copies the result out and
+ * frees the buffers -- requests that arrive while others run are admitted as
+ * lanes and memory free up, and the lanes' work overlaps on the device.  A
+ * worker that finds several small requests (at most batch_keys keys each) at
+ * the head of the queue sorts them together in one fsort_sort_batch call.
+ * Every result equals what fsort_sort_pairs returns for that request alone.
+ * All entry points are thread-safe. */
+typedef struct fsort_server fsort_server;
+
+typedef struct fsort_serve_desc {
+  uint64_t max_request_keys; /* largest n of any request (>= 1) */
+  uint64_t hbm_budget_bytes; /* device bytes for admitted requests' buffers; 0 = a quarter of free memory */
+  int32_t key_bits;          /* 16, 32 or 64 */
+  int32_t has_values;        /* requests may carry uint32_t values */
+  uint32_t lanes;            /* workers (stream + plan + thread each); 0 = 4 */
+  uint32_t max_queue;        /* waiting requests before submit answers FSORT_ERR_BUSY; 0 = 65536 */
+  uint32_t batch_keys;       /* requests of at most this many keys may share a batch; 0 = 1,048,576 */
+  uint32_t max_batch;        /* requests per batch (1..1024); 0 = 64 */
+  uint32_t flags;            /* FSORT_FLAG_LEARNED: 64-bit keys, lanes take the learned path once a
+                                model is installed with fsort_serve_set_model */
+  uint32_t reserved;
+} fsort_serve_desc;
+
+typedef struct fsort_request {
+  const void* keys_host;     /* n keys (host memory; pinned memory makes the copies asynchronous) */
+  const uint32_t* vals_host; /* n values or NULL */
+  void* keys_out_host;       /* receives the sorted keys (may equal keys_host) */
+  uint32_t* vals_out_host;   /* receives the values (NULL iff vals_host is NULL) */
+  uint64_t n;
+  int32_t precision_bits;
+  uint32_t reserved;
+} fsort_request;
+
+typedef struct fsort_result {
+  int32_t status;    /* fsort_status of the request */
+  int32_t batched;   /* 1 if it was sorted inside a batch of several requests */
+  uint64_t n;
+  double latency_ms; /* submit -> result ready */
+  double queue_ms;   /* submit -> admitted */
+  double run_ms;     /* admitted -> result ready (copies in, sort, copies out) */
+} fsort_result;
+
+typedef struct fsort_serve_stats {
+  uint64_t submitted, completed, keys_completed, batches;
+  uint64_t bytes_in_use, peak_bytes, budget_bytes;
+  uint32_t max_inflight; /* most requests admitted at once */
+  uint32_t reserved;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* latency over completed requests */
+  double span_s;                          /* first submit -> last completion */
+  double keys_per_s;                      /* keys_completed / span_s */
+} fsort_serve_stats;
+
+FSORT_API fsort_status fsort_serve_create(const fsort_serve_desc* desc, fsort_server** out);
+/* Finishes every admitted and queued request, then frees the server. */
+FSORT_API fsort_status fsort_serve_destroy(fsort_server* server);
+/* Queue a request; *ticket identifies it.  The buffers must stay valid until
+ * the request is reported done.  FSORT_ERR_BUSY: the queue is full;
+ * FSORT_ERR_INVALID_ARG: n > max_request_keys, bad pointers or precision, or
+ * buffers larger than the whole budget. */
+FSORT_API fsort_status fsort_serve_submit(fsort_server* server, const fsort_request* req, uint64_t* ticket);
+/* FSORT_NOT_READY while the request runs; FSORT_OK once done (out filled, the
+ * ticket retired); FSORT_ERR_INVALID_ARG for an unknown ticket. */
+FSORT_API fsort_status fsort_serve_poll(fsort_server* server, uint64_t ticket, fsort_result* out);
+/* Like poll, but waits up to timeout_ms (negative: no limit). */
+FSORT_API fsort_status fsort_serve_wait(fsort_server* server, uint64_t ticket, double timeout_ms, fsort_result* out);
+FSORT_API fsort_status fsort_serve_stats_get(fsort_server* server, fsort_serve_stats* out);
+/* Install the fitted model of `source` (a plan with FSORT_FLAG_LEARNED) on
+ * every lane; call while no request runs. */
+FSORT_API fsort_status fsort_serve_set_model(fsort_server* server, fsort_plan* source);
+
 /* ---- the hot-path steps one at a time (same kernels as the full sort) ---- */
 
 /* Step 2: per-pass digit histograms of keys[0..n).  counts_out (device, uint64_t)

@@ -76,6 +76,38 @@ class FsortLearnedStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class FsortServeDesc(ctypes.Structure):
+    _fields_ = [("max_request_keys", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("key_bits", ctypes.c_int32), ("has_values", ctypes.c_int32), ("lanes", ctypes.c_uint32),
+                ("max_queue", ctypes.c_uint32), ("batch_keys", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class FsortRequest(ctypes.Structure):
+    _fields_ = [("keys_host", ctypes.c_void_p), ("vals_host", ctypes.c_void_p), ("keys_out_host", ctypes.c_void_p),
+                ("vals_out_host", ctypes.c_void_p), ("n", ctypes.c_uint64), ("precision_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class FsortResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batched", ctypes.c_int32), ("n", ctypes.c_uint64),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class FsortServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("keys_completed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("span_s", ctypes.c_double), ("keys_per_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 KERNEL_KINDS = {1: "histogram", 2: "scan", 3: "scatter", 4: "copy", 5: "leaf_hist", 6: "leaf_reduce",
                 7: "leaf_scan", 8: "expand", 9: "learn_count1", 10: "learn_scatter1", 11: "learn_count2",
                 12: "learn_judge", 13: "learn_scatter2", 14: "learn_fill", 15: "learn_buckets"}
@@ -124,6 +156,13 @@ def load_library():
             "fsort_learned_set_model": ([vp, vp, vp, vp, ctypes.c_uint32, vp, vp], st),
             "fsort_mlp_forward": ([vp, vp, ctypes.c_uint32, vp, vp], st),
             "fsort_mlp_grad": ([vp, vp, vp, ctypes.c_uint32, vp, vp, vp], st),
+            "fsort_serve_create": ([ctypes.POINTER(FsortServeDesc), ctypes.POINTER(vp)], st),
+            "fsort_serve_destroy": ([vp], st),
+            "fsort_serve_submit": ([vp, ctypes.POINTER(FsortRequest), ctypes.POINTER(ctypes.c_uint64)], st),
+            "fsort_serve_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(FsortResult)], st),
+            "fsort_serve_wait": ([vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(FsortResult)], st),
+            "fsort_serve_stats_get": ([vp, ctypes.POINTER(FsortServeStats)], st),
+            "fsort_serve_set_model": ([vp, vp], st),
             "fsort_status_string": ([i32], ctypes.c_char_p),
             "fsort_version": ([], i32),
         }
@@ -401,6 +440,97 @@ def fsort_mlp_forward(w_bf16, x, out, m=None, stream=None) -> None:
 def fsort_mlp_grad(w_bf16, x, y, grads, loss=None, m=None, stream=None) -> None:
     _check(load_library().fsort_mlp_grad(_ptr(w_bf16), _ptr(x), _ptr(y), _numel(x, m), _ptr(grads), _ptr(loss),
                                          _stream(stream)), "fsort_mlp_grad")
+
+
+def fsort_serve_create(max_request_keys: int, key_bits: int, has_values: bool = True, hbm_budget_bytes: int = 0,
+                       lanes: int = 0, max_queue: int = 0, batch_keys: int = 0, max_batch: int = 0, flags: int = 0):
+    d = FsortServeDesc(max_request_keys, hbm_budget_bytes, key_bits, int(bool(has_values)), lanes, max_queue,
+                       batch_keys, max_batch, flags, 0)
+    h = ctypes.c_void_p()
+    _check(load_library().fsort_serve_create(ctypes.byref(d), ctypes.byref(h)), "fsort_serve_create")
+    return h.value
+
+
+def fsort_serve_destroy(server) -> None:
+    _check(load_library().fsort_serve_destroy(server), "fsort_serve_destroy")
+
+
+def fsort_serve_submit(server, keys_host, vals_host=None, keys_out_host=None, vals_out_host=None, n=None,
+                       precision_bits=None, key_bits=None) -> int:
+    """Queue a sort of host arrays (numpy or pinned torch tensors); the
+    result lands in keys_out_host/vals_out_host (default: in place)."""
+    kb = _key_bits_of(keys_host, key_bits)
+    r = FsortRequest(_ptr(keys_host), _ptr(vals_host), _ptr(keys_host if keys_out_host is None else keys_out_host),
+                     _ptr(vals_host if vals_out_host is None else vals_out_host), _numel(keys_host, n),
+                     kb if precision_bits is None else precision_bits, 0)
+    t = ctypes.c_uint64()
+    _check(load_library().fsort_serve_submit(server, ctypes.byref(r), ctypes.byref(t)), "fsort_serve_submit")
+    return t.value
+
+
+def fsort_serve_poll(server, ticket: int):
+    """The result dict once the request is done, else None."""
+    out = FsortResult()
+    st = load_library().fsort_serve_poll(server, ticket, ctypes.byref(out))
+    if st == 6:
+        return None
+    _check(st, "fsort_serve_poll")
+    return out.as_dict()
+
+
+def fsort_serve_wait(server, ticket: int, timeout_ms: float = -1.0):
+    out = FsortResult()
+    st = load_library().fsort_serve_wait(server, ticket, timeout_ms, ctypes.byref(out))
+    if st == 6:
+        return None
+    _check(st, "fsort_serve_wait")
+    return out.as_dict()
+
+
+def fsort_serve_stats_get(server) -> dict:
+    out = FsortServeStats()
+    _check(load_library().fsort_serve_stats_get(server, ctypes.byref(out)), "fsort_serve_stats_get")
+    return out.as_dict()
+
+
+def fsort_serve_set_model(server, plan) -> None:
+    _check(load_library().fsort_serve_set_model(server, plan), "fsort_serve_set_model")
+
+
+class Server:
+    """Owns an fsort_server handle (see the serving section of fsort.h)."""
+
+    def __init__(self, max_request_keys: int, key_bits: int, has_values: bool = True, **kw):
+        self.handle = fsort_serve_create(max_request_keys, key_bits, has_values, **kw)
+
+    def close(self) -> None:
+        if self.handle:
+            fsort_serve_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, keys_host, vals_host=None, **kw) -> int:
+        return fsort_serve_submit(self.handle, keys_host, vals_host, **kw)
+
+    def poll(self, ticket: int):
+        return fsort_serve_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0):
+        return fsort_serve_wait(self.handle, ticket, timeout_ms)
+
+    def stats(self) -> dict:
+        return fsort_serve_stats_get(self.handle)
 
 
 def fsort_status_string(status: int) -> str:
