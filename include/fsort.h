@@ -342,6 +342,40 @@ FSORT_API fsort_status fsort_serve_stats_get(fsort_server* server, fsort_serve_s
  * every lane; call while no request runs. */
 FSORT_API fsort_status fsort_serve_set_model(fsort_server* server, fsort_plan* source);
 
+/* ---- streaming histogram with rank / select --------------------------------
+ * Counts of the sort keys s(k) = k >> (key_bits - precision_bits) accumulated
+ * over any number of batches; each batch is read once and never again (the
+ * batch counter update of Sec. III-C/D: the histogram of the batches so far
+ * is kept and extended).  Queries (device arrays, stream-ordered):
+ *   rank(v)   = #{accumulated keys with s(k) < v}            (Alg. 3, GetIndex)
+ *   select(r) = s(k) of the key at sorted position r         (Alg. 2, GetItem)
+ *               (UINT64_MAX when r >= the number accumulated)
+ *   expand    = the sorted multiset of every s(k) seen, as key_bits-wide keys
+ *               (for precision_bits == key_bits: the sorted keys themselves;
+ *                Alg. 5 with no trailing bits)
+ * precision_bits <= 24 (2^p 64-bit counters).  One object serves one stream at
+ * a time.  The paper defines these on its histogram tree; the GPU keeps the
+ * leaf level plus a prefix index rebuilt after each accumulation. */
+typedef struct fsort_hist fsort_hist;
+FSORT_API fsort_status fsort_hist_create(int key_bits, int precision_bits, fsort_hist** out);
+FSORT_API fsort_status fsort_hist_destroy(fsort_hist* hist);
+FSORT_API fsort_status fsort_hist_reset(fsort_hist* hist, void* stream);
+/* Add the counts of keys[0..n) (device). */
+FSORT_API fsort_status fsort_hist_accumulate(fsort_hist* hist, const void* keys, uint64_t n, void* stream);
+/* Keys accumulated so far (host-side count; no synchronisation). */
+FSORT_API fsort_status fsort_hist_total(const fsort_hist* hist, uint64_t* total);
+/* counts_out[v] (device, 2^precision_bits uint64_t) = accumulated keys with s(k) = v. */
+FSORT_API fsort_status fsort_hist_counts(fsort_hist* hist, uint64_t* counts_out, void* stream);
+/* ranks[i] = rank(values[i]) (values >= 2^p give the total). */
+FSORT_API fsort_status fsort_hist_rank(fsort_hist* hist, const uint64_t* values, uint64_t count, uint64_t* ranks,
+                                       void* stream);
+/* values[i] = select(ranks[i]). */
+FSORT_API fsort_status fsort_hist_select(fsort_hist* hist, const uint64_t* ranks, uint64_t count, uint64_t* values,
+                                         void* stream);
+/* keys_out[0..n) (device, key_bits wide) = the sorted multiset of s(k); n must
+ * equal the total accumulated. */
+FSORT_API fsort_status fsort_hist_expand(fsort_hist* hist, void* keys_out, uint64_t n, void* stream);
+
 /* ---- the hot-path steps one at a time (same kernels as the full sort) ---- */
 
 /* Step 2: per-pass digit histograms of keys[0..n).  counts_out (device, uint64_t)

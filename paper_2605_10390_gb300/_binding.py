@@ -163,6 +163,15 @@ def load_library():
             "fsort_serve_wait": ([vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(FsortResult)], st),
             "fsort_serve_stats_get": ([vp, ctypes.POINTER(FsortServeStats)], st),
             "fsort_serve_set_model": ([vp, vp], st),
+            "fsort_hist_create": ([i32, i32, ctypes.POINTER(vp)], st),
+            "fsort_hist_destroy": ([vp], st),
+            "fsort_hist_reset": ([vp, vp], st),
+            "fsort_hist_accumulate": ([vp, vp, u64, vp], st),
+            "fsort_hist_total": ([vp, ctypes.POINTER(ctypes.c_uint64)], st),
+            "fsort_hist_counts": ([vp, vp, vp], st),
+            "fsort_hist_rank": ([vp, vp, u64, vp, vp], st),
+            "fsort_hist_select": ([vp, vp, u64, vp, vp], st),
+            "fsort_hist_expand": ([vp, vp, u64, vp], st),
             "fsort_status_string": ([i32], ctypes.c_char_p),
             "fsort_version": ([], i32),
         }
@@ -495,6 +504,81 @@ def fsort_serve_stats_get(server) -> dict:
 
 def fsort_serve_set_model(server, plan) -> None:
     _check(load_library().fsort_serve_set_model(server, plan), "fsort_serve_set_model")
+
+
+def fsort_hist_create(key_bits: int, precision_bits: int):
+    h = ctypes.c_void_p()
+    _check(load_library().fsort_hist_create(key_bits, precision_bits, ctypes.byref(h)), "fsort_hist_create")
+    return h.value
+
+
+def fsort_hist_destroy(hist) -> None:
+    _check(load_library().fsort_hist_destroy(hist), "fsort_hist_destroy")
+
+
+def fsort_hist_reset(hist, stream=None) -> None:
+    _check(load_library().fsort_hist_reset(hist, _stream(stream)), "fsort_hist_reset")
+
+
+def fsort_hist_accumulate(hist, keys, n=None, stream=None) -> None:
+    _check(load_library().fsort_hist_accumulate(hist, _ptr(keys), _numel(keys, n), _stream(stream)),
+           "fsort_hist_accumulate")
+
+
+def fsort_hist_total(hist) -> int:
+    t = ctypes.c_uint64()
+    _check(load_library().fsort_hist_total(hist, ctypes.byref(t)), "fsort_hist_total")
+    return t.value
+
+
+def fsort_hist_counts(hist, counts_out, stream=None) -> None:
+    _check(load_library().fsort_hist_counts(hist, _ptr(counts_out), _stream(stream)), "fsort_hist_counts")
+
+
+def fsort_hist_rank(hist, values, ranks, count=None, stream=None) -> None:
+    _check(load_library().fsort_hist_rank(hist, _ptr(values), _numel(values, count), _ptr(ranks), _stream(stream)),
+           "fsort_hist_rank")
+
+
+def fsort_hist_select(hist, ranks, values, count=None, stream=None) -> None:
+    _check(load_library().fsort_hist_select(hist, _ptr(ranks), _numel(ranks, count), _ptr(values), _stream(stream)),
+           "fsort_hist_select")
+
+
+def fsort_hist_expand(hist, keys_out, n=None, stream=None) -> None:
+    _check(load_library().fsort_hist_expand(hist, _ptr(keys_out), _numel(keys_out, n), _stream(stream)),
+           "fsort_hist_expand")
+
+
+class StreamHistogram:
+    """Owns an fsort_hist handle (see the streaming-histogram section of fsort.h)."""
+
+    def __init__(self, key_bits: int, precision_bits: int):
+        self.key_bits, self.precision_bits = key_bits, precision_bits
+        self.handle = fsort_hist_create(key_bits, precision_bits)
+
+    def close(self) -> None:
+        if self.handle:
+            fsort_hist_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def accumulate(self, keys, stream=None) -> None:
+        fsort_hist_accumulate(self.handle, keys, stream=stream)
+
+    def total(self) -> int:
+        return fsort_hist_total(self.handle)
 
 
 class Server:
