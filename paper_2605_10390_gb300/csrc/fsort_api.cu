@@ -57,6 +57,8 @@ struct LearnedWs {
   uint32_t *counts = nullptr, *offsets = nullptr;  // every bucket id (+ 1)
   uint32_t *hcount = nullptr, *bitmap = nullptr;
   uint2* units = nullptr;                          // bucket-sort unit list
+  uint32_t* ids = nullptr;                         // [max_n] bucket id of every input key
+  uint16_t* fine = nullptr;                        // [max_n] fine digit of every key in alt
   void* w_bf16 = nullptr;
   float *master = nullptr, *m1 = nullptr, *m2 = nullptr, *grads = nullptr, *loss_log = nullptr;
   fsort::LearnedState* st = nullptr;
@@ -342,12 +344,12 @@ fsort_status enqueue_learned(fsort_plan* p, const void* keys_in, void* keys_out,
   if (e == cudaSuccess) e = cudaMemsetAsync(L.bitmap, 0, size_t(g.nids / 32 + 1) * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(L.counts1 + l1n, 0, 4, s);
   if (e == cudaSuccess) e = launch_learn_heavy_ids(mp, L.st, L.hid, L.bitmap, s);
-  if (e == cudaSuccess) e = launch_learn_l1(kin, n, g, mp, L.st, L.counts1, L.hcount, s);
+  if (e == cudaSuccess) e = launch_learn_l1(kin, n, g, mp, L.st, L.counts1, L.hcount, L.ids, s);
   tm.mark(FSORT_KERNEL_LEARN_COUNT1, -1);
   if (e == cudaSuccess) e = launch_scan_u32(L.counts1, l1n + 1, L.off1, nullptr, L.sums, s);
-  if (e == cudaSuccess) e = launch_learn_l1_scatter(kin, n, g, mp, L.off1, alt, s);
+  if (e == cudaSuccess) e = launch_learn_l1_scatter(kin, L.ids, n, g, L.off1, alt, L.fine, s);
   tm.mark(FSORT_KERNEL_LEARN_SCATTER1, -1);
-  if (e == cudaSuccess) e = launch_learn_l2_count(alt, g, mp, L.off1, L.counts, s);
+  if (e == cudaSuccess) e = launch_learn_l2_count(L.fine, g, L.off1, L.counts, s);
   tm.mark(FSORT_KERNEL_LEARN_COUNT2, -1);
   if (e == cudaSuccess) e = launch_learn_judge(L.counts, g, L.bitmap, L.hid, L.hcount, L.st, L.large, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(L.h_st, L.st, sizeof(LearnedState), cudaMemcpyDeviceToHost, s);
@@ -365,7 +367,7 @@ fsort_status enqueue_learned(fsort_plan* p, const void* keys_in, void* keys_out,
   L.last_imbalance = double(mx) * double(B) / double(n);
   if (!accept) return enqueue_sort(p, keys_in, nullptr, keys_out, nullptr, n, 64, 64, s);
   e = launch_scan_u32(L.counts, g.nids, L.offsets, nullptr, L.sums, s);
-  if (e == cudaSuccess) e = launch_learn_l2_scatter(alt, g, mp, L.off1, L.offsets, kout, s);
+  if (e == cudaSuccess) e = launch_learn_l2_scatter(alt, L.fine, g, L.off1, L.offsets, kout, s);
   tm.mark(FSORT_KERNEL_LEARN_SCATTER2, -1);
   if (e == cudaSuccess) e = launch_learn_fill(mp, L.st, L.hid, L.large, L.offsets, L.counts, kout, p->sms, s);
   tm.mark(FSORT_KERNEL_LEARN_FILL, -1);
@@ -727,7 +729,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   }
   const bool learned = (desc->flags & FSORT_FLAG_LEARNED) != 0;
   LearnedWs lw;
-  size_t o_l[26] = {};
+  size_t o_l[28] = {};
   if (learned) {
     lw.sample_max = uint32_t(n < LearnedWs::kMaxSample ? n : LearnedWs::kMaxSample);
     const LearnedGeom gm = learned_geometry(n, learned_buckets(n));
@@ -755,6 +757,8 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     o_l[23] = take(l1 * 4);
     o_l[24] = take(l1 * 4);
     o_l[25] = take(((nb + 3) / 4 * 4 + 1) * 8);
+    o_l[26] = take(size_t(n) * 4);
+    o_l[27] = take(size_t(n) * 2);
     o_l[16] = take(size_t(kMlpParams) * 2);
     o_l[17] = take(size_t(kMlpParams) * 4);
     o_l[18] = take(size_t(kMlpParams) * 4);
@@ -826,6 +830,8 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     L.counts1 = reinterpret_cast<uint32_t*>(w + o_l[23]);
     L.off1 = reinterpret_cast<uint32_t*>(w + o_l[24]);
     L.units = reinterpret_cast<uint2*>(w + o_l[25]);
+    L.ids = reinterpret_cast<uint32_t*>(w + o_l[26]);
+    L.fine = reinterpret_cast<uint16_t*>(w + o_l[27]);
     L.w_bf16 = w + o_l[16];
     L.master = reinterpret_cast<float*>(w + o_l[17]);
     L.m1 = reinterpret_cast<float*>(w + o_l[18]);

@@ -201,17 +201,20 @@ struct LearnedGeom {
 LearnedGeom learned_geometry(uint64_t n, uint32_t buckets);
 cudaError_t launch_learn_heavy_ids(const LearnedMap& mp, LearnedState* st, uint32_t* hid, uint32_t* bitmap,
                                    cudaStream_t stream);
-// counts1[nsuper * nch] (super-bucket major), hcount[kLearnMaxHeavy] accumulated.
+// counts1[nsuper * nch] (super-bucket major), hcount[kLearnMaxHeavy] accumulated,
+// ids[n] every key's bucket id (all ones for heavy keys).
 cudaError_t launch_learn_l1(const uint64_t* keys, uint64_t n, const LearnedGeom& g, const LearnedMap& mp,
-                            const LearnedState* st, uint32_t* counts1, uint32_t* hcount, cudaStream_t stream);
-// off1: exclusive scan of counts1 with one extra entry (the total).
-cudaError_t launch_learn_l1_scatter(const uint64_t* keys, uint64_t n, const LearnedGeom& g, const LearnedMap& mp,
-                                    const uint32_t* off1, uint64_t* alt, cudaStream_t stream);
-cudaError_t launch_learn_l2_count(const uint64_t* alt, const LearnedGeom& g, const LearnedMap& mp,
-                                  const uint32_t* off1, uint32_t* counts, cudaStream_t stream);
+                            const LearnedState* st, uint32_t* counts1, uint32_t* hcount, uint32_t* ids,
+                            cudaStream_t stream);
+// off1: exclusive scan of counts1 with one extra entry (the total); fine[] receives
+// each scattered key's 10-bit fine digit at the key's position in alt.
+cudaError_t launch_learn_l1_scatter(const uint64_t* keys, const uint32_t* ids, uint64_t n, const LearnedGeom& g,
+                                    const uint32_t* off1, uint64_t* alt, uint16_t* fine, cudaStream_t stream);
+cudaError_t launch_learn_l2_count(const uint16_t* fine, const LearnedGeom& g, const uint32_t* off1, uint32_t* counts,
+                                  cudaStream_t stream);
 cudaError_t launch_learn_judge(uint32_t* counts, const LearnedGeom& g, const uint32_t* bitmap, const uint32_t* hid,
                                const uint32_t* hcount, LearnedState* st, uint32_t* large_list, cudaStream_t stream);
-cudaError_t launch_learn_l2_scatter(const uint64_t* alt, const LearnedGeom& g, const LearnedMap& mp,
+cudaError_t launch_learn_l2_scatter(const uint64_t* alt, const uint16_t* fine, const LearnedGeom& g,
                                     const uint32_t* off1, const uint32_t* off2, uint64_t* dst, cudaStream_t stream);
 cudaError_t launch_learn_fill(const LearnedMap& mp, const LearnedState* st, const uint32_t* hid,
                               const uint32_t* large_list, const uint32_t* offsets, const uint32_t* counts,

@@ -19,13 +19,15 @@
 // Sort (64-bit keys, keys only, all 64 bits; the result is the sorted
 // multiset, exactly what the plain path produces):
 //   learn_l1_count_kernel     per input chunk: non-heavy keys per super-bucket
-//                             (id >> 10), copies of every heavy key
-//   learn_l1_scatter_kernel   non-heavy keys grouped by super-bucket (scratch)
+//                             (id >> 10), copies of every heavy key; every
+//                             key's id stored (the only map lookup it gets)
+//   learn_staged_scatter<1>   non-heavy keys grouped by super-bucket (scratch),
+//                             each with its 10-bit fine digit
 //   learn_l2_count_kernel     per super-bucket: keys per bucket -- with the
 //                             heavy counts, the exact count of every bucket id
 //   learn_judge_kernel        largest non-heavy bucket; accept iff <= tau n / B
 //                             (else the plain path sorts the untouched input)
-//   learn_l2_scatter_kernel   per super-bucket: keys to their final buckets
+//   learn_staged_scatter<2>   per super-bucket: keys to their final buckets
 //   learn_fill_kernel         every heavy bucket filled with its key
 //   learn_bucket_sort_kernel  every non-heavy bucket sorted on chip (a counting
 //                             pass into sub-buckets, then insertion sorts)
@@ -469,7 +471,7 @@ __global__ void learn_heavy_ids_kernel(LearnedMap mp, LearnedState* st, uint32_t
   atomicOr(&bitmap[id >> 5], 1u << (id & 31u));
 }
 
-// Walk keys[lo, hi) with kKeysPerLane keys per lane in flight; f(key, valid).
+// Walk keys[lo, hi) with kKeysPerLane keys per lane in flight; f(key, index, valid).
 template <int kThreads, typename F>
 __device__ __forceinline__ void for_keys(const uint64_t* __restrict__ keys, uint64_t lo, uint64_t hi, F f) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -482,18 +484,21 @@ __device__ __forceinline__ void for_keys(const uint64_t* __restrict__ keys, uint
       k[j] = i < hi ? keys[i] : 0;
     }
 #pragma unroll
-    for (int j = 0; j < kKeysPerLane; ++j) f(k[j], base + j * 32 + lane < hi);
+    for (int j = 0; j < kKeysPerLane; ++j) f(k[j], base + j * 32 + lane, base + j * 32 + lane < hi);
   }
 }
 
 // Level 1 count: counts1[s * nch + c] = non-heavy keys of chunk c in super-bucket s;
-// hcount[t] += copies of heavy key t.
+// hcount[t] += copies of heavy key t; ids[i] = the key's bucket id (kHeavyId
+// for heavy keys) -- the only map lookup a key gets.
+constexpr uint32_t kHeavyId = 0xFFFFFFFFu;
 __global__ void __launch_bounds__(kPartThreads) learn_l1_count_kernel(const uint64_t* __restrict__ keys, uint64_t n,
                                                                       uint64_t chunk, uint32_t nch, uint32_t nsuper,
                                                                       LearnedMap mp,
                                                                       const LearnedState* __restrict__ st,
                                                                       uint32_t* __restrict__ counts1,
-                                                                      uint32_t* __restrict__ hcount) {
+                                                                      uint32_t* __restrict__ hcount,
+                                                                      uint32_t* __restrict__ ids) {
   extern __shared__ uint32_t l1_smem[];
   uint32_t* s_cnt = l1_smem;                 // [kMaxSuper]
   uint32_t* s_heavy = l1_smem + kMaxSuper;   // [kLearnMaxHeavy]
@@ -502,11 +507,14 @@ __global__ void __launch_bounds__(kPartThreads) learn_l1_count_kernel(const uint
   __syncthreads();
   const uint32_t c = blockIdx.x;
   const uint64_t lo = uint64_t(c) * chunk, hi = lo + chunk < n ? lo + chunk : n;
-  for_keys<kPartThreads>(keys, lo, hi, [&](uint64_t k, bool valid) {
+  for_keys<kPartThreads>(keys, lo, hi, [&](uint64_t k, uint64_t i, bool valid) {
     bool hit = false;
     uint32_t t = 0;
     const uint32_t id = map_id(k, mp, hit, t);
-    if (valid) atomicAdd(hit ? &s_heavy[t] : &s_cnt[id >> kFineBits], 1u);
+    if (valid) {
+      atomicAdd(hit ? &s_heavy[t] : &s_cnt[id >> kFineBits], 1u);
+      ids[i] = hit ? kHeavyId : id;
+    }
   });
   __syncthreads();
   for (uint32_t s = threadIdx.x; s < nsuper; s += kPartThreads) counts1[uint64_t(s) * nch + c] = s_cnt[s];
@@ -518,21 +526,16 @@ __global__ void __launch_bounds__(kPartThreads) learn_l1_count_kernel(const uint
 constexpr int kL2Threads = 1024;
 
 // Level 2 count: counts[s * 1024 + d] for super-bucket s = blockIdx.x, whose
-// keys are alt[off1[s * nch], off1[(s + 1) * nch]).
-__global__ void __launch_bounds__(kL2Threads) learn_l2_count_kernel(const uint64_t* __restrict__ alt,
+// keys are alt[off1[s * nch], off1[(s + 1) * nch]) with fine digits fine[].
+__global__ void __launch_bounds__(kL2Threads) learn_l2_count_kernel(const uint16_t* __restrict__ fine,
                                                                     const uint32_t* __restrict__ off1, uint32_t nch,
-                                                                    LearnedMap mp, uint32_t* __restrict__ counts) {
+                                                                    uint32_t* __restrict__ counts) {
   __shared__ uint32_t s_cnt[kFine];
   for (int i = threadIdx.x; i < kFine; i += kL2Threads) s_cnt[i] = 0;
   __syncthreads();
   const uint32_t s = blockIdx.x;
   const uint64_t lo = off1[uint64_t(s) * nch], hi = off1[uint64_t(s + 1) * nch];
-  for_keys<kL2Threads>(alt, lo, hi, [&](uint64_t k, bool valid) {
-    bool hit;
-    uint32_t t;
-    const uint32_t id = map_id(k, mp, hit, t);
-    if (valid) atomicAdd(&s_cnt[id & (kFine - 1)], 1u);
-  });
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += kL2Threads) atomicAdd(&s_cnt[fine[i]], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < kFine; d += kL2Threads) counts[uint64_t(s) * kFine + d] = s_cnt[d];
 }
@@ -555,17 +558,19 @@ __global__ void learn_judge_kernel(uint32_t* __restrict__ counts, uint32_t nb, c
   }
 }
 
-// Staged scatter of one source range per CTA, tile by tile (4096 keys): each
+// Staged scatter of one source range per CTA, tile by tile (8192 keys): each
 // tile is counted per digit in shared memory (slot = the old count), staged
 // grouped by digit, and written out in runs at the digit's global cursor, so
 // consecutive threads write consecutive addresses.  Order inside a digit's run
 // follows the shared-memory atomics (arbitrary; the bucket sorts fix it).  The
-// next tile is prefetched into shared memory (cp.async) while one is processed.
-//   level 1: CTA = input chunk c, digit = id >> 10, heavy keys skipped,
-//            cursors from off1[s * nch + c], output alt
-//   level 2: CTA = super-bucket s, keys alt[off1[s nch], off1[(s+1) nch]),
-//            digit = id & 1023, cursors from offsets[s * 1024 + d], output dst
-constexpr int kStThreads = 512;
+// next tile's keys are prefetched into shared memory (cp.async).
+// No map lookup: the ids come from the level-1 count.
+//   level 1: CTA = input chunk c; digit = id >> 10 (heavy keys skipped);
+//            cursors from off1[s * nch + c]; keys to alt, fine digit id & 1023
+//            to fine_out at the same position
+//   level 2: CTA = super-bucket s, keys alt[off1[s nch], off1[(s+1) nch]) with
+//            their fine digits; cursors from offsets[s * 1024 + d]; keys to dst
+constexpr int kStThreads = 1024;
 constexpr int kStIpt = 8;
 constexpr int kStTile = kStThreads * kStIpt;
 constexpr uint32_t kNoDigit = 0xFFFFu;
@@ -573,16 +578,17 @@ constexpr int kStPer = (kMaxSuper + kStThreads - 1) / kStThreads;  // digits a t
 
 // Shared-memory layout for a given digit capacity (bytes from the start).
 struct StLayout {
-  size_t stage, pre, dig, cnt, cur, delta, warp, bytes;
-  __host__ __device__ explicit StLayout(uint32_t cap) {
+  size_t stage, pre, dig, fine, cnt, cur, delta, warp, bytes;
+  __host__ __device__ StLayout(int level, uint32_t cap) {
     stage = 0;
     pre = stage + size_t(kStTile) * 8;
     dig = pre + size_t(kStTile) * 8;
-    cnt = dig + size_t(kStTile) * 2;
+    fine = dig + size_t(kStTile) * 2;
+    cnt = fine + (level == 1 ? size_t(kStTile) * 2 : 0);
     cur = cnt + size_t(cap) * 4;
     delta = cur + size_t(cap) * 4;
     warp = delta + size_t(cap) * 4;
-    bytes = warp + 32 * 4;
+    bytes = warp + 33 * 4;
   }
 };
 
@@ -594,15 +600,16 @@ __device__ __forceinline__ void prefetch_tile(uint64_t* s_pre, const uint64_t* _
 }
 
 template <int kLevel>
-__global__ void __launch_bounds__(kStThreads, 2) learn_staged_scatter_kernel(
-    const uint64_t* __restrict__ src, uint64_t n, uint64_t chunk, uint32_t nch, uint32_t nsuper, uint32_t cap,
-    LearnedMap mp, const uint32_t* __restrict__ off1, const uint32_t* __restrict__ offsets,
-    uint64_t* __restrict__ dst) {
+__global__ void __launch_bounds__(kStThreads, 1) learn_staged_scatter_kernel(
+    const uint64_t* __restrict__ src, const uint32_t* __restrict__ ids, const uint16_t* __restrict__ fine_in,
+    uint64_t n, uint64_t chunk, uint32_t nch, uint32_t nsuper, uint32_t cap, const uint32_t* __restrict__ off1,
+    const uint32_t* __restrict__ offsets, uint64_t* __restrict__ dst, uint16_t* __restrict__ fine_out) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const StLayout L(cap);
+  const StLayout L(kLevel, cap);
   uint64_t* s_stage = reinterpret_cast<uint64_t*>(smem + L.stage);
   uint64_t* s_pre = reinterpret_cast<uint64_t*>(smem + L.pre);
   uint16_t* s_dig = reinterpret_cast<uint16_t*>(smem + L.dig);
+  uint16_t* s_fine = reinterpret_cast<uint16_t*>(smem + L.fine);
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + L.cnt);
   uint32_t* s_cur = reinterpret_cast<uint32_t*>(smem + L.cur);
   uint32_t* s_delta = reinterpret_cast<uint32_t*>(smem + L.delta);
@@ -626,27 +633,40 @@ __global__ void __launch_bounds__(kStThreads, 2) learn_staged_scatter_kernel(
   for (uint32_t d = tid; d < ndig; d += kStThreads) s_cnt[d] = 0;
   for (uint64_t base = lo; base < hi; base += kStTile) {
     const uint32_t tn = uint32_t(hi - base < uint64_t(kStTile) ? hi - base : uint64_t(kStTile));
+    uint32_t tag[kStIpt];  // the keys' ids (level 1) or fine digits (level 2), loaded while the prefetch lands
+#pragma unroll
+    for (int j = 0; j < kStIpt; ++j) {
+      const uint32_t i = uint32_t(j * kStThreads + tid);
+      tag[j] = i < tn ? (kLevel == 1 ? ids[base + i] : uint32_t(fine_in[base + i])) : 0u;
+    }
     cp_async_wait_all();
     __syncthreads();
     uint64_t k[kStIpt];
     uint32_t ds[kStIpt];  // digit << 16 | slot inside the tile's digit run
+    uint32_t fn[kStIpt];  // level 1: the fine digit travelling with the key
 #pragma unroll
     for (int j = 0; j < kStIpt; ++j) {
       const uint32_t i = uint32_t(j * kStThreads + tid);
       k[j] = i < tn ? s_pre[i] : 0;
+      uint32_t d = kNoDigit;
+      fn[j] = 0;
+      if (i < tn) {
+        if (kLevel == 1) {
+          if (tag[j] != kHeavyId) {
+            d = tag[j] >> kFineBits;
+            fn[j] = tag[j] & (kFine - 1);
+          }
+        } else {
+          d = tag[j];
+        }
+      }
+      ds[j] = d << 16;
     }
-    __syncthreads();  // the prefetch buffer is free again
+    __syncthreads();  // the prefetch buffers are free again
     if (base + kStTile < hi) prefetch_tile(s_pre, src, base + kStTile, hi);
 #pragma unroll
-    for (int j = 0; j < kStIpt; ++j) {
-      const uint32_t i = uint32_t(j * kStThreads + tid);
-      bool hit;
-      uint32_t t;
-      const uint32_t id = map_id(k[j], mp, hit, t);
-      const uint32_t d = kLevel == 1 ? (id >> kFineBits) : (id & (kFine - 1));
-      ds[j] = kNoDigit << 16;
-      if (i < tn && !(kLevel == 1 && hit)) ds[j] = (d << 16) | atomicAdd(&s_cnt[d], 1u);
-    }
+    for (int j = 0; j < kStIpt; ++j)
+      if ((ds[j] >> 16) != kNoDigit) ds[j] |= atomicAdd(&s_cnt[ds[j] >> 16], 1u);
     __syncthreads();
     // exclusive scan of the tile's digit counts (thread t owns digits t*kStPer ...)
     uint32_t own[kStPer], sum = 0;
@@ -664,13 +684,21 @@ __global__ void __launch_bounds__(kStThreads, 2) learn_staged_scatter_kernel(
     }
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
-    uint32_t run = inc - sum, total = 0;
+    if (warp == 0) {  // exclusive prefix of the warp totals; the total after them
+      static_assert(kStThreads == 1024, "one warp total per lane");
+      const uint32_t x = s_warp[lane];
+      uint32_t y = x;
 #pragma unroll
-    for (int w = 0; w < kStThreads / 32; ++w) {
-      const uint32_t x = s_warp[w];
-      if (w < warp) run += x;
-      total += x;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += z;
+      }
+      s_warp[lane] = y - x;
+      if (lane == 31) s_warp[32] = y;
     }
+    __syncthreads();
+    uint32_t run = inc - sum + s_warp[warp];
+    const uint32_t total = s_warp[32];
 #pragma unroll
     for (int q = 0; q < kStPer; ++q) {
       const uint32_t d = uint32_t(tid * kStPer + q);
@@ -690,10 +718,15 @@ __global__ void __launch_bounds__(kStThreads, 2) learn_staged_scatter_kernel(
         const uint32_t p = s_cnt[d] + (ds[j] & 0xFFFFu);
         s_stage[p] = k[j];
         s_dig[p] = uint16_t(d);
+        if (kLevel == 1) s_fine[p] = uint16_t(fn[j]);
       }
     }
     __syncthreads();
-    for (uint32_t i = tid; i < total; i += kStThreads) dst[s_delta[s_dig[i]] + i] = s_stage[i];
+    for (uint32_t i = tid; i < total; i += kStThreads) {
+      const uint32_t pos = s_delta[s_dig[i]] + i;
+      dst[pos] = s_stage[i];
+      if (kLevel == 1) fine_out[pos] = s_fine[i];
+    }
     for (uint32_t d = tid; d < ndig; d += kStThreads) s_cnt[d] = 0;
   }
   cp_async_wait_all();
@@ -1199,7 +1232,8 @@ LearnedGeom learned_geometry(uint64_t n, uint32_t buckets) {
 }
 
 cudaError_t launch_learn_l1(const uint64_t* keys, uint64_t n, const LearnedGeom& g, const LearnedMap& mp,
-                            const LearnedState* st, uint32_t* counts1, uint32_t* hcount, cudaStream_t stream) {
+                            const LearnedState* st, uint32_t* counts1, uint32_t* hcount, uint32_t* ids,
+                            cudaStream_t stream) {
   constexpr int kBytes = (kMaxSuper + kLearnMaxHeavy) * 4;
   static bool attr = false;
   if (!attr) {
@@ -1208,40 +1242,41 @@ cudaError_t launch_learn_l1(const uint64_t* keys, uint64_t n, const LearnedGeom&
     attr = true;
   }
   learn_l1_count_kernel<<<g.nch, kPartThreads, kBytes, stream>>>(keys, n, g.chunk, g.nch, g.nsuper, mp, st, counts1,
-                                                                 hcount);
+                                                                 hcount, ids);
   return cudaGetLastError();
 }
 
 template <int kLevel>
-cudaError_t launch_staged(const uint64_t* src, uint64_t n, const LearnedGeom& g, const LearnedMap& mp,
-                          const uint32_t* off1, const uint32_t* offsets, uint64_t* dst, unsigned grid,
-                          cudaStream_t stream) {
+cudaError_t launch_staged(const uint64_t* src, const uint32_t* ids, const uint16_t* fine_in, uint64_t n,
+                          const LearnedGeom& g, const uint32_t* off1, const uint32_t* offsets, uint64_t* dst,
+                          uint16_t* fine_out, unsigned grid, cudaStream_t stream) {
   const uint32_t cap = g.nsuper > uint32_t(kFine) ? g.nsuper : uint32_t(kFine);
-  const StLayout L(cap);
-  static int attr_bytes = 0;
-  if (int(L.bytes) > attr_bytes) {
-    const StLayout most(kMaxSuper);
+  const StLayout L(kLevel, cap);
+  static bool attr = false;
+  if (!attr) {
+    const StLayout most(kLevel, kMaxSuper);
     cudaError_t e = cudaFuncSetAttribute(learn_staged_scatter_kernel<kLevel>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(most.bytes));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(learn_staged_scatter_kernel<kLevel>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                100);
     if (e != cudaSuccess) return e;
-    attr_bytes = int(most.bytes);
+    attr = true;
   }
-  learn_staged_scatter_kernel<kLevel><<<grid, kStThreads, L.bytes, stream>>>(src, n, g.chunk, g.nch, g.nsuper, cap,
-                                                                            mp, off1, offsets, dst);
+  learn_staged_scatter_kernel<kLevel><<<grid, kStThreads, L.bytes, stream>>>(src, ids, fine_in, n, g.chunk, g.nch,
+                                                                            g.nsuper, cap, off1, offsets, dst,
+                                                                            fine_out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_learn_l1_scatter(const uint64_t* keys, uint64_t n, const LearnedGeom& g, const LearnedMap& mp,
-                                    const uint32_t* off1, uint64_t* alt, cudaStream_t stream) {
-  return launch_staged<1>(keys, n, g, mp, off1, nullptr, alt, g.nch, stream);
+cudaError_t launch_learn_l1_scatter(const uint64_t* keys, const uint32_t* ids, uint64_t n, const LearnedGeom& g,
+                                    const uint32_t* off1, uint64_t* alt, uint16_t* fine, cudaStream_t stream) {
+  return launch_staged<1>(keys, ids, nullptr, n, g, off1, nullptr, alt, fine, g.nch, stream);
 }
 
-cudaError_t launch_learn_l2_count(const uint64_t* alt, const LearnedGeom& g, const LearnedMap& mp,
-                                  const uint32_t* off1, uint32_t* counts, cudaStream_t stream) {
-  learn_l2_count_kernel<<<g.nsuper, kL2Threads, 0, stream>>>(alt, off1, g.nch, mp, counts);
+cudaError_t launch_learn_l2_count(const uint16_t* fine, const LearnedGeom& g, const uint32_t* off1, uint32_t* counts,
+                                  cudaStream_t stream) {
+  learn_l2_count_kernel<<<g.nsuper, kL2Threads, 0, stream>>>(fine, off1, g.nch, counts);
   return cudaGetLastError();
 }
 
@@ -1252,9 +1287,9 @@ cudaError_t launch_learn_judge(uint32_t* counts, const LearnedGeom& g, const uin
   return cudaGetLastError();
 }
 
-cudaError_t launch_learn_l2_scatter(const uint64_t* alt, const LearnedGeom& g, const LearnedMap& mp,
+cudaError_t launch_learn_l2_scatter(const uint64_t* alt, const uint16_t* fine, const LearnedGeom& g,
                                     const uint32_t* off1, const uint32_t* off2, uint64_t* dst, cudaStream_t stream) {
-  return launch_staged<2>(alt, 0, g, mp, off1, off2, dst, g.nsuper, stream);
+  return launch_staged<2>(alt, nullptr, fine, 0, g, off1, off2, dst, nullptr, g.nsuper, stream);
 }
 
 cudaError_t launch_learn_fill(const LearnedMap& mp, const LearnedState* st, const uint32_t* hid,
