@@ -732,9 +732,12 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   size_t o_l[28] = {};
   if (learned) {
     lw.sample_max = uint32_t(n < LearnedWs::kMaxSample ? n : LearnedWs::kMaxSample);
-    const LearnedGeom gm = learned_geometry(n, learned_buckets(n));
-    lw.nids_max = gm.nids;
-    lw.l1_max = uint64_t(gm.nsuper) * kLearnL1Chunks + 1;
+    // the largest id table and level-1 count table over every B a sort on this plan may use
+    for (uint32_t b = 256; b <= learned_buckets(n); b <<= 1) {
+      const LearnedGeom gm = learned_geometry(n, b);
+      if (gm.nids > lw.nids_max) lw.nids_max = gm.nids;
+      if (uint64_t(gm.nsuper) * kLearnL1Chunks + 1 > lw.l1_max) lw.l1_max = uint64_t(gm.nsuper) * kLearnL1Chunks + 1;
+    }
     const size_t sm = lw.sample_max, nb = lw.nids_max + 1, l1 = lw.l1_max;
     const size_t big = sm > nb ? (sm > l1 ? sm : l1) : (nb > l1 ? nb : l1);
     const size_t scan_words = big / 4096 + 2;

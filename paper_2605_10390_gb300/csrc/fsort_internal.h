@@ -193,8 +193,9 @@ cudaError_t launch_scan_u32(const uint32_t* in, uint64_t count, uint32_t* out, u
 constexpr uint32_t kLearnL1Chunks = 4096;  // most level-1 chunks (input ranges owned by one CTA)
 struct LearnedGeom {
   uint32_t nb;      // bucket ids in use: B + 2 * kLearnMaxHeavy
-  uint32_t nsuper;  // super-buckets (id >> 10)
-  uint32_t nids;    // nsuper * 1024 (ids beyond nb are empty)
+  uint32_t fbits;   // fine digit width (10..12)
+  uint32_t nsuper;  // super-buckets (id >> fbits)
+  uint32_t nids;    // nsuper << fbits (ids beyond nb are empty)
   uint32_t nch;     // level-1 chunks
   uint64_t chunk;   // keys per level-1 chunk
 };
@@ -207,7 +208,7 @@ cudaError_t launch_learn_l1(const uint64_t* keys, uint64_t n, const LearnedGeom&
                             const LearnedState* st, uint32_t* counts1, uint32_t* hcount, uint32_t* ids,
                             cudaStream_t stream);
 // off1: exclusive scan of counts1 with one extra entry (the total); fine[] receives
-// each scattered key's 10-bit fine digit at the key's position in alt.
+// each scattered key's fine digit (id & (2^fbits - 1)) at the key's position in alt.
 cudaError_t launch_learn_l1_scatter(const uint64_t* keys, const uint32_t* ids, uint64_t n, const LearnedGeom& g,
                                     const uint32_t* off1, uint64_t* alt, uint16_t* fine, cudaStream_t stream);
 cudaError_t launch_learn_l2_count(const uint16_t* fine, const LearnedGeom& g, const uint32_t* off1, uint32_t* counts,

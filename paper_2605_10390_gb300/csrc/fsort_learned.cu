@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(kCellThreads) learn_cells_finish_kernel(const 
 }
 
 // --------------------------------------------------------------- sorting ----
-// Bucket id = (super-bucket s = id >> 10, fine digit d = id & 1023).  Level 1
+// Bucket id = (super-bucket s = id >> f, fine digit d = id & (2^f - 1)), f in 10..12.  Level 1
 // groups the non-heavy keys by s into the scratch array: each CTA owns a fixed
 // chunk of the input, counts its chunk per s, and after one flattened scan of
 // the [s][chunk] counts (super-bucket major, so the scan is the position)
@@ -450,9 +450,9 @@ __global__ void __launch_bounds__(kCellThreads) learn_cells_finish_kernel(const 
 // super-bucket: count its keys per d, then (after the judge and a scan over
 // all ids) scatter them to their final buckets, again through shared-memory
 // cursors.  No per-key global atomic; every write front fits in L2.
-constexpr int kFineBits = 10;
-constexpr int kFine = 1 << kFineBits;
-constexpr int kMaxSuper = ((1 << 22) + 2 * kLearnMaxHeavy + kFine - 1) / kFine;  // 4112
+constexpr int kFineBitsMin = 10, kFineBitsMax = 12;  // the fine digit's width is chosen per sort
+constexpr int kFineMax = 1 << kFineBitsMax;
+constexpr int kMaxSuper = ((1 << 22) + 2 * kLearnMaxHeavy + (1 << kFineBitsMin) - 1) >> kFineBitsMin;  // 4112
 constexpr int kPartThreads = 512;
 constexpr int kKeysPerLane = 8;  // keys a lane has in flight: independent table lookups hide latency
 
@@ -494,7 +494,7 @@ __device__ __forceinline__ void for_keys(const uint64_t* __restrict__ keys, uint
 constexpr uint32_t kHeavyId = 0xFFFFFFFFu;
 __global__ void __launch_bounds__(kPartThreads) learn_l1_count_kernel(const uint64_t* __restrict__ keys, uint64_t n,
                                                                       uint64_t chunk, uint32_t nch, uint32_t nsuper,
-                                                                      LearnedMap mp,
+                                                                      uint32_t fbits, LearnedMap mp,
                                                                       const LearnedState* __restrict__ st,
                                                                       uint32_t* __restrict__ counts1,
                                                                       uint32_t* __restrict__ hcount,
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(kPartThreads) learn_l1_count_kernel(const uint
     uint32_t t = 0;
     const uint32_t id = map_id(k, mp, hit, t);
     if (valid) {
-      atomicAdd(hit ? &s_heavy[t] : &s_cnt[id >> kFineBits], 1u);
+      atomicAdd(hit ? &s_heavy[t] : &s_cnt[id >> fbits], 1u);
       ids[i] = hit ? kHeavyId : id;
     }
   });
@@ -529,15 +529,16 @@ constexpr int kL2Threads = 1024;
 // keys are alt[off1[s * nch], off1[(s + 1) * nch]) with fine digits fine[].
 __global__ void __launch_bounds__(kL2Threads) learn_l2_count_kernel(const uint16_t* __restrict__ fine,
                                                                     const uint32_t* __restrict__ off1, uint32_t nch,
-                                                                    uint32_t* __restrict__ counts) {
-  __shared__ uint32_t s_cnt[kFine];
-  for (int i = threadIdx.x; i < kFine; i += kL2Threads) s_cnt[i] = 0;
+                                                                    uint32_t fbits, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t s_cnt[kFineMax];
+  const int nfine = 1 << fbits;
+  for (int i = threadIdx.x; i < nfine; i += kL2Threads) s_cnt[i] = 0;
   __syncthreads();
   const uint32_t s = blockIdx.x;
   const uint64_t lo = off1[uint64_t(s) * nch], hi = off1[uint64_t(s + 1) * nch];
   for (uint64_t i = lo + threadIdx.x; i < hi; i += kL2Threads) atomicAdd(&s_cnt[fine[i]], 1u);
   __syncthreads();
-  for (int d = threadIdx.x; d < kFine; d += kL2Threads) counts[uint64_t(s) * kFine + d] = s_cnt[d];
+  for (int d = threadIdx.x; d < nfine; d += kL2Threads) counts[(uint64_t(s) << fbits) + d] = s_cnt[d];
 }
 
 // counts[hid[t]] = hcount[t] (heavy ids hold no other key), then the judge:
@@ -575,6 +576,7 @@ constexpr int kStIpt = 8;
 constexpr int kStTile = kStThreads * kStIpt;
 constexpr uint32_t kNoDigit = 0xFFFFu;
 constexpr int kStPer = (kMaxSuper + kStThreads - 1) / kStThreads;  // digits a thread owns in the scan
+static_assert(kStPer * kStThreads >= kFineMax, "the scan covers the widest fine digit");
 
 // Shared-memory layout for a given digit capacity (bytes from the start).
 struct StLayout {
@@ -602,7 +604,8 @@ __device__ __forceinline__ void prefetch_tile(uint64_t* s_pre, const uint64_t* _
 template <int kLevel>
 __global__ void __launch_bounds__(kStThreads, 1) learn_staged_scatter_kernel(
     const uint64_t* __restrict__ src, const uint32_t* __restrict__ ids, const uint16_t* __restrict__ fine_in,
-    uint64_t n, uint64_t chunk, uint32_t nch, uint32_t nsuper, uint32_t cap, const uint32_t* __restrict__ off1,
+    uint64_t n, uint64_t chunk, uint32_t nch, uint32_t nsuper, uint32_t fbits, uint32_t cap,
+    const uint32_t* __restrict__ off1,
     const uint32_t* __restrict__ offsets, uint64_t* __restrict__ dst, uint16_t* __restrict__ fine_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const StLayout L(kLevel, cap);
@@ -615,7 +618,7 @@ __global__ void __launch_bounds__(kStThreads, 1) learn_staged_scatter_kernel(
   uint32_t* s_delta = reinterpret_cast<uint32_t*>(smem + L.delta);
   uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L.warp);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t ndig = kLevel == 1 ? nsuper : uint32_t(kFine);
+  const uint32_t ndig = kLevel == 1 ? nsuper : (1u << fbits);
   uint64_t lo, hi;
   if (kLevel == 1) {
     lo = uint64_t(blockIdx.x) * chunk;
@@ -628,7 +631,7 @@ __global__ void __launch_bounds__(kStThreads, 1) learn_staged_scatter_kernel(
   if (kLevel == 1) {
     for (uint32_t d = tid; d < ndig; d += kStThreads) s_cur[d] = off1[uint64_t(d) * nch + blockIdx.x];
   } else {
-    for (uint32_t d = tid; d < ndig; d += kStThreads) s_cur[d] = offsets[uint64_t(blockIdx.x) * kFine + d];
+    for (uint32_t d = tid; d < ndig; d += kStThreads) s_cur[d] = offsets[(uint64_t(blockIdx.x) << fbits) + d];
   }
   for (uint32_t d = tid; d < ndig; d += kStThreads) s_cnt[d] = 0;
   for (uint64_t base = lo; base < hi; base += kStTile) {
@@ -653,8 +656,8 @@ __global__ void __launch_bounds__(kStThreads, 1) learn_staged_scatter_kernel(
       if (i < tn) {
         if (kLevel == 1) {
           if (tag[j] != kHeavyId) {
-            d = tag[j] >> kFineBits;
-            fn[j] = tag[j] & (kFine - 1);
+            d = tag[j] >> fbits;
+            fn[j] = tag[j] & ((1u << fbits) - 1u);
           }
         } else {
           d = tag[j];
@@ -1222,8 +1225,13 @@ cudaError_t launch_learn_heavy_ids(const LearnedMap& mp, LearnedState* st, uint3
 LearnedGeom learned_geometry(uint64_t n, uint32_t buckets) {
   LearnedGeom g{};
   g.nb = buckets + 2u * kLearnMaxHeavy;
-  g.nsuper = (g.nb + kFine - 1) / kFine;
-  g.nids = g.nsuper * kFine;
+  // 10 fine bits: on 2^30 mixture keys 11 and 12 bits shorten level 1's
+  // write runs but lengthen level 2's by more (both scatters: 21.1 ms at 10
+  // bits, 21.7 at 11, 22.7 at 12)
+  g.fbits = kFineBitsMin;
+  if (g.fbits > kFineBitsMax) g.fbits = kFineBitsMax;
+  g.nsuper = (g.nb + (1u << g.fbits) - 1) >> g.fbits;
+  g.nids = g.nsuper << g.fbits;
   const uint64_t want = (n + kLearnL1Chunks - 1) / kLearnL1Chunks;
   g.chunk = want < 65536 ? 65536 : (want + 4095) / 4096 * 4096;
   g.nch = uint32_t((n + g.chunk - 1) / g.chunk);
@@ -1241,8 +1249,8 @@ cudaError_t launch_learn_l1(const uint64_t* keys, uint64_t n, const LearnedGeom&
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  learn_l1_count_kernel<<<g.nch, kPartThreads, kBytes, stream>>>(keys, n, g.chunk, g.nch, g.nsuper, mp, st, counts1,
-                                                                 hcount, ids);
+  learn_l1_count_kernel<<<g.nch, kPartThreads, kBytes, stream>>>(keys, n, g.chunk, g.nch, g.nsuper, g.fbits, mp, st,
+                                                                 counts1, hcount, ids);
   return cudaGetLastError();
 }
 
@@ -1250,7 +1258,7 @@ template <int kLevel>
 cudaError_t launch_staged(const uint64_t* src, const uint32_t* ids, const uint16_t* fine_in, uint64_t n,
                           const LearnedGeom& g, const uint32_t* off1, const uint32_t* offsets, uint64_t* dst,
                           uint16_t* fine_out, unsigned grid, cudaStream_t stream) {
-  const uint32_t cap = g.nsuper > uint32_t(kFine) ? g.nsuper : uint32_t(kFine);
+  const uint32_t cap = g.nsuper > (1u << g.fbits) ? g.nsuper : (1u << g.fbits);
   const StLayout L(kLevel, cap);
   static bool attr = false;
   if (!attr) {
@@ -1264,8 +1272,8 @@ cudaError_t launch_staged(const uint64_t* src, const uint32_t* ids, const uint16
     attr = true;
   }
   learn_staged_scatter_kernel<kLevel><<<grid, kStThreads, L.bytes, stream>>>(src, ids, fine_in, n, g.chunk, g.nch,
-                                                                            g.nsuper, cap, off1, offsets, dst,
-                                                                            fine_out);
+                                                                            g.nsuper, g.fbits, cap, off1, offsets,
+                                                                            dst, fine_out);
   return cudaGetLastError();
 }
 
@@ -1276,7 +1284,7 @@ cudaError_t launch_learn_l1_scatter(const uint64_t* keys, const uint32_t* ids, u
 
 cudaError_t launch_learn_l2_count(const uint16_t* fine, const LearnedGeom& g, const uint32_t* off1, uint32_t* counts,
                                   cudaStream_t stream) {
-  learn_l2_count_kernel<<<g.nsuper, kL2Threads, 0, stream>>>(fine, off1, g.nch, counts);
+  learn_l2_count_kernel<<<g.nsuper, kL2Threads, 0, stream>>>(fine, off1, g.nch, g.fbits, counts);
   return cudaGetLastError();
 }
 
