@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 32 GB arbitrary-precision configurations")
+    ap.add_argument("--only", choices=["secondary", "batched", "learned", "serving"],
+                    help="run one secondary section alone and print its JSON (profiling and debugging)")
+    ap.add_argument("--learned-log2n", type=int, default=30, help="keys of the learned section (log2)")
     return ap.parse_args()
 
 
@@ -489,6 +492,19 @@ def main():
     import paper_2605_10390_gb300 as fs
 
     torch.cuda.set_device(local_rank)
+    if args.only:
+        stream = torch.cuda.current_stream()
+        peak = measured_peaks()[0]
+        if args.only == "secondary":
+            out = run_secondary(fs, workloads, torch, stream, peak)
+        elif args.only == "batched":
+            out = run_batched(fs, workloads, torch, stream, peak)
+        elif args.only == "learned":
+            out = run_learned(fs, workloads, torch, stream, peak, log2n=args.learned_log2n)
+        else:
+            out = run_serving(fs, workloads, torch, stream)
+        print(json.dumps({"section": args.only, "result": out}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

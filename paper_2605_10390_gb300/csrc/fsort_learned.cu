@@ -450,9 +450,10 @@ __global__ void __launch_bounds__(kCellThreads) learn_cells_finish_kernel(const 
 // super-bucket: count its keys per d, then (after the judge and a scan over
 // all ids) scatter them to their final buckets, again through shared-memory
 // cursors.  No per-key global atomic; every write front fits in L2.
-constexpr int kFineBitsMin = 10, kFineBitsMax = 12;  // the fine digit's width is chosen per sort
+constexpr int kFineBitsMin = 6, kFineBitsMax = 12;  // the fine digit's width is chosen per sort
 constexpr int kFineMax = 1 << kFineBitsMax;
-constexpr int kMaxSuper = ((1 << 22) + 2 * kLearnMaxHeavy + (1 << kFineBitsMin) - 1) >> kFineBitsMin;  // 4112
+// most super-buckets: B = 2^22 at 10 fine bits, or up to 2^15 ids at 6 (both well below)
+constexpr int kMaxSuper = ((1 << 22) + 2 * kLearnMaxHeavy + (1 << 10) - 1) >> 10;  // 4112
 constexpr int kPartThreads = 512;
 constexpr int kKeysPerLane = 8;  // keys a lane has in flight: independent table lookups hide latency
 
@@ -1225,10 +1226,14 @@ cudaError_t launch_learn_heavy_ids(const LearnedMap& mp, LearnedState* st, uint3
 LearnedGeom learned_geometry(uint64_t n, uint32_t buckets) {
   LearnedGeom g{};
   g.nb = buckets + 2u * kLearnMaxHeavy;
-  // 10 fine bits: on 2^30 mixture keys 11 and 12 bits shorten level 1's
-  // write runs but lengthen level 2's by more (both scatters: 21.1 ms at 10
-  // bits, 21.7 at 11, 22.7 at 12)
-  g.fbits = kFineBitsMin;
+  // At most 10 fine bits: on 2^30 mixture keys 11 and 12 bits shorten level
+  // 1's write runs but lengthen level 2's by more (both scatters: 21.1 ms at
+  // 10 bits, 21.7 at 11, 22.7 at 12).  Fewer for small sorts, so that level 2
+  // (one CTA per super-bucket) has 256..1024 CTAs.
+  uint32_t lb = 0;
+  while ((1u << lb) < g.nb) ++lb;
+  g.fbits = lb > 9 + kFineBitsMax ? kFineBitsMax : (lb > 9 + kFineBitsMin ? lb - 9 : kFineBitsMin);
+  if (g.fbits > 10) g.fbits = 10;
   if (g.fbits > kFineBitsMax) g.fbits = kFineBitsMax;
   g.nsuper = (g.nb + (1u << g.fbits) - 1) >> g.fbits;
   g.nids = g.nsuper << g.fbits;
