@@ -13,7 +13,7 @@ constexpr uint32_t kDevTimeoutLookback = 1u;  // a look-back wait gave up
 constexpr uint32_t kDevTimeoutLoad = 2u;      // a bulk-copy wait gave up
 constexpr uint32_t kDevBadTile = 4u;          // a dynamic tile id beyond the grid (counter not reset)
 constexpr uint32_t kDevBadLookback = 8u;      // a look-back walk reached its chunk's first tile without a prefix
-constexpr uint32_t kDevBadOutput = 16u;       // a scatter target fell outside the output (only after a timeout)
+constexpr uint32_t kDevBadOutput = 16u;       // a tile skipped its output after a failed bounded wait
 constexpr uint32_t kDevBadBucket = 32u;       // a learned-path bucket exceeded the on-chip capacity (judge bypassed)
 
 // Bounded waits give up after this many nanoseconds of %globaltimer.

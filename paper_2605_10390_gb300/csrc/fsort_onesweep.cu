@@ -67,7 +67,7 @@ struct SmemLayout {
   static constexpr size_t kOff = kCnt + kRadix * 4;  // 8-byte aligned: all above are multiples of 1 KB
   static constexpr size_t kScan = kOff + kRadix * 8;
   static constexpr size_t kBar = kScan + 16 * 4;
-  static constexpr size_t kTileId = kBar + 8;
+  static constexpr size_t kTileId = kBar + 8;  // tile id, then a failed-wait flag
   static constexpr size_t kBytes = kTileId + 16;
 };
 
@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
 
   if (tid == 0) {
     *s_tile = atomicAdd(a.tile_counter, 1u);
+    s_tile[1] = 0;  // set when a bounded wait of this tile gave up
     mbar_init(s_bar, 1);
     fence_mbar_init();
   }
@@ -273,6 +274,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
         t -= used;
         if (t == chunk_first) {  // a chunk's first tile always publishes a prefix
           atomicOr(a.status, kDevBadLookback);
+          s_tile[1] = 1;
           break;
         }
         if (used < w) {  // blocked on an unpublished predecessor
@@ -280,6 +282,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
             t_wait = global_timer_ns();
           } else if (global_timer_ns() - t_wait > kWaitLimitNs) {
             atomicOr(a.status, kDevTimeoutLookback);
+            s_tile[1] = 1;
             break;
           }
           __nanosleep(64);
@@ -300,6 +303,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
         while (!ld_acquire_gpu(flag)) {
           if (global_timer_ns() - t_wait > kWaitLimitNs) {
             atomicOr(a.status, kDevTimeoutLookback);
+            s_tile[1] = 1;
             break;
           }
           __nanosleep(128);
@@ -316,8 +320,13 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   __syncthreads();
   if (last_in_chunk && tid == 0) st_release_gpu(a.chunk_flag + chunk + 1, 1u);
 
-  // 6. write the staged tile out in digit runs
-  bool out_of_range = false;
+  // 6. write the staged tile out in digit runs.  Without a failed wait every
+  // offset is exact (each digit's run lies inside the output); after one the
+  // tile writes nothing, so a partial prefix can never address past it.
+  if (s_tile[1]) {
+    if (tid == 0) atomicOr(a.status, kDevBadOutput);
+    return;
+  }
 #pragma unroll 4
   for (uint32_t s = tid; s < tile_n; s += kBlock) {
     K k;
@@ -331,14 +340,9 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
       from = s_src16[s];
     }
     const uint64_t o = s_off[dig(k, shift, mask)] + s;
-    if (o >= n_bound) {  // only reachable after a timed-out wait; never write outside the output
-      out_of_range = true;
-      continue;
-    }
     kout[o] = k;
     if (kVals) vout[o] = s_vals[from];
   }
-  if (out_of_range) atomicOr(a.status, kDevBadOutput);
 }
 
 template <typename K, bool kVals>
