@@ -71,6 +71,91 @@ struct SmemLayout {
   static constexpr size_t kBytes = kTileId + 16;
 };
 
+// Look-back for digit d of `tile` (kWindow predecessors per round trip,
+// bounded wait), publication of the tile's inclusive prefix, and the digit's
+// 64-bit output offset s_off[d] = chunk base + exclusive prefix - tile
+// position.  The last tile of a chunk hands the next chunk its bases.
+// Returns false when a wait gave up (the device status records why).
+__device__ __forceinline__ bool digit_offset(const OnesweepArgs& a, uint32_t tile, uint32_t chunk,
+                                             uint32_t chunk_first, bool first_in_chunk, bool last_in_chunk,
+                                             const unsigned long long* base_row, uint32_t d, uint32_t cnt,
+                                             uint32_t tile_excl, uint32_t* lb, unsigned long long* s_off) {
+  bool ok = true;
+  uint32_t excl = 0;
+  if (!first_in_chunk) {
+    uint32_t t = tile;  // tiles [chunk_first, t) are still to the left
+    uint64_t t_wait = 0;
+    while (true) {
+      const uint32_t left = t - chunk_first;
+      const uint32_t w = left < uint32_t(kWindow) ? left : uint32_t(kWindow);
+      uint32_t v[kWindow];
+#pragma unroll
+      for (int i = 0; i < kWindow; ++i)
+        v[i] = (uint32_t(i) < w) ? ld_relaxed_gpu(a.lookback + uint64_t(t - 1 - i) * kRadix + d) : 0u;
+      bool stop = false, found = false;
+      uint32_t used = 0;
+#pragma unroll
+      for (int i = 0; i < kWindow; ++i) {
+        if (!stop && uint32_t(i) < w) {
+          const uint32_t f = v[i] & ~kCountMask;
+          if (f == 0) {
+            stop = true;  // not published yet: read again from here
+          } else {
+            excl += v[i] & kCountMask;
+            ++used;
+            if (f == kFlagPrefix) stop = found = true;
+          }
+        }
+      }
+      if (found) break;
+      t -= used;
+      if (t == chunk_first) {  // a chunk's first tile always publishes a prefix
+        atomicOr(a.status, kDevBadLookback);
+        ok = false;
+        break;
+      }
+      if (used < w) {  // blocked on an unpublished predecessor
+        if (t_wait == 0) {
+          t_wait = global_timer_ns();
+        } else if (global_timer_ns() - t_wait > kWaitLimitNs) {
+          atomicOr(a.status, kDevTimeoutLookback);
+          ok = false;
+          break;
+        }
+        __nanosleep(64);
+      } else {
+        t_wait = 0;
+      }
+    }
+    st_relaxed_gpu(lb + d, kFlagPrefix | (excl + cnt));
+  }
+  // 64-bit base of this digit in this chunk.
+  unsigned long long base;
+  if (base_row) {
+    base = base_row[d];
+  } else {
+    const uint32_t* flag = a.chunk_flag + chunk;
+    if (!ld_acquire_gpu(flag)) {
+      const uint64_t t_wait = global_timer_ns();
+      while (!ld_acquire_gpu(flag)) {
+        if (global_timer_ns() - t_wait > kWaitLimitNs) {
+          atomicOr(a.status, kDevTimeoutLookback);
+          ok = false;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    base = a.chunk_base[uint64_t(chunk) * kRadix + d];
+  }
+  s_off[d] = base + excl - tile_excl;
+  if (last_in_chunk) {  // hand the next chunk its 64-bit bases
+    a.chunk_base[uint64_t(chunk + 1) * kRadix + d] = base + excl + cnt;
+    __threadfence();
+  }
+  return ok;
+}
+
 template <typename K, bool kVals>
 __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks)
     onesweep_kernel(const OnesweepArgs a) {
@@ -241,82 +326,10 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   }
 
   // 5. decoupled look-back for digit d = tid, kWindow predecessors per round trip
-  if (tid < kRadix) {
-    const int d = tid;
-    const uint32_t cnt = s_cnt[d];
-    uint32_t excl = 0;
-    if (!first_in_chunk) {
-      uint32_t t = tile;  // tiles [chunk_first, t) are still to the left
-      uint64_t t_wait = 0;
-      while (true) {
-        const uint32_t left = t - chunk_first;
-        const uint32_t w = left < uint32_t(kWindow) ? left : uint32_t(kWindow);
-        uint32_t v[kWindow];
-#pragma unroll
-        for (int i = 0; i < kWindow; ++i)
-          v[i] = (uint32_t(i) < w) ? ld_relaxed_gpu(a.lookback + uint64_t(t - 1 - i) * kRadix + d) : 0u;
-        bool stop = false, found = false;
-        uint32_t used = 0;
-#pragma unroll
-        for (int i = 0; i < kWindow; ++i) {
-          if (!stop && uint32_t(i) < w) {
-            const uint32_t f = v[i] & ~kCountMask;
-            if (f == 0) {
-              stop = true;  // not published yet: read again from here
-            } else {
-              excl += v[i] & kCountMask;
-              ++used;
-              if (f == kFlagPrefix) stop = found = true;
-            }
-          }
-        }
-        if (found) break;
-        t -= used;
-        if (t == chunk_first) {  // a chunk's first tile always publishes a prefix
-          atomicOr(a.status, kDevBadLookback);
-          s_tile[1] = 1;
-          break;
-        }
-        if (used < w) {  // blocked on an unpublished predecessor
-          if (t_wait == 0) {
-            t_wait = global_timer_ns();
-          } else if (global_timer_ns() - t_wait > kWaitLimitNs) {
-            atomicOr(a.status, kDevTimeoutLookback);
-            s_tile[1] = 1;
-            break;
-          }
-          __nanosleep(64);
-        } else {
-          t_wait = 0;
-        }
-      }
-      st_relaxed_gpu(lb + d, kFlagPrefix | (excl + cnt));
-    }
-    // 64-bit base of this digit in this chunk.
-    unsigned long long base;
-    if (base_row) {
-      base = base_row[d];
-    } else {
-      const uint32_t* flag = a.chunk_flag + chunk;
-      if (!ld_acquire_gpu(flag)) {
-        const uint64_t t_wait = global_timer_ns();
-        while (!ld_acquire_gpu(flag)) {
-          if (global_timer_ns() - t_wait > kWaitLimitNs) {
-            atomicOr(a.status, kDevTimeoutLookback);
-            s_tile[1] = 1;
-            break;
-          }
-          __nanosleep(128);
-        }
-      }
-      base = a.chunk_base[uint64_t(chunk) * kRadix + d];
-    }
-    s_off[d] = base + excl - s_excl[d];
-    if (last_in_chunk) {  // hand the next chunk its 64-bit bases
-      a.chunk_base[uint64_t(chunk + 1) * kRadix + d] = base + excl + cnt;
-      __threadfence();
-    }
-  }
+  if (tid < kRadix)
+    if (!digit_offset(a, tile, chunk, chunk_first, first_in_chunk, last_in_chunk, base_row, uint32_t(tid), s_cnt[tid],
+                      s_excl[tid], lb, s_off))
+      s_tile[1] = 1;
   __syncthreads();
   if (last_in_chunk && tid == 0) st_release_gpu(a.chunk_flag + chunk + 1, 1u);
 
