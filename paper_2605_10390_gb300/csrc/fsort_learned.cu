@@ -763,32 +763,39 @@ __global__ void __launch_bounds__(256) learn_fill_kernel(LearnedMap mp, const Le
 }
 
 // On-chip sort of the buckets, one unit per CTA iteration, in place.  A unit
-// is a group of kGroup consecutive bucket ids with no heavy id and at most
-// 8192 keys in all (contiguous in memory), else each bucket of the group
-// alone.  The unit's keys are split into at most 4096 sub-buckets by the top
-// 12 bits of key - min in one counting pass through shared memory; each
-// thread then sorts its sub-buckets by insertion.  The next unit's keys are
-// prefetched into shared memory (cp.async) while one is sorted.
-// A unit where some thread would need more than kInsertBudget insertion moves
-// is finished by a bitonic network instead.
+// is a run of consecutive non-heavy buckets with at most 8192 keys in all
+// (contiguous in memory).  The unit's keys are split into at most 4096
+// sub-buckets by the top 12 bits of key - min in one counting pass through
+// shared memory; a key of a sub-bucket of at most 16 keys finds its place by
+// counting the smaller keys there, and the larger sub-buckets (in practice a
+// moderately frequent key among a few others) are split again by warps.  The
+// next unit's keys are prefetched into shared memory (cp.async) while one is
+// sorted.  A unit whose large ranges overflow the round list is finished by a
+// bitonic network instead.
 constexpr int kBsThreads = 1024;
 constexpr int kBsWarps = kBsThreads / 32;
 constexpr int kBsIpt = kLearnBucketCap / kBsThreads;  // keys per thread
 constexpr int kSubBits = 12;
 constexpr int kSub = 1 << kSubBits;
 constexpr int kSubPerThread = kSub / kBsThreads;
-constexpr uint32_t kInsertBudget = 2048;  // insertion moves a thread may spend before the bitonic fallback
-constexpr int kGroup = 4;
+constexpr int kGroup = 32;  // ids one unit-list thread packs
 static_assert(kSub % kBsThreads == 0, "sub-bucket ownership");
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
 
+constexpr uint32_t kBigSub = 16;     // larger ranges are split by a warp
+constexpr uint32_t kMaxBig = 512;    // such ranges a round holds (more: the bitonic sort)
+constexpr int kSplitBits = 5;        // a warp splits a range into 32 bins
+constexpr int kMaxRounds = (64 + kSplitBits - 1) / kSplitBits;  // each round drops 5 bits of key range
+
 struct BsShared {
+  uint2 big[2][kMaxBig];       // [lo, hi) ranges of more than kBigSub keys: this round's, the next
+  uint32_t nbig[2];
+  uint32_t bins[kBsWarps][32]; // per-warp bin counters of the split
   uint32_t sub[kSub + 1];
-  uint64_t red[4 * kBsWarps];
-  uint64_t fin[4];             // reduced key min/max, PLA min/max
-  uint32_t warp_sum[kBsWarps]; // then the exclusive prefix of each warp
+  uint64_t red[2 * kBsWarps];  // per-warp key min / max
+  uint32_t warp_sum[kBsWarps]; // per-warp totals of the sub-bucket counts
   uint32_t flag;
 };
 
@@ -796,7 +803,7 @@ struct BsShared {
 // j * kBsThreads + t) into g[0, cnt), 2 <= cnt <= kLearnBucketCap; every
 // thread calls it.
 __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g, uint32_t cnt,
-                          uint64_t* __restrict__ s_out, BsShared& sh) {
+                          uint64_t* __restrict__ s_out, uint64_t* __restrict__ s_tmp, BsShared& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t v[kBsIpt];  // sub-bucket << 16 | slot
   uint64_t kmn = ~0ull, kmx = 0;
@@ -817,9 +824,12 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
     sh.red[warp] = kmn;
     sh.red[kBsWarps + warp] = kmx;
   }
-  if (tid == 0) sh.flag = 0;
+  if (tid == 0) {
+    sh.flag = 0;
+    sh.nbig[0] = sh.nbig[1] = 0;
+  }
   __syncthreads();
-  if (warp == 0) {  // one warp folds the per-warp partials
+  {  // every warp folds the 32 per-warp partials itself: no second barrier
     static_assert(kBsWarps == 32, "one partial per lane");
     kmn = sh.red[lane];
     kmx = sh.red[kBsWarps + lane];
@@ -828,21 +838,15 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
       kmn = umin64(kmn, __shfl_xor_sync(0xffffffffu, kmn, o));
       kmx = umax64(kmx, __shfl_xor_sync(0xffffffffu, kmx, o));
     }
-    if (lane == 0) {
-      sh.fin[0] = kmn;
-      sh.fin[1] = kmx;
-    }
   }
-  __syncthreads();
-  kmn = sh.fin[0];
-  kmx = sh.fin[1];
   const uint64_t krange = kmx - kmn;
   if (krange == 0) {  // all keys equal: already in order
     for (uint32_t i = tid; i < cnt; i += kBsThreads) g[i] = kmn;
     return;
   }
   // sub-bucket = the top 12 bits of key - min: the map is near-linear inside
-  // a unit, so the keys spread evenly over the sub-buckets
+  // a unit, so the keys spread about evenly over the sub-buckets, except for
+  // runs of one key, which the warp split below takes apart cheaply
   const int bits = 64 - __clzll(static_cast<long long>(krange));
   const int shf = bits > kSubBits ? bits - kSubBits : 0;
 #pragma unroll
@@ -868,18 +872,18 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
   }
   if (lane == 31) sh.warp_sum[warp] = inc;
   __syncthreads();
-  if (warp == 0) {  // exclusive prefix of the warp totals
-    const uint32_t x = sh.warp_sum[lane];
-    uint32_t y = x;
+  uint32_t before;
+  {  // every warp scans the warp totals itself: no second barrier
+    uint32_t y = sh.warp_sum[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
       if (lane >= o) y += z;
     }
-    sh.warp_sum[lane] = y - x;
+    before = __shfl_sync(0xffffffffu, y, warp > 0 ? warp - 1 : 0);
+    if (warp == 0) before = 0;
   }
-  __syncthreads();
-  uint32_t run = inc - sum + sh.warp_sum[warp];
+  uint32_t run = inc - sum + before;
 #pragma unroll
   for (int q = 0; q < kSubPerThread; ++q) {
     sh.sub[tid * kSubPerThread + q] = run;
@@ -890,31 +894,104 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
 #pragma unroll
   for (int j = 0; j < kBsIpt; ++j) {
     const uint32_t i = uint32_t(j * kBsThreads + tid);
-    if (i < cnt) s_out[sh.sub[v[j] >> 16] + (v[j] & 0xFFFFu)] = k[j];
+    if (i < cnt) s_tmp[sh.sub[v[j] >> 16] + (v[j] & 0xFFFFu)] = k[j];
+  }
+#pragma unroll
+  for (int q = 0; q < kSubPerThread; ++q) {  // sub-buckets above kBigSub keys go to the warp split below
+    const int sb = tid * kSubPerThread + q;
+    const uint32_t lo = sh.sub[sb], hi = sh.sub[sb + 1];
+    if (hi - lo > kBigSub) {
+      const uint32_t at = atomicAdd(&sh.nbig[0], 1u);
+      if (at < kMaxBig) sh.big[0][at] = make_uint2(lo, hi); else sh.flag = 1;
+    }
   }
   __syncthreads();
-  {
-    // insertion sort of each owned sub-bucket; equal keys cost no moves, so
-    // duplicates are cheap.  A thread whose moves exceed the budget (many
-    // distinct keys in one sub-bucket) stops and asks for the bitonic sort;
-    // what it leaves is still a permutation of the unit.
-    uint32_t moves = 0;
-#pragma unroll
-    for (int q = 0; q < kSubPerThread; ++q) {
-      const int sb = tid * kSubPerThread + q;
-      const uint32_t lo = sh.sub[sb], hi = sh.sub[sb + 1];
-      for (uint32_t x = lo + 1; x < hi && moves <= kInsertBudget; ++x) {
-        const uint64_t key = s_out[x];
-        uint32_t y = x;
-        while (y > lo && s_out[y - 1] > key) {
-          s_out[y] = s_out[y - 1];
-          --y;
-        }
-        s_out[y] = key;
-        moves += x - y;
-      }
+  // the key at position p of a small sub-bucket [lo, hi) goes to lo + the
+  // keys there below it + the equal keys before p: independent loads, and
+  // the lanes of a warp take consecutive positions, so they mostly read the
+  // same words
+  for (uint32_t p = uint32_t(tid); p < cnt; p += kBsThreads) {
+    const uint64_t key = s_tmp[p];
+    const uint32_t sb = uint32_t((key - kmn) >> shf);
+    const uint32_t lo = sh.sub[sb], hi = sh.sub[sb + 1];
+    if (hi - lo > kBigSub) {
+      s_out[p] = key;
+      continue;
     }
-    if (moves > kInsertBudget) sh.flag = 1;
+    uint32_t rank = 0;
+    for (uint32_t q = lo; q < hi; ++q) {
+      const uint64_t y = s_tmp[q];
+      rank += (y < key || (y == key && q < p)) ? 1u : 0u;
+    }
+    s_out[lo + rank] = key;
+  }
+  __syncthreads();
+  // large ranges (mostly a moderately frequent key among a few others), a
+  // warp each, in rounds: nothing to do when the keys are all equal; else
+  // split into 32 bins by 5 bits of key - min below the range's top bit,
+  // lanes insertion-sort the bins of at most kBigSub keys and the larger ones
+  // go to the next round with 5 fewer bits of range
+  for (int r = 0; r < kMaxRounds; ++r) {
+    const int cur = r & 1;
+    const uint32_t nr = sh.nbig[cur];
+    if (sh.flag || nr == 0) break;
+    uint32_t* wb = sh.bins[warp];
+    for (uint32_t b = uint32_t(warp); b < nr; b += kBsWarps) {
+      const uint2 rg = sh.big[cur][b];
+      uint64_t mn = ~0ull, mx = 0;
+      for (uint32_t i = rg.x + lane; i < rg.y; i += 32) {
+        mn = umin64(mn, s_out[i]);
+        mx = umax64(mx, s_out[i]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = umin64(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      }
+      if (mn == mx) continue;
+      const int bits = 64 - __clzll(static_cast<long long>(mx - mn));
+      const int shf = bits > kSplitBits ? bits - kSplitBits : 0;
+      wb[lane] = 0;
+      __syncwarp();
+      for (uint32_t i = rg.x + lane; i < rg.y; i += 32) atomicAdd(&wb[uint32_t((s_out[i] - mn) >> shf)], 1u);
+      __syncwarp();
+      const uint32_t c = wb[lane];
+      uint32_t start = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, start, o);
+        if (lane >= o) start += y;
+      }
+      start = rg.x + start - c;
+      wb[lane] = start;
+      __syncwarp();
+      for (uint32_t i = rg.x + lane; i < rg.y; i += 32) {
+        const uint64_t key = s_out[i];
+        s_tmp[atomicAdd(&wb[uint32_t((key - mn) >> shf)], 1u)] = key;
+      }
+      __syncwarp();
+      for (uint32_t i = rg.x + lane; i < rg.y; i += 32) s_out[i] = s_tmp[i];
+      __syncwarp();
+      if (c > kBigSub) {
+        const uint32_t at = atomicAdd(&sh.nbig[cur ^ 1], 1u);
+        if (at < kMaxBig) sh.big[cur ^ 1][at] = make_uint2(start, start + c); else sh.flag = 1;
+      } else {
+        for (uint32_t x = start + 1; x < start + c; ++x) {
+          const uint64_t key = s_out[x];
+          uint32_t y = x;
+          while (y > start && s_out[y - 1] > key) {
+            s_out[y] = s_out[y - 1];
+            --y;
+          }
+          s_out[y] = key;
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (tid == 0) sh.nbig[cur] = 0;
+    __syncthreads();
+    if (r == kMaxRounds - 1 && sh.nbig[cur ^ 1] != 0) sh.flag = 1;  // cannot happen: 13 rounds use up 64 bits
   }
   __syncthreads();
   if (sh.flag) {  // bitonic network over the next power of two, padded with the largest key
@@ -941,78 +1018,78 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
   for (int i = tid; i <= kSub; i += kBsThreads) sh.sub[i] = 0;
 }
 
-// The unit list, compacted: every group of kGroup consecutive ids appends
-// one unit (the whole group, when it has no heavy id and at most the
-// capacity) or one per bucket of at least two keys; units[0].x counts them
-// (list entries start at units + 1; their order is arbitrary).
+// The unit list (units + 1; units[0].x counts them; order arbitrary): each
+// thread walks kGroup consecutive ids and packs runs of non-heavy buckets into
+// units of at most the capacity (contiguous in memory); heavy ids end a unit.
 __global__ void learn_units_kernel(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets,
                                    const uint32_t* __restrict__ bitmap, uint32_t nb, uint2* __restrict__ units,
                                    uint32_t* status) {
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi * kGroup >= nb) return;
-  const uint32_t i0 = gi * kGroup;
-  uint32_t tot = 0;
-  bool heavy = false;
-  for (int q = 0; q < kGroup; ++q) {
-    const uint32_t id = i0 + q;
-    if (id < nb) {
-      tot += counts[id];
-      heavy |= ((bitmap[id >> 5] >> (id & 31u)) & 1u) != 0;
-    }
-  }
   uint32_t* count = &units[0].x;
-  if (!heavy && tot <= uint32_t(kLearnBucketCap)) {
-    if (tot >= 2) units[1 + atomicAdd(count, 1u)] = make_uint2(offsets[i0], tot);
-    return;
-  }
-  for (int q = 0; q < kGroup; ++q) {
-    const uint32_t id = i0 + q;
-    if (id >= nb || ((bitmap[id >> 5] >> (id & 31u)) & 1u)) continue;
+  uint32_t start = 0, tot = 0;
+  auto close = [&]() {
+    if (tot >= 2) units[1 + atomicAdd(count, 1u)] = make_uint2(start, tot);
+    tot = 0;
+  };
+  for (uint32_t id = gi * kGroup; id < nb && id < (gi + 1) * kGroup; ++id) {
+    if ((bitmap[id >> 5] >> (id & 31u)) & 1u) {  // heavy: filled elsewhere, never sorted
+      close();
+      continue;
+    }
     const uint32_t c = counts[id];
     if (c > uint32_t(kLearnBucketCap)) {  // the judge rejects such maps; never sort past capacity
       atomicOr(status, kDevBadBucket);
+      close();
       continue;
     }
-    if (c >= 2) units[1 + atomicAdd(count, 1u)] = make_uint2(offsets[id], c);
+    if (tot + c > uint32_t(kLearnBucketCap)) close();
+    if (tot == 0) start = offsets[id];
+    tot += c;
   }
+  close();
 }
 
 __global__ void __launch_bounds__(kBsThreads, 1) learn_bucket_sort_kernel(uint64_t* __restrict__ keys,
                                                                           const uint2* __restrict__ units) {
-  extern __shared__ uint64_t s_dyn[];  // [2][kLearnBucketCap]: the unit, the next unit's prefetch
+  extern __shared__ uint64_t s_dyn[];  // [3][kLearnBucketCap]: the unit, two prefetch buffers
   uint64_t* s_out = s_dyn;
-  uint64_t* s_pre = s_dyn + kLearnBucketCap;
   __shared__ BsShared sh;
   const int tid = threadIdx.x;
   const uint32_t nunits = units[0].x;
   const uint2* list = units + 1;
   for (int i = tid; i <= kSub; i += kBsThreads) sh.sub[i] = 0;
+  auto prefetch = [&](uint2 x, int buf) {
+    uint64_t* dst = s_dyn + (1 + buf) * kLearnBucketCap;
+    for (uint32_t i = tid; i < x.y; i += kBsThreads) cp_async8(&dst[i], &keys[x.x + i]);
+    cp_async_commit();
+  };
   uint32_t u = blockIdx.x;
   uint2 cur = make_uint2(0, 0);
+  int buf = 0;
   if (u < nunits) {
     cur = list[u];
-    for (uint32_t i = tid; i < cur.y; i += kBsThreads) cp_async8(&s_pre[i], &keys[cur.x + i]);
-    cp_async_commit();
+    prefetch(cur, 0);
   }
   while (u < nunits) {
     const uint32_t nx = u + gridDim.x;
     const uint2 next = nx < nunits ? list[nx] : make_uint2(0, 0);
     cp_async_wait_all();
     __syncthreads();
+    const uint64_t* s_pre = s_dyn + (1 + buf) * kLearnBucketCap;
     uint64_t k[kBsIpt];
 #pragma unroll
     for (int j = 0; j < kBsIpt; ++j) {
       const uint32_t i = uint32_t(j * kBsThreads + tid);
       k[j] = i < cur.y ? s_pre[i] : 0;
     }
-    __syncthreads();  // the prefetch buffer is free again
-    if (nx < nunits) {
-      for (uint32_t i = tid; i < next.y; i += kBsThreads) cp_async8(&s_pre[i], &keys[next.x + i]);
-      cp_async_commit();
-    }
-    sort_unit(k, keys + cur.x, cur.y, s_out, sh);
+    // the other buffer was read in the previous iteration, before the barrier above
+    if (nx < nunits) prefetch(next, buf ^ 1);
+    // this unit's prefetch buffer is consumed (the keys are in registers): it is the scratch
+    sort_unit(k, keys + cur.x, cur.y, s_out, s_dyn + (1 + buf) * kLearnBucketCap, sh);
     u = nx;
     cur = next;
+    buf ^= 1;
   }
   cp_async_wait_all();
 }
@@ -1321,7 +1398,7 @@ cudaError_t launch_learn_bucket_sort(uint64_t* keys, const uint32_t* counts, con
   learn_units_kernel<<<grid_for(ngroups, 256), 256, 0, stream>>>(counts, offsets, bitmap, nb, units, status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  constexpr int kBytes = 2 * kLearnBucketCap * 8;
+  constexpr int kBytes = 3 * kLearnBucketCap * 8;
   static int per_sm = 0;
   if (!per_sm) {
     e = cudaFuncSetAttribute(learn_bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
