@@ -71,6 +71,9 @@ typedef enum fsort_status {
 #define FSORT_FLAG_HOST_IO 0x4u /* also allocate device buffers of max_n keys (+values) for fsort_sort_pairs_host */
 #define FSORT_FLAG_GRAPH 0x2u   /* batched sorts replay a captured CUDA graph when the batch shape repeats */
 #define FSORT_FLAG_LEARNED 0x8u /* allocate the learned bucket mapping (64-bit keys only); see fsort_learned_fit */
+#define FSORT_FLAG_CHAINED_SCATTER 0x10u /* every scatter pass in the chained (decoupled look-back) form; by
+                                            default sorts of n < 2^32 keys read their tiles' digit offsets from
+                                            a table of per-tile counts made before each pass */
 
 typedef struct fsort_plan fsort_plan;
 
@@ -423,11 +426,13 @@ FSORT_API fsort_status fsort_expand(fsort_plan* plan, const uint64_t* counts, vo
 #define FSORT_KERNEL_LEARN_SCATTER2 13 /* learned path: scan + keys to their buckets */
 #define FSORT_KERNEL_LEARN_FILL 14     /* learned path: heavy buckets */
 #define FSORT_KERNEL_LEARN_BUCKETS 15  /* learned path: on-chip sort of every bucket */
+#define FSORT_KERNEL_TILE_COUNT 16     /* table scatter: per-tile digit counts of a later pass's input */
+#define FSORT_KERNEL_TILE_SCAN 17      /* table scatter: per-chunk digit offsets (scan of the chunk totals) */
 
 typedef struct fsort_kernel_time {
   int32_t kind;   /* FSORT_KERNEL_* */
-  int32_t pass;   /* scatter pass index, else -1 */
-  int32_t active; /* scatter/copy: 1 if the device schedule ran it (0: exited at once); others 1 */
+  int32_t pass;   /* scatter, tile count and tile scan: the pass index, else -1 */
+  int32_t active; /* per-pass kernels and copy: 1 if the device schedule ran it (0: exited at once); others 1 */
   int32_t call;   /* index of the sort call since timing was enabled or last reported */
   uint64_t n;     /* keys of that call */
   float ms;       /* device time between CUDA events recorded around the launch on the call's stream */

@@ -13,6 +13,7 @@ _lib = None
 FSORT_FLAG_HOST_IO = 0x4
 FSORT_FLAG_GRAPH = 0x2
 FSORT_FLAG_LEARNED = 0x8
+FSORT_FLAG_CHAINED_SCATTER = 0x10
 FSORT_MLP_PARAMS = 4353
 FSORT_LEARN_CELLS = 56320
 FSORT_LEARN_MAX_HEAVY = 8192
@@ -110,7 +111,8 @@ class FsortServeStats(ctypes.Structure):
 
 KERNEL_KINDS = {1: "histogram", 2: "scan", 3: "scatter", 4: "copy", 5: "leaf_hist", 6: "leaf_reduce",
                 7: "leaf_scan", 8: "expand", 9: "learn_count1", 10: "learn_scatter1", 11: "learn_count2",
-                12: "learn_judge", 13: "learn_scatter2", 14: "learn_fill", 15: "learn_buckets"}
+                12: "learn_judge", 13: "learn_scatter2", 14: "learn_fill", 15: "learn_buckets", 16: "tile_count",
+                17: "tile_scan"}
 
 
 def lib_path() -> str:

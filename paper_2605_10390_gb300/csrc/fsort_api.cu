@@ -92,6 +92,12 @@ struct fsort_plan {
   uint32_t* chunk_flag = nullptr; // [kMaxPasses][max_chunks]
   Schedule* sched = nullptr;
   uint32_t* status = nullptr;    // sticky device error bits
+  uint64_t table_tiles = 0;      // tiles of the largest sort the offset table serves (n < 2^32)
+  uint32_t table_chunks = 0;     // chunks of the count kernel (at most two per SM)
+  uint32_t* tilerel = nullptr;   // [table_tiles][256] per-tile digit offsets within the tile's chunk
+  uint32_t* chunksum = nullptr;  // [table_chunks][256] per-chunk digit totals
+  uint32_t* chunkoff = nullptr;  // [table_chunks][256] per-chunk digit output offsets
+  bool chained = false;          // FSORT_FLAG_CHAINED_SCATTER: always the look-back scatter
   uint32_t* leaf_part = nullptr; // expand path (16-bit keys)
   uint64_t* leaf_spill = nullptr;
   uint64_t* leaf_counts = nullptr;
@@ -276,6 +282,68 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
   }
   CallTimer tm(p, n, s, true);
   const DigitPlan plan = make_plan(key_bits, precision_bits, p->digit_bits);
+  const void* kb[3] = {keys_in, p->alt_keys, keys_out};
+  const uint32_t* vb[3] = {vals_in, p->alt_vals, vals_out};
+  if (!p->chained && n < (1ull << 32)) {
+    // Scatter passes over a table of per-tile offsets: one read of the input
+    // for every pass's histogram and the first pass's table; before each later
+    // pass, one read of its input for its table.
+    const TableGeom g = table_geometry(n, key_bits, p->sms);
+    TileCountArgs ca{};
+    for (int b = 0; b < 3; ++b) ca.keys[b] = kb[b];
+    ca.n = n;
+    ca.plan = plan;
+    ca.tile = g.tile;
+    ca.tiles = g.tiles;
+    ca.chunk_tiles = g.chunk_tiles;
+    ca.tilerel = p->tilerel;
+    ca.chunksum = p->chunksum;
+    ca.hist = p->hist;
+    ca.status = p->status;
+    e = launch_tile_count(ca, key_bits, plan.passes, g.chunks, s);
+    tm.mark(FSORT_KERNEL_HISTOGRAM, -1);
+    if (e == cudaSuccess)
+      e = launch_scan_schedule(p->hist, p->chunk_base, p->chunk_flag, plan.passes, 1, in_place ? 1 : 0, p->sched, s);
+    tm.mark(FSORT_KERNEL_SCAN, -1);
+    for (int j = 0; j < plan.passes && e == cudaSuccess; ++j) {
+      if (j > 0) {
+        TileCountArgs cj = ca;
+        cj.plan.passes = 1;
+        cj.plan.shift[0] = plan.shift[j];
+        cj.plan.mask[0] = plan.mask[j];
+        cj.hist = nullptr;
+        cj.sched = p->sched;
+        cj.pass = j;
+        e = launch_tile_count(cj, key_bits, 1, g.chunks, s);
+        tm.mark(FSORT_KERNEL_TILE_COUNT, j);
+      }
+      if (e == cudaSuccess)
+        e = launch_chunk_scan(p->chunksum, g.chunks, p->chunk_base + uint64_t(j) * kRadix, p->sched, j, p->chunkoff, s);
+      tm.mark(FSORT_KERNEL_TILE_SCAN, j);
+      TileScatterArgs a{};
+      for (int b = 0; b < 3; ++b) {
+        a.keys[b] = kb[b];
+        a.vals[b] = has_vals ? vb[b] : nullptr;
+      }
+      a.n = n;
+      a.shift = plan.shift[j];
+      a.mask = plan.mask[j];
+      a.tiles = g.tiles;
+      a.chunk_tiles = g.chunk_tiles;
+      a.tilerel = p->tilerel;
+      a.chunkoff = p->chunkoff;
+      a.sched = p->sched;
+      a.pass = j;
+      a.status = p->status;
+      if (e == cudaSuccess) e = launch_tile_scatter(a, key_bits, has_vals, s);
+      tm.mark(FSORT_KERNEL_SCATTER, j);
+    }
+    if (e == cudaSuccess) e = launch_schedule_copy(kb, vb, key_bits, has_vals, n, p->sched, p->sms, s);
+    tm.mark(FSORT_KERNEL_COPY, -1);
+    tm.finish();
+    if (e != cudaSuccess) return from_cuda(e);
+    return finish_call(p, s);
+  }
   const uint64_t tiles = (n + p->tile - 1) / p->tile;
   const uint64_t chunks = (n + p->chunk_keys - 1) / p->chunk_keys;
   const uint64_t clear_words = kCounterBytes / 4 + tiles * kRadix;
@@ -285,8 +353,6 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
     e = launch_scan_schedule(p->hist, p->chunk_base, p->chunk_flag, plan.passes, uint32_t(chunks),
                              in_place ? 1 : 0, p->sched, s);
   tm.mark(FSORT_KERNEL_SCAN, -1);
-  const void* kb[3] = {keys_in, p->alt_keys, keys_out};
-  const uint32_t* vb[3] = {vals_in, p->alt_vals, vals_out};
   for (int j = 0; j < plan.passes && e == cudaSuccess; ++j) {
     OnesweepArgs a{};
     for (int b = 0; b < 3; ++b) {
@@ -655,7 +721,8 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   if (!valid_key_bits(desc->key_bits) || desc->max_n < 1) return FSORT_ERR_INVALID_ARG;
   if (desc->has_values != 0 && desc->has_values != 1) return FSORT_ERR_INVALID_ARG;
   if (desc->digit_bits != 0 && desc->digit_bits != 8) return FSORT_ERR_UNSUPPORTED;
-  if (desc->flags & ~(FSORT_FLAG_HOST_IO | FSORT_FLAG_GRAPH | FSORT_FLAG_LEARNED)) return FSORT_ERR_INVALID_ARG;
+  if (desc->flags & ~(FSORT_FLAG_HOST_IO | FSORT_FLAG_GRAPH | FSORT_FLAG_LEARNED | FSORT_FLAG_CHAINED_SCATTER))
+    return FSORT_ERR_INVALID_ARG;
   if ((desc->flags & FSORT_FLAG_LEARNED) && desc->key_bits != 64) return FSORT_ERR_UNSUPPORTED;
   if (desc->max_n > (1ull << 36)) return FSORT_ERR_UNSUPPORTED;
 
@@ -670,6 +737,13 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   }
   const int kb = desc->key_bits / 8;
   const uint64_t n = desc->max_n;
+  p->chained = (desc->flags & FSORT_FLAG_CHAINED_SCATTER) != 0;
+  if (!p->chained) {
+    const uint64_t tn = n < (1ull << 32) ? n : (1ull << 32) - 1;
+    const uint64_t tt = uint64_t(table_tile_keys_for(desc->key_bits));
+    p->table_tiles = (tn + tt - 1) / tt;
+    p->table_chunks = uint32_t(p->sms) * 2;
+  }
   p->tile = tile_keys_for(desc->key_bits);
   p->chunk_keys = chunk_keys_for(desc->key_bits);
   p->max_tiles = (n + p->tile - 1) / p->tile;
@@ -696,6 +770,9 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   const size_t o_cflag = take(size_t(kMaxPasses) * p->max_chunks * 4);
   const size_t o_sched = take(sizeof(Schedule));
   const size_t o_status = take(sizeof(uint32_t));
+  const size_t o_trel = take(size_t(p->table_tiles) * kRadix * 4);
+  const size_t o_csum = take(size_t(p->table_chunks) * kRadix * 4);
+  const size_t o_coff = take(size_t(p->table_chunks) * kRadix * 4);
   size_t o_lpart = 0, o_lspill = 0, o_lcnt = 0, o_loff = 0;
   const bool batch = desc->max_segments > 0;
   if (desc->max_segments > 65535) {
@@ -788,6 +865,9 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   p->chunk_flag = reinterpret_cast<uint32_t*>(w + o_cflag);
   p->sched = reinterpret_cast<Schedule*>(w + o_sched);
   p->status = reinterpret_cast<uint32_t*>(w + o_status);
+  p->tilerel = reinterpret_cast<uint32_t*>(w + o_trel);
+  p->chunksum = reinterpret_cast<uint32_t*>(w + o_csum);
+  p->chunkoff = reinterpret_cast<uint32_t*>(w + o_coff);
   if (batch) {
     p->d_seg_large = reinterpret_cast<SegDesc*>(w + o_bsl);
     p->d_seg_small = reinterpret_cast<SegDesc*>(w + o_bss);
@@ -1327,7 +1407,9 @@ fsort_status fsort_plan_timing_report(fsort_plan* plan, fsort_kernel_time* out, 
     o.n = r.n;
     o.reserved = 0.f;
     o.active = 1;
-    if (r.slot >= 0 && r.kind == FSORT_KERNEL_SCATTER) o.active = t.h_sched[r.slot].pass[r.pass].active;
+    if (r.slot >= 0 && r.pass >= 0 &&
+        (r.kind == FSORT_KERNEL_SCATTER || r.kind == FSORT_KERNEL_TILE_COUNT || r.kind == FSORT_KERNEL_TILE_SCAN))
+      o.active = t.h_sched[r.slot].pass[r.pass].active;
     if (r.slot >= 0 && r.kind == FSORT_KERNEL_COPY) o.active = t.h_sched[r.slot].copy.active;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, t.ev[r.ev0], t.ev[r.ev1]) != cudaSuccess) return FSORT_ERR_CUDA;

@@ -1,0 +1,476 @@
+// fsort_blocks.cu -- the scatter passes (Sec. II: "stable scatter") as
+// reduce-then-scan over a table of per-tile digit offsets: no chain between
+// tiles.
+//
+//  KT1 tile_count_kernel    one read of a pass's input: the digit counts of
+//                           every tile (and, on the first read of the input,
+//                           every pass's digit histogram for the schedule).
+//  KT2 column scan          per digit, the exclusive scan of the tile counts
+//                           on top of the digit's global base (Alg. 3's rank
+//                           of every leaf, split over tiles): the first output
+//                           position of digit d for tile t.
+//  KT3 tile_scatter_kernel  one CTA per tile: bulk copy of keys and values into
+//                           shared memory, stable in-warp ranks, the tile's
+//                           digit prefixes, permutation into digit order in
+//                           shared memory, and the write-out in digit runs at
+//                           the tile's table offsets.
+//
+// The tile-local steps are those of the chained scatter (fsort_onesweep.cu);
+// what differs is where a tile's digit offsets come from: the chained form
+// waits for its predecessors' prefixes (decoupled look-back), this form reads
+// them from a table that one extra read of the pass input (2 bytes per 16-bit
+// key) and a small scan made before the pass.  Tiles run in launch order, so
+// the runs that neighbouring tiles write into the same output lines meet in
+// L2 at about the same time.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fsort_dev.cuh"
+#include "fsort_internal.h"
+#include "fsort_rank.cuh"
+
+namespace fsort {
+namespace {
+
+constexpr int kRadix = 256;
+constexpr int kCountThreads = 1024;
+constexpr int kScanThreads = 1024;
+
+// Scatter tiles: threads, keys per thread, CTAs per SM.
+template <typename K>
+struct TileShape;
+template <>
+struct TileShape<uint16_t> { static constexpr int kBlock = 512, kIpt = 16, kMinBlocks = 2; };
+template <>
+struct TileShape<uint32_t> { static constexpr int kBlock = 512, kIpt = 12, kMinBlocks = 2; };
+template <>
+struct TileShape<uint64_t> { static constexpr int kBlock = 512, kIpt = 8, kMinBlocks = 2; };
+
+// ------------------------------------------------------------------ KT1 ----
+// P = digits counted per key (compile time).  Digit 0 of `plan` is the pass
+// whose table is written: CTA c walks the tiles of chunk c in order and writes
+// for each tile the counts of its digits in the chunk's earlier tiles
+// (tilerel[t][256]), then the chunk's totals (chunksum[c][256]).  With `hist`
+// set, all P digits are also added to the global 64-bit histogram hist[j][256].
+// The chunk streams through kCountStages shared-memory buffers of kStepTiles
+// tiles each, filled by bulk copies while earlier steps are counted.
+constexpr int kStepTiles = 2;
+constexpr int kCountStages = 3;
+
+// Count CTAs per SM: two for 16-bit keys (3 x 32 KB of buffers each), one for
+// wider keys.
+template <typename K>
+__host__ __device__ constexpr int count_ctas_per_sm() { return sizeof(K) == 2 ? 2 : 1; }
+template <typename K>
+__host__ __device__ constexpr uint32_t count_step_keys() {
+  return uint32_t(kStepTiles) * TileShape<K>::kBlock * TileShape<K>::kIpt;
+}
+template <typename K>
+__host__ __device__ constexpr size_t count_smem_bytes() {
+  return size_t(kCountStages) * count_step_keys<K>() * sizeof(K);
+}
+
+template <typename K, int P>
+__global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_count_kernel(TileCountArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];  // [kCountStages][step keys]
+  __shared__ uint32_t s_tile[kStepTiles][kRadix];             // digit 0, the step's tiles
+  __shared__ uint32_t s_rest[(P > 1 ? P - 1 : 1) * kRadix];  // digits 1.., whole CTA
+  __shared__ uint64_t s_bar[kCountStages];
+  __shared__ uint32_t s_fail;
+  constexpr uint32_t kStepKeys = count_step_keys<K>();
+  constexpr uint32_t kVec = 16 / sizeof(K);
+  static_assert(kStepTiles == 2, "a key's tile within the step is one comparison");
+  K* buf = reinterpret_cast<K*>(smem);
+  const K* keys;
+  if (a.sched) {
+    const PassDesc pd = a.sched->pass[a.pass];
+    if (!pd.active) return;
+    keys = static_cast<const K*>(a.keys[pd.src]);
+  } else {
+    keys = static_cast<const K*>(a.keys[kBufIn]);
+  }
+  const int tid = threadIdx.x;
+  const uint32_t t_begin = blockIdx.x * a.chunk_tiles;
+  const uint32_t t_end = (t_begin + a.chunk_tiles < a.tiles) ? t_begin + a.chunk_tiles : a.tiles;
+  const uint64_t k_end = (uint64_t(t_end) * a.tile < a.n) ? uint64_t(t_end) * a.tile : a.n;
+  const uint32_t steps = (t_end - t_begin + kStepTiles - 1) / kStepTiles;
+  // step s covers keys [e0, e1); its body of whole 16-byte vectors is copied in bulk
+  auto step_range = [&](uint32_t st, uint64_t& e0, uint64_t& e1) {
+    e0 = uint64_t(t_begin + st * kStepTiles) * a.tile;
+    e1 = (e0 + uint64_t(kStepTiles) * a.tile < k_end) ? e0 + uint64_t(kStepTiles) * a.tile : k_end;
+  };
+  auto issue = [&](uint32_t st) {  // thread 0 only
+    uint64_t e0, e1;
+    step_range(st, e0, e1);
+    const uint32_t bytes = uint32_t((e1 - e0) * sizeof(K)) & ~15u;
+    uint64_t* bar = &s_bar[st % kCountStages];
+    mbar_arrive_expect_tx(bar, bytes);
+    if (bytes) bulk_copy_g2s(buf + size_t(st % kCountStages) * kStepKeys, keys + e0, bytes, bar);
+  };
+  if (tid == 0) {
+    for (int i = 0; i < kCountStages; ++i) mbar_init(&s_bar[i], 1);
+    fence_mbar_init();
+    s_fail = 0;
+    for (uint32_t st = 0; st < steps && st < uint32_t(kCountStages); ++st) issue(st);
+  }
+  for (int i = tid; i < kStepTiles * kRadix; i += kCountThreads) (&s_tile[0][0])[i] = 0;
+  for (int i = tid; i < (P - 1) * kRadix; i += kCountThreads) s_rest[i] = 0;
+  __syncthreads();
+
+  uint32_t shift[P], mask[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    shift[j] = a.plan.shift[j];
+    mask[j] = a.plan.mask[j];
+  }
+  auto count_key = [&](K k, uint32_t slot) {
+    atomicAdd(&s_tile[slot][dig(k, shift[0], mask[0])], 1u);
+#pragma unroll
+    for (int j = 1; j < P; ++j) atomicAdd(&s_rest[(j - 1) * kRadix + dig(k, shift[j], mask[j])], 1u);
+  };
+  uint32_t acc = 0;  // thread d < 256: digit d of pass 0 in the chunk's tiles so far
+  for (uint32_t st = 0; st < steps; ++st) {
+    uint64_t e0, e1;
+    step_range(st, e0, e1);
+    const uint32_t keys_n = uint32_t(e1 - e0);
+    const uint32_t body = (keys_n * uint32_t(sizeof(K)) & ~15u) / sizeof(K);
+    if (!mbar_wait_bounded(&s_bar[st % kCountStages], (st / kCountStages) & 1u)) s_fail = 1;
+    const K* b = buf + size_t(st % kCountStages) * kStepKeys;
+    const uint4* bv = reinterpret_cast<const uint4*>(b);
+    for (uint32_t v = tid; v < body / kVec; v += kCountThreads) {
+      const uint4 q = bv[v];
+      const uint32_t slot = (v * kVec >= a.tile) ? 1u : 0u;  // vectors never straddle tiles
+      const K* kk = reinterpret_cast<const K*>(&q);
+#pragma unroll
+      for (int e = 0; e < int(kVec); ++e) count_key(kk[e], slot);
+    }
+    for (uint32_t i = body + tid; i < keys_n; i += kCountThreads)  // ragged end of the keys
+      count_key(keys[e0 + i], i >= a.tile ? 1u : 0u);
+    __syncthreads();
+    if (s_fail) {  // the table would be wrong: mark it so that no scatter uses it
+      if (tid == 0) atomicOr(a.status, kDevTimeoutLoad | kDevBadTable);
+      return;
+    }
+    if (tid < kRadix) {
+#pragma unroll
+      for (int j = 0; j < kStepTiles; ++j) {
+        if (t_begin + st * kStepTiles + j < t_end) a.tilerel[uint64_t(t_begin + st * kStepTiles + j) * kRadix + tid] = acc;
+        acc += s_tile[j][tid];
+        s_tile[j][tid] = 0;
+      }
+    }
+    if (tid == 0 && st + kCountStages < steps) {  // every thread has read this buffer (barrier above)
+      fence_proxy_async_smem();
+      issue(st + kCountStages);
+    }
+    __syncthreads();
+  }
+  if (tid < kRadix) a.chunksum[uint64_t(blockIdx.x) * kRadix + tid] = acc;
+  if (a.hist) {
+    if (tid < kRadix && acc) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hist[tid]), (unsigned long long)acc);
+    for (int i = tid; i < (P - 1) * kRadix; i += kCountThreads) {
+      const uint32_t c = s_rest[i];
+      if (c) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hist[kRadix + i]), (unsigned long long)c);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ KT2 ----
+// One CTA per digit d: chunkoff[c][d] = base[d] + sum over c' < c of
+// chunksum[c'][d] (Alg. 3's rank of every leaf, split over chunks; 32-bit).
+__global__ void __launch_bounds__(kScanThreads) chunk_scan_kernel(const uint32_t* __restrict__ sum,
+                                                                  const uint64_t* __restrict__ base,
+                                                                  uint32_t chunks, const Schedule* sched,
+                                                                  int32_t pass, uint32_t* __restrict__ off) {
+  if (sched && !sched->pass[pass].active) return;
+  __shared__ uint32_t s_warp[32];
+  const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t running = uint32_t(base[d]);  // positions are below 2^32 on this path
+  for (uint32_t c0 = 0; c0 < chunks; c0 += kScanThreads) {
+    const uint32_t c = c0 + threadIdx.x;
+    const uint32_t x = c < chunks ? sum[uint64_t(c) * kRadix + d] : 0u;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+      const uint32_t t = s_warp[w];
+      before += w < warp ? t : 0u;
+      all += t;
+    }
+    if (c < chunks) off[uint64_t(c) * kRadix + d] = running + before + inc - x;
+    running += all;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ KT3 ----
+template <typename K, bool kVals>
+struct TileSmem {
+  static constexpr int kBlock = TileShape<K>::kBlock;
+  static constexpr int kIpt = TileShape<K>::kIpt;
+  static constexpr int kTile = kBlock * kIpt;
+  static constexpr int kWarps = kBlock / 32;
+  static constexpr size_t kKeys = 0;
+  static constexpr size_t kVals_ = kKeys + size_t(kTile) * sizeof(K);
+  static constexpr size_t kMask = kVals_ + (kVals ? size_t(kTile) * 4 : 0);
+  static constexpr size_t kMaskWords = 2 * size_t(kWarps) * kRadix;  // peer masks, double-buffered
+  static constexpr size_t kWcnt = kMask + kMaskWords * 4;
+  static constexpr size_t kOff = kWcnt + size_t(kWarps) * kRadix * 4;
+  static constexpr size_t kScan = kOff + kRadix * 4;
+  static constexpr size_t kBar = kScan + 16 * 4;
+  static constexpr size_t kBytes = kBar + 16;
+};
+
+// Buffer `sel` of a by-BufSel triple, selected without indexing the
+// parameter array (which would copy it to local memory).
+template <typename T>
+__device__ __forceinline__ T* pick(T* const (&b)[3], int sel) {
+  return sel == kBufIn ? b[0] : (sel == kBufAlt ? b[1] : b[2]);
+}
+
+template <typename K, bool kVals>
+__global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks)
+    tile_scatter_kernel(const TileScatterArgs a) {
+  using L = TileSmem<K, kVals>;
+  constexpr int kBlock = L::kBlock;
+  constexpr int kIpt = L::kIpt;
+  constexpr int kTile = L::kTile;
+  constexpr int kWarps = L::kWarps;
+  static_assert(kTile <= 65536, "in-warp ranks and source positions are kept in 16 bits");
+  static_assert(L::kMaskWords * 4 >= size_t(kTile) * (sizeof(K) == 2 ? 4 : 2), "records fit the mask words");
+  static_assert(L::kMask % 16 == 0, "16-byte clears");
+  extern __shared__ __align__(1024) unsigned char smem[];
+  K* s_keys = reinterpret_cast<K*>(smem + L::kKeys);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + L::kVals_);
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem + L::kMask);
+  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem + L::kWcnt);
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(smem + L::kOff);
+  uint32_t* s_scan = reinterpret_cast<uint32_t*>(smem + L::kScan);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + L::kBar);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  int src = kBufIn, dst = kBufOut;
+  if (a.sched) {
+    const PassDesc pd = a.sched->pass[a.pass];
+    if (!pd.active) return;
+    src = pd.src;
+    dst = pd.dst;
+  }
+  if (ld_relaxed_gpu(a.status) & kDevBadTable) return;  // the offsets are not trustworthy: write nothing
+  const uint32_t tile = blockIdx.x;
+  const uint64_t t0 = uint64_t(tile) * kTile;
+  const uint32_t tile_n = uint32_t((a.n - t0 < uint64_t(kTile)) ? (a.n - t0) : uint64_t(kTile));
+
+  // 1. stage the tile: bulk copies for the 16-byte-aligned body, plain loads
+  // for a ragged end; meanwhile clear the peer masks and warp counters.
+  const uint32_t kbody = (tile_n * uint32_t(sizeof(K))) & ~15u;
+  const uint32_t vbody = kVals ? ((tile_n * 4u) & ~15u) : 0u;
+  const K* kin = static_cast<const K*>(pick(a.keys, src));
+  const uint32_t* vin = pick(a.vals, src);
+  if (tid == 0) {
+    mbar_init(s_bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(s_bar, kbody + vbody);
+    if (kbody) bulk_copy_g2s(s_keys, kin + t0, kbody, s_bar);
+    if (vbody) bulk_copy_g2s(s_vals, vin + t0, vbody, s_bar);
+  }
+  {
+    uint4* z = reinterpret_cast<uint4*>(s_mask);
+    for (int i = tid; i < int((L::kMaskWords + size_t(kWarps) * kRadix) / 4); i += kBlock) z[i] = make_uint4(0, 0, 0, 0);
+  }
+  if (tid < kRadix)  // lands while the copy does
+    s_off[tid] = a.chunkoff[uint64_t(tile / a.chunk_tiles) * kRadix + tid] + a.tilerel[uint64_t(tile) * kRadix + tid];
+  for (uint32_t i = kbody / sizeof(K) + tid; i < tile_n; i += kBlock) s_keys[i] = kin[t0 + i];
+  if (kVals)
+    for (uint32_t i = vbody / 4 + tid; i < tile_n; i += kBlock) s_vals[i] = vin[t0 + i];
+  __syncthreads();  // the mbarrier's init is visible before anyone waits on it
+  if (!mbar_wait_bounded(s_bar, 0)) {  // staged data not known complete: write nothing
+    if (tid == 0) atomicOr(a.status, kDevTimeoutLoad | kDevBadOutput);
+    return;
+  }
+
+  // 2. stable in-warp ranks and per-warp digit counts
+  const uint32_t shift = a.shift, mask = a.mask;
+  uint32_t* wmask0 = s_mask + warp * kRadix;
+  uint32_t* wmask1 = s_mask + (kWarps + warp) * kRadix;
+  uint32_t* wcnt = s_wcnt + warp * kRadix;
+  const int wbase = warp * 32 * kIpt;
+  Item<K> it[kIpt];
+  rank_strip<K, kIpt>(s_keys, tile_n, wbase, shift, mask, wmask0, wmask1, wcnt, it);
+  __syncthreads();
+
+  // 3. per digit: warp prefixes, the tile's exclusive digit prefix, and the
+  // output offset of the digit's run (the tile's table entry minus the run's
+  // start inside the tile, modulo 2^32)
+  {
+    const int d = tid;
+    uint32_t run = 0;
+    if (d < kRadix) {
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = s_wcnt[w * kRadix + d];
+        s_wcnt[w * kRadix + d] = run;
+        run += c;
+      }
+    }
+    const uint32_t ex = digit_excl_scan<kBlock>(run, s_scan);
+    if (d < kRadix) {
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) s_wcnt[w * kRadix + d] += ex;
+      s_off[d] -= ex;
+    }
+  }
+  __syncthreads();
+
+  // 4. permute into digit order in shared memory (the peer-mask words hold
+  // the records: 16-bit keys packed with their source position, wider keys
+  // in place plus a 16-bit source position)
+  uint32_t* s_rec32 = s_mask;
+  uint16_t* s_src16 = reinterpret_cast<uint16_t*>(s_mask);
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    const int pos = wbase + i * 32 + lane;
+    if (uint32_t(pos) < tile_n) {
+      const K k = it[i].k();
+      const uint32_t p = s_wcnt[warp * kRadix + dig(k, shift, mask)] + it[i].r();
+      if (sizeof(K) == 2) {
+        s_rec32[p] = uint32_t(k) | (uint32_t(pos) << 16);
+      } else {
+        s_keys[p] = k;
+        s_src16[p] = uint16_t(pos);
+      }
+    }
+  }
+  __syncthreads();
+
+  // 5. write-out in digit runs, consecutive threads to consecutive addresses
+  K* kout = const_cast<K*>(static_cast<const K*>(pick(a.keys, dst)));
+  uint32_t* vout = const_cast<uint32_t*>(pick(a.vals, dst));
+#pragma unroll 4
+  for (uint32_t s = tid; s < tile_n; s += kBlock) {
+    K k;
+    uint32_t from;
+    if (sizeof(K) == 2) {
+      const uint32_t r = s_rec32[s];
+      k = K(r & 0xFFFFu);
+      from = r >> 16;
+    } else {
+      k = s_keys[s];
+      from = s_src16[s];
+    }
+    const uint32_t o = s_off[dig(k, shift, mask)] + s;
+    kout[o] = k;
+    if (kVals) vout[o] = s_vals[from];
+  }
+}
+
+template <typename K, bool kVals>
+cudaError_t launch_scatter_typed(const TileScatterArgs& a, uint32_t tiles, cudaStream_t stream) {
+  using L = TileSmem<K, kVals>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tile_scatter_kernel<K, kVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(L::kBytes));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tile_scatter_kernel<K, kVals>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  tile_scatter_kernel<K, kVals><<<tiles, L::kBlock, L::kBytes, stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t launch_count_typed(const TileCountArgs& a, int passes, unsigned grid, cudaStream_t stream) {
+  switch (passes) {
+#define FSORT_TILE_COUNT_CASE(P)                                                                \
+  case P: {                                                                                     \
+    static bool attr_set = false;                                                               \
+    if (!attr_set) {                                                                            \
+      const cudaError_t e = cudaFuncSetAttribute(tile_count_kernel<K, P>,                        \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                                 int(count_smem_bytes<K>()));                   \
+      if (e != cudaSuccess) return e;                                                           \
+      attr_set = true;                                                                          \
+    }                                                                                           \
+    tile_count_kernel<K, P><<<grid, kCountThreads, count_smem_bytes<K>(), stream>>>(a);         \
+    break;                                                                                      \
+  }
+    FSORT_TILE_COUNT_CASE(1)
+    FSORT_TILE_COUNT_CASE(2)
+    FSORT_TILE_COUNT_CASE(3)
+    FSORT_TILE_COUNT_CASE(4)
+    FSORT_TILE_COUNT_CASE(5)
+    FSORT_TILE_COUNT_CASE(6)
+    FSORT_TILE_COUNT_CASE(7)
+    FSORT_TILE_COUNT_CASE(8)
+#undef FSORT_TILE_COUNT_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int table_tile_keys_for(int key_bits) {
+  switch (key_bits) {
+    case 16: return TileSmem<uint16_t, true>::kTile;
+    case 32: return TileSmem<uint32_t, true>::kTile;
+    case 64: return TileSmem<uint64_t, true>::kTile;
+    default: return 0;
+  }
+}
+
+TableGeom table_geometry(uint64_t n, int key_bits, int sms) {
+  TableGeom g{};
+  g.tile = uint32_t(table_tile_keys_for(key_bits));
+  if (!g.tile || !n) return g;
+  g.tiles = uint32_t((n + g.tile - 1) / g.tile);
+  const int per_sm = key_bits == 16 ? count_ctas_per_sm<uint16_t>() : count_ctas_per_sm<uint64_t>();
+  const uint32_t want = uint32_t(sms) * uint32_t(per_sm);  // one chunk per resident count CTA
+  g.chunk_tiles = (g.tiles + want - 1) / want;
+  g.chunk_tiles = (g.chunk_tiles + kStepTiles - 1) / kStepTiles * kStepTiles;  // whole steps
+  g.chunks = (g.tiles + g.chunk_tiles - 1) / g.chunk_tiles;
+  return g;
+}
+
+cudaError_t launch_tile_count(const TileCountArgs& a, int key_bits, int passes, uint32_t chunks,
+                              cudaStream_t stream) {
+  if (!chunks) return cudaSuccess;
+  switch (key_bits) {
+    case 16: return launch_count_typed<uint16_t>(a, passes, chunks, stream);
+    case 32: return launch_count_typed<uint32_t>(a, passes, chunks, stream);
+    case 64: return launch_count_typed<uint64_t>(a, passes, chunks, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_chunk_scan(const uint32_t* chunksum, uint32_t chunks, const uint64_t* base, const Schedule* sched,
+                              int pass, uint32_t* chunkoff, cudaStream_t stream) {
+  if (!chunks) return cudaSuccess;
+  chunk_scan_kernel<<<kRadix, kScanThreads, 0, stream>>>(chunksum, base, chunks, sched, pass, chunkoff);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scatter(const TileScatterArgs& a, int key_bits, bool has_vals, cudaStream_t stream) {
+  if (!a.tiles) return cudaSuccess;
+  switch (key_bits) {
+    case 16: return has_vals ? launch_scatter_typed<uint16_t, true>(a, a.tiles, stream)
+                             : launch_scatter_typed<uint16_t, false>(a, a.tiles, stream);
+    case 32: return has_vals ? launch_scatter_typed<uint32_t, true>(a, a.tiles, stream)
+                             : launch_scatter_typed<uint32_t, false>(a, a.tiles, stream);
+    case 64: return has_vals ? launch_scatter_typed<uint64_t, true>(a, a.tiles, stream)
+                             : launch_scatter_typed<uint64_t, false>(a, a.tiles, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fsort

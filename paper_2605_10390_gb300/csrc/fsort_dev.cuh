@@ -15,6 +15,7 @@ constexpr uint32_t kDevBadTile = 4u;          // a dynamic tile id beyond the gr
 constexpr uint32_t kDevBadLookback = 8u;      // a look-back walk reached its chunk's first tile without a prefix
 constexpr uint32_t kDevBadOutput = 16u;       // a tile skipped its output after a failed bounded wait
 constexpr uint32_t kDevBadBucket = 32u;       // a learned-path bucket exceeded the on-chip capacity (judge bypassed)
+constexpr uint32_t kDevBadTable = 64u;        // a tile-offset table is incomplete (a count wait gave up)
 
 // Bounded waits give up after this many nanoseconds of %globaltimer.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;

@@ -79,6 +79,63 @@ struct OnesweepArgs {
 };
 cudaError_t launch_onesweep(const OnesweepArgs& args, int key_bits, bool has_vals, cudaStream_t stream);
 
+// ---- scatter passes over a table of per-tile offsets (fsort_blocks.cu) ----
+// For n < 2^32 keys: `tiles` tiles of `tile` keys, grouped in `chunks` runs of
+// `chunk_tiles` consecutive tiles (one count CTA each; the last may be shorter).
+struct TableGeom {
+  uint32_t tile;
+  uint32_t tiles;
+  uint32_t chunk_tiles;
+  uint32_t chunks;
+};
+int table_tile_keys_for(int key_bits);
+TableGeom table_geometry(uint64_t n, int key_bits, int sms);
+
+// KT1: for the pass of digit 0 of `plan`, per tile the counts of each digit in
+// the earlier tiles of its chunk (tilerel[t][256]) and per chunk the digit
+// totals (chunksum[c][256]); with hist set, every digit of `plan` is also
+// added to hist[j][256].  sched set: the keys are those pass `pass` reads, and
+// an inactive pass counts nothing; else keys[kBufIn].
+struct TileCountArgs {
+  const void* keys[3];
+  uint64_t n;
+  DigitPlan plan;
+  uint32_t tile;
+  uint32_t tiles;
+  uint32_t chunk_tiles;
+  uint32_t pad;
+  uint32_t* tilerel;
+  uint32_t* chunksum;
+  uint64_t* hist;
+  const Schedule* sched;
+  int32_t pass;
+  int32_t pad2;
+  uint32_t* status;  // a failed bounded wait sets kDevBadTable: the scatter then writes nothing
+};
+cudaError_t launch_tile_count(const TileCountArgs& a, int key_bits, int passes, uint32_t chunks,
+                              cudaStream_t stream);
+// KT2: chunkoff[c][d] = base[d] + counts of digit d in chunks before c (32-bit).
+cudaError_t launch_chunk_scan(const uint32_t* chunksum, uint32_t chunks, const uint64_t* base, const Schedule* sched,
+                              int pass, uint32_t* chunkoff, cudaStream_t stream);
+// KT3: one stable scatter pass, one CTA per tile, tile t writing digit d from
+// chunkoff[t / chunk_tiles][d] + tilerel[t][d] on.
+struct TileScatterArgs {
+  const void* keys[3];  // by BufSel: input, plan scratch, output
+  const uint32_t* vals[3];
+  uint64_t n;
+  uint32_t shift;
+  uint32_t mask;
+  uint32_t tiles;
+  uint32_t chunk_tiles;
+  const uint32_t* tilerel;
+  const uint32_t* chunkoff;
+  const Schedule* sched;  // null: always run, input -> output
+  int32_t pass;
+  int32_t pad2;
+  uint32_t* status;
+};
+cudaError_t launch_tile_scatter(const TileScatterArgs& a, int key_bits, bool has_vals, cudaStream_t stream);
+
 // Final copy when the schedule leaves the result in the wrong buffer.
 cudaError_t launch_schedule_copy(const void* const keys[3], const uint32_t* const vals[3], int key_bits,
                                  bool has_vals, uint64_t n, const Schedule* sched, int sms, cudaStream_t stream);

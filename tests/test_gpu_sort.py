@@ -45,10 +45,10 @@ def sizes(kb):
 def plans():
     made = {}
 
-    def get(kb, vals, max_n=1 << 22):
-        key = (kb, vals, max_n)
+    def get(kb, vals, max_n=1 << 22, flags=0):
+        key = (kb, vals, max_n, flags)
         if key not in made:
-            made[key] = fs.Plan(max_n, kb, has_values=vals)
+            made[key] = fs.Plan(max_n, kb, has_values=vals, flags=flags)
         return made[key]
 
     yield get
@@ -141,11 +141,17 @@ def test_expand_matches_oracle(plans, dist):
 PRECISIONS = {16: [16, 13, 9, 8, 3, 1], 32: [32, 21, 16, 9], 64: [64, 40, 32, 16, 1]}
 
 
+# The two forms of the scatter passes: over fixed blocks of tiles (the default
+# below 2^32 keys) and chained by decoupled look-back.
+FORMS = {"blocks": 0, "chained": fs.FSORT_FLAG_CHAINED_SCATTER}
+
+
 @pytest.mark.parametrize("kb", [16, 32, 64])
 @pytest.mark.parametrize("with_vals", [True, False])
 @pytest.mark.parametrize("in_place", [True, False])
-def test_sort_matches_oracle(plans, kb, with_vals, in_place):
-    plan = plans(kb, with_vals)
+@pytest.mark.parametrize("form", list(FORMS))
+def test_sort_matches_oracle(plans, kb, with_vals, in_place, form):
+    plan = plans(kb, with_vals, flags=FORMS[form])
     rng = np.random.default_rng(kb)
     for p in PRECISIONS[kb]:
         for n in sizes(kb):
@@ -169,8 +175,9 @@ def test_sort_matches_oracle(plans, kb, with_vals, in_place):
 
 
 @pytest.mark.parametrize("dist", DISTS)
-def test_every_distribution_kv16(plans, dist):
-    plan = plans(16, True)
+@pytest.mark.parametrize("form", list(FORMS))
+def test_every_distribution_kv16(plans, dist, form):
+    plan = plans(16, True, flags=FORMS[form])
     n = (1 << 21) + 17
     keys = gen(dist, n, 16, stream=11)
     idx = np.arange(n, dtype=np.uint32)
@@ -215,19 +222,22 @@ def test_512mb_workload_full_size(dist):
         assert np.array_equal(host(dk), keys)  # input untouched
 
 
-def test_lookback_chunks_beyond_2pow30():
-    """More keys than one look-back chunk holds (< 2^30): chunk bases carry the
-    counts across chunks.  Keys only, 12-bit precision (radix path)."""
+def test_beyond_2pow30_keys_both_forms():
+    """More keys than one look-back chunk holds (< 2^30): in the chained form
+    the chunk bases carry the counts across chunks; in the block form output
+    positions pass 2^30.  Keys only, 12-bit precision (radix path)."""
     n = (1 << 30) + 4099
     keys = workloads.generate("zipf1.1", n, 16, seed=0, stream=9)
     wk, _ = oracle.sort(keys, None, 16, 12)
-    with fs.Plan(n, 16, has_values=False) as plan:
-        info = plan.describe(n, precision_bits=12)
-        assert info["chunk_keys"] < n
-        dk = dev(keys)
-        plan.sort(dk, None, precision_bits=12)
-        plan.sync()
-        assert np.array_equal(host(dk), wk)
+    for flags in FORMS.values():
+        with fs.Plan(n, 16, has_values=False, flags=flags) as plan:
+            info = plan.describe(n, precision_bits=12)
+            assert info["chunk_keys"] < n
+            dk = dev(keys)
+            plan.sort(dk, None, precision_bits=12)
+            plan.sync()
+            assert np.array_equal(host(dk), wk)
+            del dk
 
 
 def test_empty_input_and_describe(plans):
