@@ -217,15 +217,33 @@ struct TileSmem {
   static constexpr int kIpt = TileShape<K>::kIpt;
   static constexpr int kTile = kBlock * kIpt;
   static constexpr int kWarps = kBlock / 32;
-  static constexpr size_t kKeys = 0;
+  static constexpr size_t kKeys = 0;  // the staged keys, then the keys in digit order
   static constexpr size_t kVals_ = kKeys + size_t(kTile) * sizeof(K);
-  static constexpr size_t kMask = kVals_ + (kVals ? size_t(kTile) * 4 : 0);
-  static constexpr size_t kMaskWords = 2 * size_t(kWarps) * kRadix;  // peer masks, double-buffered
+  static constexpr size_t kSrc = kVals_ + (kVals ? size_t(kTile) * 4 : 0);  // source slot of each ordered key
+  static constexpr size_t kMask = kSrc + size_t(kTile) * 2;
+  static constexpr size_t kMaskWords = size_t(kWarps) * kRadix;  // peer masks
   static constexpr size_t kWcnt = kMask + kMaskWords * 4;
   static constexpr size_t kOff = kWcnt + size_t(kWarps) * kRadix * 4;
   static constexpr size_t kScan = kOff + kRadix * 4;
   static constexpr size_t kBar = kScan + 16 * 4;
   static constexpr size_t kBytes = kBar + 16;
+};
+
+// kIpt keys of one thread in registers; 16-bit keys two to a word.
+template <typename K, int kIpt>
+struct KeyRegs {
+  K k[kIpt];
+  __device__ __forceinline__ void set(int i, K v) { k[i] = v; }
+  __device__ __forceinline__ K get(int i) const { return k[i]; }
+};
+template <int kIpt>
+struct KeyRegs<uint16_t, kIpt> {
+  uint32_t w[(kIpt + 1) / 2];
+  __device__ __forceinline__ void set(int i, uint16_t v) {
+    if (i & 1) w[i >> 1] |= uint32_t(v) << 16;
+    else w[i >> 1] = v;
+  }
+  __device__ __forceinline__ uint16_t get(int i) const { return uint16_t((i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu)); }
 };
 
 // Buffer `sel` of a by-BufSel triple, selected without indexing the
@@ -244,7 +262,6 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   constexpr int kTile = L::kTile;
   constexpr int kWarps = L::kWarps;
   static_assert(kTile <= 65536, "in-warp ranks and source positions are kept in 16 bits");
-  static_assert(L::kMaskWords * 4 >= size_t(kTile) * (sizeof(K) == 2 ? 4 : 2), "records fit the mask words");
   static_assert(L::kMask % 16 == 0, "16-byte clears");
   extern __shared__ __align__(1024) unsigned char smem[];
   K* s_keys = reinterpret_cast<K*>(smem + L::kKeys);
@@ -296,18 +313,26 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
     return;
   }
 
-  // 2. stable in-warp ranks and per-warp digit counts
+  // 2. each warp counts the digits of its strip (item i of lane l is the key
+  // at wbase + i*32 + l); the keys stay in registers
   const uint32_t shift = a.shift, mask = a.mask;
-  uint32_t* wmask0 = s_mask + warp * kRadix;
-  uint32_t* wmask1 = s_mask + (kWarps + warp) * kRadix;
+  uint32_t* wmask = s_mask + warp * kRadix;
   uint32_t* wcnt = s_wcnt + warp * kRadix;
   const int wbase = warp * 32 * kIpt;
-  Item<K> it[kIpt];
-  rank_strip<K, kIpt>(s_keys, tile_n, wbase, shift, mask, wmask0, wmask1, wcnt, it);
+  KeyRegs<K, kIpt> kr;
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    const int pos = wbase + i * 32 + lane;
+    const bool valid = uint32_t(pos) < tile_n;
+    const K k = valid ? s_keys[pos] : K(0);
+    kr.set(i, k);
+    if (valid) atomicAdd(&wcnt[dig(k, shift, mask)], 1u);
+  }
   __syncthreads();
 
-  // 3. per digit: warp prefixes, the tile's exclusive digit prefix, and the
-  // output offset of the digit's run (the tile's table entry minus the run's
+  // 3. per digit: each warp's first position of the digit in the tile's
+  // digit order (warp prefixes on top of the tile's exclusive digit prefix),
+  // and the output offset of the digit's run (the table entry minus the run's
   // start inside the tile, modulo 2^32)
   {
     const int d = tid;
@@ -329,23 +354,52 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   }
   __syncthreads();
 
-  // 4. permute into digit order in shared memory (the peer-mask words hold
-  // the records: 16-bit keys packed with their source position, wider keys
-  // in place plus a 16-bit source position)
-  uint32_t* s_rec32 = s_mask;
-  uint16_t* s_src16 = reinterpret_cast<uint16_t*>(s_mask);
+  // 4. stable ranks, straight to the key's slot in digit order: per round of
+  // 32 keys each lane adds its lane bit to the warp's word of its digit (the
+  // word is then the lane's peer mask, as __match_any_sync would give); the
+  // lowest peer takes the group's slots from the warp's running position of
+  // the digit.  Locally skewed strips (presorted runs, constant digits) use
+  // the hardware match.any instead, which is fast when a round has few
+  // distinct digits (the choice changes speed only).
+  {
+    const uint32_t lt = lanemask_lt(), me = 1u << lane;
+    bool use_match;
+    {
+      const uint32_t d0 = uint32_t(wbase + lane) < tile_n ? dig(kr.get(0), shift, mask) : 0xFFFFFFFFu;
+      use_match = __popc(__ballot_sync(0xffffffffu, d0 == __shfl_sync(0xffffffffu, d0, 0))) >= 16;
+    }
+    uint16_t* s_src = reinterpret_cast<uint16_t*>(smem + L::kSrc);
 #pragma unroll
-  for (int i = 0; i < kIpt; ++i) {
-    const int pos = wbase + i * 32 + lane;
-    if (uint32_t(pos) < tile_n) {
-      const K k = it[i].k();
-      const uint32_t p = s_wcnt[warp * kRadix + dig(k, shift, mask)] + it[i].r();
-      if (sizeof(K) == 2) {
-        s_rec32[p] = uint32_t(k) | (uint32_t(pos) << 16);
+    for (int i = 0; i < kIpt; ++i) {
+      const int pos = wbase + i * 32 + lane;
+      const bool valid = uint32_t(pos) < tile_n;
+      const K k = kr.get(i);
+      const uint32_t d = dig(k, shift, mask);
+      uint32_t peers;
+      if (use_match) {
+        peers = __match_any_sync(0xffffffffu, valid ? d : (0x100u + lane));  // invalid lanes match nobody
+        if (!valid) peers = 0;
       } else {
-        s_keys[p] = k;
-        s_src16[p] = uint16_t(pos);
+        if (valid) atomicAdd(&wmask[d], me);
+        __syncwarp();
+        peers = valid ? wmask[d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wmask[d] = 0;  // the word is zero again before the next round
+        __syncwarp();
       }
+      const uint32_t below = __popc(peers & lt);
+      uint32_t base = 0;
+      if (valid && below == 0) {  // the group's leader; no other lane touches this digit's counter now
+        base = wcnt[d];
+        wcnt[d] = base + uint32_t(__popc(peers));
+      }
+      base = __shfl_sync(0xffffffffu, base, valid ? (__ffs(peers) - 1) : lane);
+      if (valid) {
+        const uint32_t p = base + below;
+        s_keys[p] = k;
+        if (kVals) s_src[p] = uint16_t(pos);
+      }
+      __syncwarp();  // the leader's counter update is seen by the next round's leader
     }
   }
   __syncthreads();
@@ -353,21 +407,13 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   // 5. write-out in digit runs, consecutive threads to consecutive addresses
   K* kout = const_cast<K*>(static_cast<const K*>(pick(a.keys, dst)));
   uint32_t* vout = const_cast<uint32_t*>(pick(a.vals, dst));
+  const uint16_t* s_src = reinterpret_cast<const uint16_t*>(smem + L::kSrc);
 #pragma unroll 4
   for (uint32_t s = tid; s < tile_n; s += kBlock) {
-    K k;
-    uint32_t from;
-    if (sizeof(K) == 2) {
-      const uint32_t r = s_rec32[s];
-      k = K(r & 0xFFFFu);
-      from = r >> 16;
-    } else {
-      k = s_keys[s];
-      from = s_src16[s];
-    }
+    const K k = s_keys[s];
     const uint32_t o = s_off[dig(k, shift, mask)] + s;
     kout[o] = k;
-    if (kVals) vout[o] = s_vals[from];
+    if (kVals) vout[o] = s_vals[s_src[s]];
   }
 }
 
