@@ -45,7 +45,7 @@ WORKLOAD = ("512 MB: 2^28 uint16 keys + uint32 index values, stable, 16-bit prec
             "5 distributions per step (uniform, zipf s=1.1, gauss mu=32768 sigma=1024, 90% presorted, all-equal)")
 METRIC = "Gkeys/s (16-bit keys + 32-bit values, 512 MB per sort, 5 distributions)"
 SCATTER_SRC = [os.path.join(ROOT, "paper_2605_10390_gb300", "csrc", f)
-               for f in ("fsort_onesweep.cu", "fsort_dev.cuh", "fsort_rank.cuh")]
+               for f in ("fsort_blocks.cu", "fsort_dev.cuh", "fsort_rank.cuh")]
 
 
 def parse_args():
@@ -609,7 +609,7 @@ def main():
                        "values": "uint32 original index", "sorts_per_step": len(DISTS), "digit_bits": info["digit_bits"],
                        "tile_keys": info["tile_keys"], "l2": "inputs larger than L2 (1.5 GiB per sort), no flush",
                        "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "onesweep scatter pass (K3)", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "table scatter pass (KT3, tile_scatter_kernel)", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "algorithmic_bytes_per_launch": per_launch, "launches": len(sc),
                          "avg_launch_ms": sc_ms / len(sc) if sc else None, "peak_source": peak_src,

@@ -72,7 +72,7 @@ typedef enum fsort_status {
 #define FSORT_FLAG_GRAPH 0x2u   /* batched sorts replay a captured CUDA graph when the batch shape repeats */
 #define FSORT_FLAG_LEARNED 0x8u /* allocate the learned bucket mapping (64-bit keys only); see fsort_learned_fit */
 #define FSORT_FLAG_CHAINED_SCATTER 0x10u /* every scatter pass in the chained (decoupled look-back) form; by
-                                            default sorts of n < 2^32 keys read their tiles' digit offsets from
+                                            default sorts of n <= 2^32 keys read their tiles' digit offsets from
                                             a table of per-tile counts made before each pass */
 
 typedef struct fsort_plan fsort_plan;

@@ -284,7 +284,7 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
   const DigitPlan plan = make_plan(key_bits, precision_bits, p->digit_bits);
   const void* kb[3] = {keys_in, p->alt_keys, keys_out};
   const uint32_t* vb[3] = {vals_in, p->alt_vals, vals_out};
-  if (!p->chained && n < (1ull << 32)) {
+  if (!p->chained && n <= (1ull << 32)) {  // output positions fit 32 bits (offsets are exact modulo 2^32)
     // Scatter passes over a table of per-tile offsets: one read of the input
     // for every pass's histogram and the first pass's table; before each later
     // pass, one read of its input for its table.
@@ -739,7 +739,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   const uint64_t n = desc->max_n;
   p->chained = (desc->flags & FSORT_FLAG_CHAINED_SCATTER) != 0;
   if (!p->chained) {
-    const uint64_t tn = n < (1ull << 32) ? n : (1ull << 32) - 1;
+    const uint64_t tn = n < (1ull << 32) ? n : (1ull << 32);
     const uint64_t tt = uint64_t(table_tile_keys_for(desc->key_bits));
     p->table_tiles = (tn + tt - 1) / tt;
     p->table_chunks = uint32_t(p->sms) * 2;

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kScanThreads) chunk_scan_kernel(const uint32_t
   if (sched && !sched->pass[pass].active) return;
   __shared__ uint32_t s_warp[32];
   const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t running = uint32_t(base[d]);  // positions are below 2^32 on this path
+  uint32_t running = uint32_t(base[d]);  // n <= 2^32: every position is exact modulo 2^32
   for (uint32_t c0 = 0; c0 < chunks; c0 += kScanThreads) {
     const uint32_t c = c0 + threadIdx.x;
     const uint32_t x = c < chunks ? sum[uint64_t(c) * kRadix + d] : 0u;

@@ -80,7 +80,7 @@ struct OnesweepArgs {
 cudaError_t launch_onesweep(const OnesweepArgs& args, int key_bits, bool has_vals, cudaStream_t stream);
 
 // ---- scatter passes over a table of per-tile offsets (fsort_blocks.cu) ----
-// For n < 2^32 keys: `tiles` tiles of `tile` keys, grouped in `chunks` runs of
+// For n <= 2^32 keys: `tiles` tiles of `tile` keys, grouped in `chunks` runs of
 // `chunk_tiles` consecutive tiles (one count CTA each; the last may be shorter).
 struct TableGeom {
   uint32_t tile;
