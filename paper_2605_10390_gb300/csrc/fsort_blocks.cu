@@ -217,10 +217,13 @@ struct TileSmem {
   static constexpr int kIpt = TileShape<K>::kIpt;
   static constexpr int kTile = kBlock * kIpt;
   static constexpr int kWarps = kBlock / 32;
-  static constexpr size_t kKeys = 0;  // the staged keys, then the keys in digit order
-  static constexpr size_t kVals_ = kKeys + size_t(kTile) * sizeof(K);
-  static constexpr size_t kSrc = kVals_ + (kVals ? size_t(kTile) * 4 : 0);  // source slot of each ordered key
-  static constexpr size_t kMask = kSrc + size_t(kTile) * 2;
+  // The staged keys, then (16-bit keys) records key | source slot << 16 over
+  // the keys and source areas together, or (wider keys) the keys in digit
+  // order plus their 16-bit source slots.
+  static constexpr size_t kKeys = 0;
+  static constexpr size_t kSrc = kKeys + size_t(kTile) * sizeof(K);
+  static constexpr size_t kVals_ = kSrc + size_t(kTile) * 2;
+  static constexpr size_t kMask = kVals_ + (kVals ? size_t(kTile) * 4 : 0);
   static constexpr size_t kMaskWords = size_t(kWarps) * kRadix;  // peer masks
   static constexpr size_t kWcnt = kMask + kMaskWords * 4;
   static constexpr size_t kOff = kWcnt + size_t(kWarps) * kRadix * 4;
@@ -368,6 +371,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
       const uint32_t d0 = uint32_t(wbase + lane) < tile_n ? dig(kr.get(0), shift, mask) : 0xFFFFFFFFu;
       use_match = __popc(__ballot_sync(0xffffffffu, d0 == __shfl_sync(0xffffffffu, d0, 0))) >= 16;
     }
+    uint32_t* s_rec32 = reinterpret_cast<uint32_t*>(smem + L::kKeys);
     uint16_t* s_src = reinterpret_cast<uint16_t*>(smem + L::kSrc);
 #pragma unroll
     for (int i = 0; i < kIpt; ++i) {
@@ -389,17 +393,17 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
       }
       const uint32_t below = __popc(peers & lt);
       uint32_t base = 0;
-      if (valid && below == 0) {  // the group's leader; no other lane touches this digit's counter now
-        base = wcnt[d];
-        wcnt[d] = base + uint32_t(__popc(peers));
-      }
+      if (valid && below == 0) base = atomicAdd(&wcnt[d], uint32_t(__popc(peers)));  // the group's leader
       base = __shfl_sync(0xffffffffu, base, valid ? (__ffs(peers) - 1) : lane);
       if (valid) {
         const uint32_t p = base + below;
-        s_keys[p] = k;
-        if (kVals) s_src[p] = uint16_t(pos);
+        if (sizeof(K) == 2) {
+          s_rec32[p] = uint32_t(k) | (uint32_t(pos) << 16);
+        } else {
+          s_keys[p] = k;
+          if (kVals) s_src[p] = uint16_t(pos);
+        }
       }
-      __syncwarp();  // the leader's counter update is seen by the next round's leader
     }
   }
   __syncthreads();
@@ -407,13 +411,23 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   // 5. write-out in digit runs, consecutive threads to consecutive addresses
   K* kout = const_cast<K*>(static_cast<const K*>(pick(a.keys, dst)));
   uint32_t* vout = const_cast<uint32_t*>(pick(a.vals, dst));
+  const uint32_t* s_rec32 = reinterpret_cast<const uint32_t*>(smem + L::kKeys);
   const uint16_t* s_src = reinterpret_cast<const uint16_t*>(smem + L::kSrc);
 #pragma unroll 4
   for (uint32_t s = tid; s < tile_n; s += kBlock) {
-    const K k = s_keys[s];
+    K k;
+    uint32_t from = 0;
+    if (sizeof(K) == 2) {
+      const uint32_t r = s_rec32[s];
+      k = K(r & 0xFFFFu);
+      from = r >> 16;
+    } else {
+      k = s_keys[s];
+      if (kVals) from = s_src[s];
+    }
     const uint32_t o = s_off[dig(k, shift, mask)] + s;
     kout[o] = k;
-    if (kVals) vout[o] = s_vals[s_src[s]];
+    if (kVals) vout[o] = s_vals[from];
   }
 }
 
