@@ -149,7 +149,7 @@ def run_e2e(fs, workloads, torch, n, rank, world, dist, kb, vb, steps):
     # two output sets: step k writes set k % 2 once step k - 2's sorts are done
     outs = [[(torch.empty(n, dtype=torch.uint16).pin_memory(), torch.empty(n, dtype=torch.uint32).pin_memory())
              for _ in DISTS] for _ in range(2)]
-    lanes = 3
+    lanes = 2  # measured best: three lanes contend for the host link and ran slower
     budget = lanes * n * (kb + vb) + (64 << 20)
     with fs.Server(n, KEY_BITS, True, lanes=lanes, hbm_budget_bytes=budget, batch_keys=1 << 16) as srv:
         def run(nsteps):
