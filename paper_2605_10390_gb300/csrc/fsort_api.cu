@@ -97,6 +97,8 @@ struct fsort_plan {
   uint32_t* tilerel = nullptr;   // [table_tiles][256] per-tile digit offsets within the tile's chunk
   uint32_t* chunksum = nullptr;  // [table_chunks][256] per-chunk digit totals
   uint32_t* chunkoff = nullptr;  // [table_chunks][256] per-chunk digit output offsets
+  uint64_t* orand = nullptr;     // [2] OR and AND of the keys of one sort (0 and all ones between calls)
+  uint32_t* totals = nullptr;    // [2][256] digit totals of a pass (by pass parity; zero between uses)
   bool chained = false;          // FSORT_FLAG_CHAINED_SCATTER: always the look-back scatter
   uint32_t* leaf_part = nullptr; // expand path (16-bit keys)
   uint64_t* leaf_spill = nullptr;
@@ -292,33 +294,36 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
     TileCountArgs ca{};
     for (int b = 0; b < 3; ++b) ca.keys[b] = kb[b];
     ca.n = n;
-    ca.plan = plan;
+    ca.shift = plan.shift[0];
+    ca.mask = plan.mask[0];
     ca.tile = g.tile;
     ca.tiles = g.tiles;
     ca.chunk_tiles = g.chunk_tiles;
     ca.tilerel = p->tilerel;
     ca.chunksum = p->chunksum;
-    ca.hist = p->hist;
+    ca.totals = p->totals;
+    ca.orand = p->orand;
     ca.status = p->status;
-    e = launch_tile_count(ca, key_bits, plan.passes, g.chunks, s);
+    // totals left dirty by an interrupted call would misplace every key: clear them
+    e = cudaMemsetAsync(p->totals, 0, 2 * kRadix * 4, s);
+    if (e == cudaSuccess) e = launch_tile_count(ca, key_bits, g.chunks, s);
     tm.mark(FSORT_KERNEL_HISTOGRAM, -1);
-    if (e == cudaSuccess)
-      e = launch_scan_schedule(p->hist, p->chunk_base, p->chunk_flag, plan.passes, 1, in_place ? 1 : 0, p->sched, s);
+    if (e == cudaSuccess) e = launch_table_schedule(p->orand, plan, in_place ? 1 : 0, p->sched, s);
     tm.mark(FSORT_KERNEL_SCAN, -1);
     for (int j = 0; j < plan.passes && e == cudaSuccess; ++j) {
       if (j > 0) {
         TileCountArgs cj = ca;
-        cj.plan.passes = 1;
-        cj.plan.shift[0] = plan.shift[j];
-        cj.plan.mask[0] = plan.mask[j];
-        cj.hist = nullptr;
+        cj.shift = plan.shift[j];
+        cj.mask = plan.mask[j];
+        cj.orand = nullptr;
+        cj.totals = p->totals + (j & 1) * kRadix;
         cj.sched = p->sched;
         cj.pass = j;
-        e = launch_tile_count(cj, key_bits, 1, g.chunks, s);
+        e = launch_tile_count(cj, key_bits, g.chunks, s);
         tm.mark(FSORT_KERNEL_TILE_COUNT, j);
       }
       if (e == cudaSuccess)
-        e = launch_chunk_scan(p->chunksum, g.chunks, p->chunk_base + uint64_t(j) * kRadix, p->sched, j, p->chunkoff, s);
+        e = launch_chunk_scan(p->chunksum, p->totals + (j & 1) * kRadix, g.chunks, p->sched, j, p->chunkoff, s);
       tm.mark(FSORT_KERNEL_TILE_SCAN, j);
       TileScatterArgs a{};
       for (int b = 0; b < 3; ++b) {
@@ -332,6 +337,7 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
       a.chunk_tiles = g.chunk_tiles;
       a.tilerel = p->tilerel;
       a.chunkoff = p->chunkoff;
+      a.totals = p->totals + (j & 1) * kRadix;
       a.sched = p->sched;
       a.pass = j;
       a.status = p->status;
@@ -773,6 +779,8 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   const size_t o_trel = take(size_t(p->table_tiles) * kRadix * 4);
   const size_t o_csum = take(size_t(p->table_chunks) * kRadix * 4);
   const size_t o_coff = take(size_t(p->table_chunks) * kRadix * 4);
+  const size_t o_orand = take(2 * sizeof(uint64_t));
+  const size_t o_totals = take(2 * kRadix * 4);
   size_t o_lpart = 0, o_lspill = 0, o_lcnt = 0, o_loff = 0;
   const bool batch = desc->max_segments > 0;
   if (desc->max_segments > 65535) {
@@ -868,6 +876,8 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   p->tilerel = reinterpret_cast<uint32_t*>(w + o_trel);
   p->chunksum = reinterpret_cast<uint32_t*>(w + o_csum);
   p->chunkoff = reinterpret_cast<uint32_t*>(w + o_coff);
+  p->orand = reinterpret_cast<uint64_t*>(w + o_orand);
+  p->totals = reinterpret_cast<uint32_t*>(w + o_totals);
   if (batch) {
     p->d_seg_large = reinterpret_cast<SegDesc*>(w + o_bsl);
     p->d_seg_small = reinterpret_cast<SegDesc*>(w + o_bss);
@@ -934,6 +944,9 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   }
   // Zero what must start at zero: histogram accumulators, status, counters.
   e = cudaMemset(p->hist, 0, hist_bytes);
+  if (e == cudaSuccess) e = cudaMemset(p->orand, 0, sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMemset(p->orand + 1, 0xFF, sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMemset(p->totals, 0, 2 * kRadix * 4);
   if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(p->counters, 0, kCounterBytes);
   if (e == cudaSuccess && batch) e = cudaMemset(p->d_bhist, 0, size_t(desc->max_segments) * pmax * kRadix * 8);

@@ -47,13 +47,16 @@ template <>
 struct TileShape<uint64_t> { static constexpr int kBlock = 512, kIpt = 8, kMinBlocks = 2; };
 
 // ------------------------------------------------------------------ KT1 ----
-// P = digits counted per key (compile time).  Digit 0 of `plan` is the pass
-// whose table is written: CTA c walks the tiles of chunk c in order and writes
-// for each tile the counts of its digits in the chunk's earlier tiles
-// (tilerel[t][256]), then the chunk's totals (chunksum[c][256]).  With `hist`
-// set, all P digits are also added to the global 64-bit histogram hist[j][256].
-// The chunk streams through kCountStages shared-memory buffers of kStepTiles
-// tiles each, filled by bulk copies while earlier steps are counted.
+// One digit (shift, mask) per launch.  CTA c walks the tiles of chunk c in
+// order and writes for each tile the counts of its digits in the chunk's
+// earlier tiles (tilerel[t][256]), then the chunk's totals (chunksum[c][256])
+// and adds them to the pass's digit totals (totals[256], zero on entry).
+// kOrAnd (the first read of the input) also folds every key into
+// orand[0] |= k and orand[1] &= k: a pass is trivial (all keys share its
+// digit) exactly when the two agree on the digit's bits, so the schedule needs
+// no histogram of the other passes.  The chunk streams through kCountStages
+// shared-memory buffers of kStepTiles tiles each, filled by bulk copies while
+// earlier steps are counted.
 constexpr int kStepTiles = 2;
 constexpr int kCountStages = 3;
 
@@ -70,11 +73,10 @@ __host__ __device__ constexpr size_t count_smem_bytes() {
   return size_t(kCountStages) * count_step_keys<K>() * sizeof(K);
 }
 
-template <typename K, int P>
+template <typename K, bool kOrAnd>
 __global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_count_kernel(TileCountArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];  // [kCountStages][step keys]
-  __shared__ uint32_t s_tile[kStepTiles][kRadix];             // digit 0, the step's tiles
-  __shared__ uint32_t s_rest[(P > 1 ? P - 1 : 1) * kRadix];  // digits 1.., whole CTA
+  __shared__ uint32_t s_tile[kStepTiles][kRadix];  // the step's tiles
   __shared__ uint64_t s_bar[kCountStages];
   __shared__ uint32_t s_fail;
   constexpr uint32_t kStepKeys = count_step_keys<K>();
@@ -114,21 +116,18 @@ __global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_co
     for (uint32_t st = 0; st < steps && st < uint32_t(kCountStages); ++st) issue(st);
   }
   for (int i = tid; i < kStepTiles * kRadix; i += kCountThreads) (&s_tile[0][0])[i] = 0;
-  for (int i = tid; i < (P - 1) * kRadix; i += kCountThreads) s_rest[i] = 0;
   __syncthreads();
 
-  uint32_t shift[P], mask[P];
-#pragma unroll
-  for (int j = 0; j < P; ++j) {
-    shift[j] = a.plan.shift[j];
-    mask[j] = a.plan.mask[j];
-  }
+  const uint32_t shift = a.shift, mask = a.mask;
+  uint64_t k_or = 0, k_and = ~0ull;  // this thread's keys folded
   auto count_key = [&](K k, uint32_t slot) {
-    atomicAdd(&s_tile[slot][dig(k, shift[0], mask[0])], 1u);
-#pragma unroll
-    for (int j = 1; j < P; ++j) atomicAdd(&s_rest[(j - 1) * kRadix + dig(k, shift[j], mask[j])], 1u);
+    atomicAdd(&s_tile[slot][dig(k, shift, mask)], 1u);
+    if (kOrAnd) {
+      k_or |= uint64_t(k);
+      k_and &= uint64_t(k);
+    }
   };
-  uint32_t acc = 0;  // thread d < 256: digit d of pass 0 in the chunk's tiles so far
+  uint32_t acc = 0;  // thread d < 256: digit d in the chunk's tiles so far
   for (uint32_t st = 0; st < steps; ++st) {
     uint64_t e0, e1;
     step_range(st, e0, e1);
@@ -165,27 +164,57 @@ __global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_co
     }
     __syncthreads();
   }
-  if (tid < kRadix) a.chunksum[uint64_t(blockIdx.x) * kRadix + tid] = acc;
-  if (a.hist) {
-    if (tid < kRadix && acc) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hist[tid]), (unsigned long long)acc);
-    for (int i = tid; i < (P - 1) * kRadix; i += kCountThreads) {
-      const uint32_t c = s_rest[i];
-      if (c) atomicAdd(reinterpret_cast<unsigned long long*>(&a.hist[kRadix + i]), (unsigned long long)c);
+  if (tid < kRadix) {
+    a.chunksum[uint64_t(blockIdx.x) * kRadix + tid] = acc;
+    if (acc) atomicAdd(&a.totals[tid], acc);
+  }
+  if (kOrAnd) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      k_or |= __shfl_xor_sync(0xffffffffu, k_or, o);
+      k_and &= __shfl_xor_sync(0xffffffffu, k_and, o);
+    }
+    if ((tid & 31) == 0) {
+      atomicOr(reinterpret_cast<unsigned long long*>(&a.orand[0]), (unsigned long long)k_or);
+      atomicAnd(reinterpret_cast<unsigned long long*>(&a.orand[1]), (unsigned long long)k_and);
     }
   }
 }
 
 // ------------------------------------------------------------------ KT2 ----
-// One CTA per digit d: chunkoff[c][d] = base[d] + sum over c' < c of
-// chunksum[c'][d] (Alg. 3's rank of every leaf, split over chunks; 32-bit).
+// The schedule from the keys' OR and AND (one thread): pass j is trivial when
+// no bit of its digit differs between keys; then the buffer routing.  Leaves
+// the accumulators at OR = 0, AND = all ones for the next call.
+__global__ void table_schedule_kernel(uint64_t* __restrict__ orand, DigitPlan plan, int in_place, Schedule* sched) {
+  const uint64_t diff = orand[0] ^ orand[1];
+  int trivial[kMaxPasses];
+  for (int j = 0; j < kMaxPasses; ++j)
+    trivial[j] = j < plan.passes ? (((diff >> plan.shift[j]) & uint64_t(plan.mask[j])) == 0) : 1;
+  route_passes(trivial, plan.passes, in_place, sched);
+  orand[0] = 0;
+  orand[1] = ~0ull;
+}
+
+// One CTA per digit d: chunkoff[c][d] = (keys of digits below d, from the
+// pass's totals) + (keys of digit d in chunks before c) (Alg. 3's rank of
+// every leaf, split over chunks; 32-bit, exact modulo 2^32).
 __global__ void __launch_bounds__(kScanThreads) chunk_scan_kernel(const uint32_t* __restrict__ sum,
-                                                                  const uint64_t* __restrict__ base,
+                                                                  const uint32_t* __restrict__ totals,
                                                                   uint32_t chunks, const Schedule* sched,
                                                                   int32_t pass, uint32_t* __restrict__ off) {
   if (sched && !sched->pass[pass].active) return;
   __shared__ uint32_t s_warp[32];
   const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t running = uint32_t(base[d]);  // n <= 2^32: every position is exact modulo 2^32
+  // keys of the digits below d
+  uint32_t below = threadIdx.x < uint32_t(d) ? totals[threadIdx.x] : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
+  if (lane == 0) s_warp[warp] = below;
+  __syncthreads();
+  uint32_t running = 0;
+#pragma unroll
+  for (int w = 0; w < kRadix / 32; ++w) running += s_warp[w];
+  __syncthreads();
   for (uint32_t c0 = 0; c0 < chunks; c0 += kScanThreads) {
     const uint32_t c = c0 + threadIdx.x;
     const uint32_t x = c < chunks ? sum[uint64_t(c) * kRadix + d] : 0u;
@@ -276,6 +305,8 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + L::kBar);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
+  // the chunk scan of this pass has read the totals: leave them zero for the next count
+  if (blockIdx.x == 0 && tid < kRadix && a.totals) a.totals[tid] = 0;
   int src = kBufIn, dst = kBufOut;
   if (a.sched) {
     const PassDesc pd = a.sched->pass[a.pass];
@@ -447,35 +478,23 @@ cudaError_t launch_scatter_typed(const TileScatterArgs& a, uint32_t tiles, cudaS
   return cudaGetLastError();
 }
 
-template <typename K>
-cudaError_t launch_count_typed(const TileCountArgs& a, int passes, unsigned grid, cudaStream_t stream) {
-  switch (passes) {
-#define FSORT_TILE_COUNT_CASE(P)                                                                \
-  case P: {                                                                                     \
-    static bool attr_set = false;                                                               \
-    if (!attr_set) {                                                                            \
-      const cudaError_t e = cudaFuncSetAttribute(tile_count_kernel<K, P>,                        \
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                                 int(count_smem_bytes<K>()));                   \
-      if (e != cudaSuccess) return e;                                                           \
-      attr_set = true;                                                                          \
-    }                                                                                           \
-    tile_count_kernel<K, P><<<grid, kCountThreads, count_smem_bytes<K>(), stream>>>(a);         \
-    break;                                                                                      \
+template <typename K, bool kOrAnd>
+cudaError_t launch_count_variant(const TileCountArgs& a, uint32_t grid, cudaStream_t stream) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(tile_count_kernel<K, kOrAnd>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(count_smem_bytes<K>()));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
   }
-    FSORT_TILE_COUNT_CASE(1)
-    FSORT_TILE_COUNT_CASE(2)
-    FSORT_TILE_COUNT_CASE(3)
-    FSORT_TILE_COUNT_CASE(4)
-    FSORT_TILE_COUNT_CASE(5)
-    FSORT_TILE_COUNT_CASE(6)
-    FSORT_TILE_COUNT_CASE(7)
-    FSORT_TILE_COUNT_CASE(8)
-#undef FSORT_TILE_COUNT_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
+  tile_count_kernel<K, kOrAnd><<<grid, kCountThreads, count_smem_bytes<K>(), stream>>>(a);
   return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t launch_count_typed(const TileCountArgs& a, uint32_t grid, cudaStream_t stream) {
+  return a.orand ? launch_count_variant<K, true>(a, grid, stream) : launch_count_variant<K, false>(a, grid, stream);
 }
 
 }  // namespace
@@ -502,21 +521,26 @@ TableGeom table_geometry(uint64_t n, int key_bits, int sms) {
   return g;
 }
 
-cudaError_t launch_tile_count(const TileCountArgs& a, int key_bits, int passes, uint32_t chunks,
-                              cudaStream_t stream) {
+cudaError_t launch_tile_count(const TileCountArgs& a, int key_bits, uint32_t chunks, cudaStream_t stream) {
   if (!chunks) return cudaSuccess;
   switch (key_bits) {
-    case 16: return launch_count_typed<uint16_t>(a, passes, chunks, stream);
-    case 32: return launch_count_typed<uint32_t>(a, passes, chunks, stream);
-    case 64: return launch_count_typed<uint64_t>(a, passes, chunks, stream);
+    case 16: return launch_count_typed<uint16_t>(a, chunks, stream);
+    case 32: return launch_count_typed<uint32_t>(a, chunks, stream);
+    case 64: return launch_count_typed<uint64_t>(a, chunks, stream);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_chunk_scan(const uint32_t* chunksum, uint32_t chunks, const uint64_t* base, const Schedule* sched,
-                              int pass, uint32_t* chunkoff, cudaStream_t stream) {
+cudaError_t launch_table_schedule(uint64_t* orand, const DigitPlan& plan, int in_place, Schedule* sched,
+                                  cudaStream_t stream) {
+  table_schedule_kernel<<<1, 1, 0, stream>>>(orand, plan, in_place, sched);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_scan(const uint32_t* chunksum, const uint32_t* totals, uint32_t chunks,
+                              const Schedule* sched, int pass, uint32_t* chunkoff, cudaStream_t stream) {
   if (!chunks) return cudaSuccess;
-  chunk_scan_kernel<<<kRadix, kScanThreads, 0, stream>>>(chunksum, base, chunks, sched, pass, chunkoff);
+  chunk_scan_kernel<<<kRadix, kScanThreads, 0, stream>>>(chunksum, totals, chunks, sched, pass, chunkoff);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,38 @@ struct Schedule {
   int32_t pad[3];
 };
 
+// Route the active passes through the input, scratch and output buffers so
+// that the last one writes the result where it belongs, adding a final copy
+// only when no assignment can (one thread).  Buffer sequence b_0 = input,
+// ..., b_k = the buffer holding the result (k active passes).  In place
+// (input == output): alternate scratch/input; odd k ends in the scratch buffer
+// and needs the copy back.  Out of place: count backwards from the output so
+// the last active pass writes it; k == 0 copies.
+__device__ inline void route_passes(const int* trivial, int passes, int in_place, Schedule* sched) {
+  int k = 0;
+  for (int j = 0; j < passes; ++j) k += trivial[j] ? 0 : 1;
+  int cur = kBufIn, idx = 0;
+  for (int j = 0; j < kMaxPasses; ++j) {
+    PassDesc pd{0, kBufIn, kBufIn, 0};
+    if (j < passes && !trivial[j]) {
+      ++idx;
+      int nxt;
+      if (in_place) nxt = (idx & 1) ? kBufAlt : kBufIn;
+      else nxt = ((k - idx) & 1) ? kBufAlt : kBufOut;
+      pd.active = 1;
+      pd.src = cur;
+      pd.dst = nxt;
+      cur = nxt;
+    }
+    sched->pass[j] = pd;
+  }
+  PassDesc cp{0, cur, in_place ? kBufIn : kBufOut, 0};
+  if (in_place) cp.active = (cur != kBufIn);
+  else cp.active = (cur != kBufOut);
+  sched->copy = cp;
+  sched->active_passes = k;
+}
+
 // ---- PTX wrappers ------------------------------------------------------------
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

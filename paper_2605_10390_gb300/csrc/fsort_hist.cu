@@ -149,34 +149,7 @@ __global__ void __launch_bounds__(kRadix) scan_schedule_kernel(uint64_t* __restr
     for (uint32_t c = d; c < chunks; c += kRadix) chunk_flag[uint64_t(j) * chunks + c] = 0;
   }
   __syncthreads();
-  if (d == 0 && sched) {
-    int k = 0;
-    for (int j = 0; j < passes; ++j) k += s_trivial[j] ? 0 : 1;
-    // Buffer sequence b_0 = input, ..., b_k = the buffer holding the result.
-    // In place (input == output): alternate scratch/input; odd k ends in the
-    // scratch buffer and needs the copy back.  Out of place: count backwards
-    // from the output so the last active pass writes it; k == 0 copies.
-    int cur = kBufIn, idx = 0;
-    for (int j = 0; j < kMaxPasses; ++j) {
-      PassDesc pd{0, kBufIn, kBufIn, 0};
-      if (j < passes && !s_trivial[j]) {
-        ++idx;
-        int nxt;
-        if (in_place) nxt = (idx & 1) ? kBufAlt : kBufIn;
-        else nxt = ((k - idx) & 1) ? kBufAlt : kBufOut;
-        pd.active = 1;
-        pd.src = cur;
-        pd.dst = nxt;
-        cur = nxt;
-      }
-      sched->pass[j] = pd;
-    }
-    PassDesc cp{0, cur, in_place ? kBufIn : kBufOut, 0};
-    if (in_place) cp.active = (cur != kBufIn);
-    else cp.active = (cur != kBufOut);
-    sched->copy = cp;
-    sched->active_passes = k;
-  }
+  if (d == 0 && sched) route_passes(s_trivial, passes, in_place, sched);
 }
 
 // Generic row-wise exclusive scan: one CTA of 1024 threads per row.

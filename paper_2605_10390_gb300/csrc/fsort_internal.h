@@ -91,32 +91,40 @@ struct TableGeom {
 int table_tile_keys_for(int key_bits);
 TableGeom table_geometry(uint64_t n, int key_bits, int sms);
 
-// KT1: for the pass of digit 0 of `plan`, per tile the counts of each digit in
-// the earlier tiles of its chunk (tilerel[t][256]) and per chunk the digit
-// totals (chunksum[c][256]); with hist set, every digit of `plan` is also
-// added to hist[j][256].  sched set: the keys are those pass `pass` reads, and
-// an inactive pass counts nothing; else keys[kBufIn].
+// KT1: for the digit (shift, mask), per tile the counts of each digit in the
+// earlier tiles of its chunk (tilerel[t][256]), per chunk the digit totals
+// (chunksum[c][256]) and over all chunks totals[256] += them (zero on entry);
+// with orand set, also orand[0] |= every key and orand[1]
+// &= every key (accumulators: 0 and all ones on entry).  sched set: the keys
+// are those pass `pass` reads, and an inactive pass counts nothing; else
+// keys[kBufIn].
 struct TileCountArgs {
   const void* keys[3];
   uint64_t n;
-  DigitPlan plan;
+  uint32_t shift;
+  uint32_t mask;
   uint32_t tile;
   uint32_t tiles;
   uint32_t chunk_tiles;
   uint32_t pad;
   uint32_t* tilerel;
   uint32_t* chunksum;
-  uint64_t* hist;
+  uint32_t* totals;
+  uint64_t* orand;
   const Schedule* sched;
   int32_t pass;
   int32_t pad2;
   uint32_t* status;  // a failed bounded wait sets kDevBadTable: the scatter then writes nothing
 };
-cudaError_t launch_tile_count(const TileCountArgs& a, int key_bits, int passes, uint32_t chunks,
-                              cudaStream_t stream);
-// KT2: chunkoff[c][d] = base[d] + counts of digit d in chunks before c (32-bit).
-cudaError_t launch_chunk_scan(const uint32_t* chunksum, uint32_t chunks, const uint64_t* base, const Schedule* sched,
-                              int pass, uint32_t* chunkoff, cudaStream_t stream);
+cudaError_t launch_tile_count(const TileCountArgs& a, int key_bits, uint32_t chunks, cudaStream_t stream);
+// The pass schedule from the keys' OR and AND (a pass is trivial when they
+// agree on its digit); resets the accumulators.
+cudaError_t launch_table_schedule(uint64_t* orand, const DigitPlan& plan, int in_place, Schedule* sched,
+                                  cudaStream_t stream);
+// KT2: chunkoff[c][d] = keys of digits below d (from totals) + keys of digit d
+// in chunks before c (32-bit, exact modulo 2^32).
+cudaError_t launch_chunk_scan(const uint32_t* chunksum, const uint32_t* totals, uint32_t chunks,
+                              const Schedule* sched, int pass, uint32_t* chunkoff, cudaStream_t stream);
 // KT3: one stable scatter pass, one CTA per tile, tile t writing digit d from
 // chunkoff[t / chunk_tiles][d] + tilerel[t][d] on.
 struct TileScatterArgs {
@@ -129,6 +137,7 @@ struct TileScatterArgs {
   uint32_t chunk_tiles;
   const uint32_t* tilerel;
   const uint32_t* chunkoff;
+  uint32_t* totals;  // this pass's digit totals, zeroed here once the chunk scan has read them
   const Schedule* sched;  // null: always run, input -> output
   int32_t pass;
   int32_t pad2;
