@@ -2,26 +2,30 @@
 // reduce-then-scan over a table of per-tile digit offsets: no chain between
 // tiles.
 //
-//  KT1 tile_count_kernel    one read of a pass's input: the digit counts of
-//                           every tile (and, on the first read of the input,
-//                           every pass's digit histogram for the schedule).
-//  KT2 column scan          per digit, the exclusive scan of the tile counts
-//                           on top of the digit's global base (Alg. 3's rank
-//                           of every leaf, split over tiles): the first output
-//                           position of digit d for tile t.
-//  KT3 tile_scatter_kernel  one CTA per tile: bulk copy of keys and values into
-//                           shared memory, stable in-warp ranks, the tile's
-//                           digit prefixes, permutation into digit order in
-//                           shared memory, and the write-out in digit runs at
-//                           the tile's table offsets.
+//  KT1 tile_count_kernel      one read of a pass's input, one CTA per chunk of
+//                             consecutive tiles: for every tile the counts of
+//                             each digit in the chunk's earlier tiles, the
+//                             chunk's totals, the pass's totals; on the first
+//                             read of the input also the OR and AND of all keys
+//  table_schedule_kernel      trivial passes (OR and AND agree on the digit)
+//                             and the buffer routing
+//  KT2 chunk_scan_kernel      per digit, the keys of lower digits plus the
+//                             exclusive scan of the chunk totals (Alg. 3's rank
+//                             of every leaf, split over chunks)
+//  KT3 tile_scatter_kernel    one CTA per tile: bulk copy of keys and values
+//                             into shared memory, per-warp digit counts, the
+//                             tile's digit prefixes, stable ranks placed
+//                             straight into digit order in shared memory, and
+//                             the write-out in digit runs at the tile's offsets
+//                             (chunk offset + offset within the chunk).
 //
-// The tile-local steps are those of the chained scatter (fsort_onesweep.cu);
-// what differs is where a tile's digit offsets come from: the chained form
-// waits for its predecessors' prefixes (decoupled look-back), this form reads
-// them from a table that one extra read of the pass input (2 bytes per 16-bit
-// key) and a small scan made before the pass.  Tiles run in launch order, so
-// the runs that neighbouring tiles write into the same output lines meet in
-// L2 at about the same time.
+// The tile-local steps follow the chained scatter (fsort_onesweep.cu); what
+// differs is where a tile's digit offsets come from: the chained form waits
+// for its predecessors' prefixes (decoupled look-back), this form reads them
+// from a table that one read of the pass input (kb bytes per key) and a small
+// scan made before the pass.  Tiles run in launch order, so the runs that
+// neighbouring tiles write into the same output lines meet in L2 at about the
+// same time.
 #include <cstdint>
 #include <cuda_runtime.h>
 
