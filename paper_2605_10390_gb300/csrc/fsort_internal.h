@@ -256,7 +256,7 @@ cudaError_t launch_scan_u32(const uint32_t* in, uint64_t count, uint32_t* out, u
                             cudaStream_t stream);
 
 // Sorting with the map: two-level partition geometry for a sort of n keys.
-constexpr uint32_t kLearnL1Chunks = 4096;  // most level-1 chunks (input ranges owned by one CTA)
+constexpr uint32_t kLearnL1Chunks = 16384;  // most level-1 chunks (input ranges owned by one CTA)
 struct LearnedGeom {
   uint32_t nb;      // bucket ids in use: B + 2 * kLearnMaxHeavy
   uint32_t fbits;   // fine digit width (10..12)

@@ -1147,23 +1147,30 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_
   if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
+// Exclusive scan of the block sums in place, kScanTile at a time with a
+// running carry; sums[nblocks] receives the grand total.
 __global__ void __launch_bounds__(kScanThreads) scan_top_kernel(uint32_t* __restrict__ sums, uint32_t nblocks) {
   __shared__ uint32_t s_w[32];
-  const uint32_t at = threadIdx.x * kScanIpt;
-  uint32_t x[kScanIpt], v = 0;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < nblocks; base += uint32_t(kScanTile)) {
+    const uint32_t at = base + threadIdx.x * kScanIpt;
+    uint32_t x[kScanIpt], v = 0;
 #pragma unroll
-  for (int j = 0; j < kScanIpt; ++j) {
-    x[j] = (at + j < nblocks) ? sums[at + j] : 0u;
-    v += x[j];
-  }
-  uint32_t total;
-  uint32_t run = block_excl_scan(v, s_w, total);
+    for (int j = 0; j < kScanIpt; ++j) {
+      x[j] = (at + j < nblocks) ? sums[at + j] : 0u;
+      v += x[j];
+    }
+    uint32_t total;
+    uint32_t run = carry + block_excl_scan(v, s_w, total);
 #pragma unroll
-  for (int j = 0; j < kScanIpt; ++j) {
-    if (at + j < nblocks) sums[at + j] = run;
-    run += x[j];
+    for (int j = 0; j < kScanIpt; ++j) {
+      if (at + j < nblocks) sums[at + j] = run;
+      run += x[j];
+    }
+    carry += total;
+    __syncthreads();  // s_w is reused by the next segment's scan
   }
-  if (threadIdx.x == 0) sums[nblocks] = total;
+  if (threadIdx.x == 0) sums[nblocks] = carry;
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t* __restrict__ in, uint64_t count,
@@ -1283,7 +1290,7 @@ cudaError_t launch_scan_u32(const uint32_t* in, uint64_t count, uint32_t* out, u
                             cudaStream_t stream) {
   if (!count) return cudaSuccess;
   const uint64_t blocks = (count + kScanTile - 1) / kScanTile;
-  if (blocks > kScanTile) return cudaErrorInvalidValue;
+  if (blocks >= (1ull << 32)) return cudaErrorInvalidValue;
   scan_reduce_kernel<<<unsigned(blocks), kScanThreads, 0, stream>>>(in, count, sums);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1315,7 +1322,7 @@ LearnedGeom learned_geometry(uint64_t n, uint32_t buckets) {
   g.nsuper = (g.nb + (1u << g.fbits) - 1) >> g.fbits;
   g.nids = g.nsuper << g.fbits;
   const uint64_t want = (n + kLearnL1Chunks - 1) / kLearnL1Chunks;
-  g.chunk = want < 65536 ? 65536 : (want + 4095) / 4096 * 4096;
+  g.chunk = want < 16384 ? 16384 : (want + 4095) / 4096 * 4096;
   g.nch = uint32_t((n + g.chunk - 1) / g.chunk);
   if (g.nch == 0) g.nch = 1;
   return g;
