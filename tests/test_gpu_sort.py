@@ -240,6 +240,21 @@ def test_beyond_2pow30_keys_both_forms():
             del dk
 
 
+def test_beyond_2pow31_keys_table_form():
+    """More than 2^31 keys (output positions past the signed 32-bit range) in
+    the default scatter form, whose offsets are 32-bit: keys only, 12-bit
+    precision."""
+    n = (1 << 31) + 4099
+    keys = workloads.generate("uniform", n, 16, seed=0, stream=12)
+    want, _ = oracle.sort(keys, None, 16, 12)
+    with fs.Plan(n, 16, has_values=False) as plan:
+        dk = dev(keys)
+        plan.sort(dk, None, precision_bits=12)
+        plan.sync()
+        got = host(dk)
+    assert np.array_equal(got, want)
+
+
 def test_empty_input_and_describe(plans):
     plan = plans(16, True)
     k = torch.empty(0, dtype=torch.uint16, device="cuda")
