@@ -30,7 +30,8 @@
 //   learn_staged_scatter<2>   per super-bucket: keys to their final buckets
 //   learn_fill_kernel         every heavy bucket filled with its key
 //   learn_bucket_sort_kernel  every non-heavy bucket sorted on chip (a counting
-//                             pass into sub-buckets, then insertion sorts)
+//                             pass into sub-buckets, ranks by counting inside
+//                             small ones, warp splits of large ones)
 // Positions inside a bucket are assigned by shared-memory atomics (order
 // arbitrary); the on-chip sort then orders each bucket completely.
 //
