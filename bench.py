@@ -75,6 +75,23 @@ def measured_peaks():
     return 6800.0, "fallback (6.8 TB/s, earlier GB300 measurement)"
 
 
+def max_over_ranks(torch, dist, values, device):
+    """Element-wise maximum over the ranks of per-rank times (a step of the
+    whole job ends when its slowest rank does); the values themselves on one
+    rank.  Replicas only: this is the one collective, outside the data path."""
+    vals = [float(v) for v in values]
+    if not dist:
+        return vals
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_gkeys_per_s(world: int, keys_per_rank: int, seconds: float) -> float:
+    """Whole-job throughput: the keys all ranks sorted over the max-over-ranks time."""
+    return world * keys_per_rank / seconds / 1e9
+
+
 def source_hash(paths) -> str:
     h = hashlib.sha256()
     for p in paths:
@@ -194,15 +211,13 @@ def run_e2e(fs, workloads, torch, n, rank, world, dist, kb, vb, steps):
             if st > 0:
                 sync_total += time.perf_counter() - t1
     hplan.close()
-    if dist:
-        t = torch.tensor([total, sync_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total, sync_total = float(t[0].item()), float(t[1].item())
-    return {"value": world * steps * len(DISTS) * n / total / 1e9, "unit": "Gkeys/s",
+    total, sync_total = max_over_ranks(torch, dist, [total, sync_total], "cuda")
+    return {"value": job_gkeys_per_s(world, steps * len(DISTS) * n, total), "unit": "Gkeys/s",
             "h2d_bytes_per_step": len(DISTS) * n * (kb + vb), "d2h_bytes_per_step": len(DISTS) * n * (kb + vb),
             "steps": steps, "output_checked": sorted_ok,
             "api": f"fsort_serve_submit / fsort_serve_wait ({lanes} lanes, pinned host buffers in and out)",
-            "sync_single_call": {"value": world * sync_steps * len(DISTS) * n / sync_total / 1e9, "unit": "Gkeys/s",
+            "sync_single_call": {"value": job_gkeys_per_s(world, sync_steps * len(DISTS) * n, sync_total),
+                                 "unit": "Gkeys/s",
                                  "api": "fsort_sort_pairs_host (pinned host buffers, synchronous)"},
             "host_link": "copies measured at ~211 GB/s host to device and ~194 GB/s back; ~343 GB/s both at once"}
 
@@ -628,16 +643,11 @@ def main():
         dist.barrier()
     clocks = sampler.stop() if sampler else None
     plan.sync()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, dist, [ev0.elapsed_time(ev1)], "cuda")[0]
     recs = fs.fsort_plan_timing_report(plan.handle, 1 << 14)
     fs.fsort_plan_set_timing(plan.handle, False)
 
-    keys_total = world * args.steps * len(DISTS) * n
-    value = keys_total / (ms / 1e3) / 1e9
+    value = job_gkeys_per_s(world, args.steps * len(DISTS) * n, ms / 1e3)
 
     # Roofline of the dominant kernel (scatter): algorithmic 12 n bytes per active launch.
     kb, vb = KEY_BITS // 8, 4
