@@ -80,9 +80,9 @@ __host__ __device__ constexpr size_t count_smem_bytes() {
 template <typename K, bool kOrAnd>
 __global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_count_kernel(TileCountArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];  // [kCountStages][step keys]
-  __shared__ uint32_t s_tile[kStepTiles][kRadix];  // the step's tiles
+  __shared__ uint32_t s_tile[2][kStepTiles][kRadix];  // the step's tiles; steps alternate between two sets
   __shared__ uint64_t s_bar[kCountStages];
-  __shared__ uint32_t s_fail;
+  __shared__ uint32_t s_fail[2];  // by step parity: a step reads only its own flag after its barrier
   constexpr uint32_t kStepKeys = count_step_keys<K>();
   constexpr uint32_t kVec = 16 / sizeof(K);
   static_assert(kStepTiles == 2, "a key's tile within the step is one comparison");
@@ -116,16 +116,17 @@ __global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_co
   if (tid == 0) {
     for (int i = 0; i < kCountStages; ++i) mbar_init(&s_bar[i], 1);
     fence_mbar_init();
-    s_fail = 0;
+    s_fail[0] = s_fail[1] = 0;
     for (uint32_t st = 0; st < steps && st < uint32_t(kCountStages); ++st) issue(st);
   }
-  for (int i = tid; i < kStepTiles * kRadix; i += kCountThreads) (&s_tile[0][0])[i] = 0;
+  for (int i = tid; i < 2 * kStepTiles * kRadix; i += kCountThreads) (&s_tile[0][0][0])[i] = 0;
   __syncthreads();
 
   const uint32_t shift = a.shift, mask = a.mask;
   uint64_t k_or = 0, k_and = ~0ull;  // this thread's keys folded
+  uint32_t set = 0;
   auto count_key = [&](K k, uint32_t slot) {
-    atomicAdd(&s_tile[slot][dig(k, shift, mask)], 1u);
+    atomicAdd(&s_tile[set][slot][dig(k, shift, mask)], 1u);
     if (kOrAnd) {
       k_or |= uint64_t(k);
       k_and &= uint64_t(k);
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_co
     step_range(st, e0, e1);
     const uint32_t keys_n = uint32_t(e1 - e0);
     const uint32_t body = (keys_n * uint32_t(sizeof(K)) & ~15u) / sizeof(K);
-    if (!mbar_wait_bounded(&s_bar[st % kCountStages], (st / kCountStages) & 1u)) s_fail = 1;
+    if (!mbar_wait_bounded(&s_bar[st % kCountStages], (st / kCountStages) & 1u)) s_fail[st & 1u] = 1;
     const K* b = buf + size_t(st % kCountStages) * kStepKeys;
     const uint4* bv = reinterpret_cast<const uint4*>(b);
     for (uint32_t v = tid; v < body / kVec; v += kCountThreads) {
@@ -150,23 +151,23 @@ __global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_co
     for (uint32_t i = body + tid; i < keys_n; i += kCountThreads)  // ragged end of the keys
       count_key(keys[e0 + i], i >= a.tile ? 1u : 0u);
     __syncthreads();
-    if (s_fail) {  // the table would be wrong: mark it so that no scatter uses it
+    if (s_fail[st & 1u]) {  // the table would be wrong: mark it so that no scatter uses it
       if (tid == 0) atomicOr(a.status, kDevTimeoutLoad | kDevBadTable);
       return;
     }
-    if (tid < kRadix) {
+    if (tid < kRadix) {  // meanwhile the next step counts into the other set
 #pragma unroll
       for (int j = 0; j < kStepTiles; ++j) {
         if (t_begin + st * kStepTiles + j < t_end) a.tilerel[uint64_t(t_begin + st * kStepTiles + j) * kRadix + tid] = acc;
-        acc += s_tile[j][tid];
-        s_tile[j][tid] = 0;
+        acc += s_tile[set][j][tid];
+        s_tile[set][j][tid] = 0;  // cleared before this thread reaches the next barrier, so before step st + 2 counts
       }
     }
     if (tid == 0 && st + kCountStages < steps) {  // every thread has read this buffer (barrier above)
       fence_proxy_async_smem();
       issue(st + kCountStages);
     }
-    __syncthreads();
+    set ^= 1u;
   }
   if (tid < kRadix) {
     a.chunksum[uint64_t(blockIdx.x) * kRadix + tid] = acc;
