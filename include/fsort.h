@@ -97,6 +97,9 @@ typedef struct fsort_plan_info {
   uint64_t workspace_bytes;/* device scratch owned by the plan */
   uint64_t algorithmic_bytes; /* bytes the hot path must move: key read for the histogram plus
                                  read+write of keys(+values) per pass (expand: read + write of keys) */
+  int32_t scatter_form;    /* 0: per-tile offsets from a table of tile counts (n <= 2^32), 1: chained by
+                              decoupled look-back (tile_keys and num_tiles describe this form) */
+  int32_t reserved;
 } fsort_plan_info;
 
 /* Create a plan: validates desc, allocates all device scratch for sorts of up

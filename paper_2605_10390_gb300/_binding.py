@@ -50,7 +50,8 @@ class FsortBatchConfig(ctypes.Structure):
 class FsortPlanInfo(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int32), ("digit_bits", ctypes.c_int32), ("expand_path", ctypes.c_int32),
                 ("tile_keys", ctypes.c_int32), ("num_tiles", ctypes.c_uint64), ("chunk_keys", ctypes.c_uint64),
-                ("workspace_bytes", ctypes.c_uint64), ("algorithmic_bytes", ctypes.c_uint64)]
+                ("workspace_bytes", ctypes.c_uint64), ("algorithmic_bytes", ctypes.c_uint64),
+                ("scatter_form", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1012,10 +1012,13 @@ fsort_status fsort_plan_describe(const fsort_plan* plan, uint64_t n, int key_bit
   if (st != FSORT_OK) return st;
   std::memset(out, 0, sizeof(*out));
   const uint64_t kb = uint64_t(key_bits) / 8, vb = has_values ? 4 : 0;
+  const bool table = !plan->chained && n <= (1ull << 32);  // the form enqueue_sort takes
+  const int tile = table ? table_tile_keys_for(key_bits) : plan->tile;
   out->digit_bits = plan->digit_bits;
-  out->tile_keys = plan->tile;
+  out->tile_keys = tile;
   out->chunk_keys = plan->chunk_keys;
   out->workspace_bytes = plan->ws_bytes;
+  out->scatter_form = table ? 0 : 1;
   if (use_expand(key_bits, precision_bits, has_values != 0)) {
     out->expand_path = 1;
     out->passes = 0;
@@ -1023,7 +1026,7 @@ fsort_status fsort_plan_describe(const fsort_plan* plan, uint64_t n, int key_bit
     out->algorithmic_bytes = 2 * kb * n;
   } else {
     out->passes = (precision_bits + plan->digit_bits - 1) / plan->digit_bits;
-    out->num_tiles = (n + plan->tile - 1) / plan->tile;
+    out->num_tiles = (n + tile - 1) / tile;
     out->algorithmic_bytes = kb * n + uint64_t(out->passes) * 2 * (kb + vb) * n;
   }
   return FSORT_OK;

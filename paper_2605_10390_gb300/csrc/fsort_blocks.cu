@@ -44,7 +44,7 @@ constexpr int kScanThreads = 1024;
 template <typename K>
 struct TileShape;
 template <>
-struct TileShape<uint16_t> { static constexpr int kBlock = 512, kIpt = 16, kMinBlocks = 2; };
+struct TileShape<uint16_t> { static constexpr int kBlock = 512, kIpt = 18, kMinBlocks = 2; };
 template <>
 struct TileShape<uint32_t> { static constexpr int kBlock = 512, kIpt = 12, kMinBlocks = 2; };
 template <>

@@ -20,7 +20,8 @@ if not torch.cuda.is_available():  # collected on CPU-only machines, never run t
 
 import paper_2605_10390_gb300 as fs  # noqa: E402
 
-TILE = {16: 8192, 32: 6144, 64: 4096}
+TILE = {16: 8192, 32: 6144, 64: 4096}        # chained scatter form
+TABLE_TILE = {16: 9216, 32: 6144, 64: 4096}  # scatter form over the tile-offset table
 DISTS = ["uniform", "zipf1.1", "gauss", "presorted", "equal"]
 
 
@@ -37,8 +38,9 @@ def host(t):
 
 
 def sizes(kb):
-    t = TILE[kb]
-    return [1, 7, 8, 100, t - 1, t, t + 1, 3 * t + 123, (1 << 18) + 5]
+    t, u = TILE[kb], TABLE_TILE[kb]
+    near = sorted({t - 1, t, t + 1, u - 1, u, u + 1, 2 * u + 1})
+    return [1, 7, 8, 100] + near + [3 * t + 123, (1 << 18) + 5]
 
 
 @pytest.fixture(scope="module")
@@ -262,6 +264,10 @@ def test_empty_input_and_describe(plans):
     info = plan.describe(1 << 20, precision_bits=16, has_values=True)
     assert info["passes"] == 2 and info["digit_bits"] == 8 and info["expand_path"] == 0
     assert info["algorithmic_bytes"] == 26 * (1 << 20)
+    assert info["scatter_form"] == 0 and info["tile_keys"] == TABLE_TILE[16]  # table form below 2^32 keys
+    assert info["num_tiles"] == -(-(1 << 20) // TABLE_TILE[16])
+    chained = plans(16, True, flags=FORMS["chained"]).describe(1 << 20, precision_bits=16, has_values=True)
+    assert chained["scatter_form"] == 1 and chained["tile_keys"] == TILE[16]
     info = plan.describe(1 << 20, precision_bits=16, has_values=False)
     assert info["expand_path"] == 1 and info["algorithmic_bytes"] == 4 * (1 << 20)
 
