@@ -494,7 +494,8 @@ FSORT_API uint32_t fsort_plan_device_flags(const fsort_plan* plan);
 /* Human-readable name of a status code (static storage). */
 FSORT_API const char* fsort_status_string(fsort_status status);
 
-/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH (for this 0.x series: 100 = first release, 200 =
+ * fsort_plan_info with scatter_form, scatter passes from a table of per-tile offsets by default). */
 FSORT_API int fsort_version(void);
 
 #ifdef __cplusplus

@@ -1454,6 +1454,6 @@ const char* fsort_status_string(fsort_status status) {
 
 uint32_t fsort_plan_device_flags(const fsort_plan* plan) { return plan ? plan->last_device_flags : 0u; }
 
-int fsort_version(void) { return 100; }
+int fsort_version(void) { return 200; }  // 2.0: fsort_plan_info gained scatter_form; table-form scatter passes
 
 }  // extern "C"
