@@ -123,15 +123,8 @@ template <typename K, bool kVals, int kCap>
 cudaError_t launch_small_typed(const SegDesc* segs, uint32_t count, const DigitPlan& plan, uint32_t* counter, int ctas,
                                cudaStream_t stream) {
   using L = SmallLayout<K, kVals, kCap>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(small_sort_kernel<K, kVals, kCap>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::kBytes));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(small_sort_kernel<K, kVals, kCap>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static const cudaError_t attr = set_smem_attrs(small_sort_kernel<K, kVals, kCap>, L::kBytes, true);
+  if (attr != cudaSuccess) return attr;
   small_sort_kernel<K, kVals, kCap><<<unsigned(ctas), kSmallBlock, L::kBytes, stream>>>(segs, count, plan, counter);
   return cudaGetLastError();
 }

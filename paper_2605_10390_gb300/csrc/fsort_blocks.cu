@@ -470,29 +470,16 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
 template <typename K, bool kVals>
 cudaError_t launch_scatter_typed(const TileScatterArgs& a, uint32_t tiles, cudaStream_t stream) {
   using L = TileSmem<K, kVals>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tile_scatter_kernel<K, kVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(L::kBytes));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(tile_scatter_kernel<K, kVals>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static const cudaError_t attr = set_smem_attrs(tile_scatter_kernel<K, kVals>, L::kBytes, true);
+  if (attr != cudaSuccess) return attr;
   tile_scatter_kernel<K, kVals><<<tiles, L::kBlock, L::kBytes, stream>>>(a);
   return cudaGetLastError();
 }
 
 template <typename K, bool kOrAnd>
 cudaError_t launch_count_variant(const TileCountArgs& a, uint32_t grid, cudaStream_t stream) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(tile_count_kernel<K, kOrAnd>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               int(count_smem_bytes<K>()));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static const cudaError_t attr = set_smem_attrs(tile_count_kernel<K, kOrAnd>, count_smem_bytes<K>(), false);
+  if (attr != cudaSuccess) return attr;
   tile_count_kernel<K, kOrAnd><<<grid, kCountThreads, count_smem_bytes<K>(), stream>>>(a);
   return cudaGetLastError();
 }

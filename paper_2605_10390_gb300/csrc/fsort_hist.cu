@@ -466,13 +466,9 @@ int leaf_hist_grid(int sms) { return sms; }
 
 cudaError_t launch_leaf_histogram(const uint16_t* keys, uint64_t n, uint32_t* partials, uint64_t* spill, int sms,
                                   cudaStream_t stream) {
-  static bool attr_set = false;
   const size_t smem = size_t(kLeafWords) * 4;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(leaf_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static const cudaError_t attr = set_smem_attrs(leaf_hist_kernel, smem, false);
+  if (attr != cudaSuccess) return attr;
   cudaError_t e = cudaMemsetAsync(spill, 0, sizeof(uint64_t) * 65536, stream);
   if (e != cudaSuccess) return e;
   leaf_hist_kernel<<<leaf_hist_grid(sms), kLeafThreads, smem, stream>>>(

@@ -9,6 +9,18 @@
 
 namespace fsort {
 
+// A kernel's dynamic shared-memory limit and, with max_carveout, all of the
+// unified L1/shared capacity as shared memory.  Callers keep the result in a
+// function-local static, so each kernel is set up once per process, and
+// thread-safely (C++ static initialisation), whichever host thread calls first.
+template <typename F>
+inline cudaError_t set_smem_attrs(F* kernel, size_t bytes, bool max_carveout) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e == cudaSuccess && max_carveout)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
+
 // Digit plan of one sort: pass j extracts bits [shift[j], shift[j] + width[j]).
 struct DigitPlan {
   int32_t passes;

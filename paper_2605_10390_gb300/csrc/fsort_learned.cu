@@ -1333,12 +1333,8 @@ cudaError_t launch_learn_l1(const uint64_t* keys, uint64_t n, const LearnedGeom&
                             const LearnedState* st, uint32_t* counts1, uint32_t* hcount, uint32_t* ids,
                             cudaStream_t stream) {
   constexpr int kBytes = (kMaxSuper + kLearnMaxHeavy) * 4;
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(learn_l1_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static const cudaError_t attr = set_smem_attrs(learn_l1_count_kernel, kBytes, false);
+  if (attr != cudaSuccess) return attr;
   learn_l1_count_kernel<<<g.nch, kPartThreads, kBytes, stream>>>(keys, n, g.chunk, g.nch, g.nsuper, g.fbits, mp, st,
                                                                  counts1, hcount, ids);
   return cudaGetLastError();
@@ -1350,17 +1346,9 @@ cudaError_t launch_staged(const uint64_t* src, const uint32_t* ids, const uint16
                           uint16_t* fine_out, unsigned grid, cudaStream_t stream) {
   const uint32_t cap = g.nsuper > (1u << g.fbits) ? g.nsuper : (1u << g.fbits);
   const StLayout L(kLevel, cap);
-  static bool attr = false;
-  if (!attr) {
-    const StLayout most(kLevel, kMaxSuper);
-    cudaError_t e = cudaFuncSetAttribute(learn_staged_scatter_kernel<kLevel>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(most.bytes));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(learn_staged_scatter_kernel<kLevel>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               100);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static const cudaError_t attr =
+      set_smem_attrs(learn_staged_scatter_kernel<kLevel>, StLayout(kLevel, kMaxSuper).bytes, true);
+  if (attr != cudaSuccess) return attr;
   learn_staged_scatter_kernel<kLevel><<<grid, kStThreads, L.bytes, stream>>>(src, ids, fine_in, n, g.chunk, g.nch,
                                                                             g.nsuper, g.fbits, cap, off1, offsets,
                                                                             dst, fine_out);
@@ -1407,16 +1395,14 @@ cudaError_t launch_learn_bucket_sort(uint64_t* keys, const uint32_t* counts, con
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   constexpr int kBytes = 3 * kLearnBucketCap * 8;
-  static int per_sm = 0;
-  if (!per_sm) {
-    e = cudaFuncSetAttribute(learn_bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(learn_bucket_sort_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, learn_bucket_sort_kernel, kBsThreads, kBytes);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-  }
+  static const int per_sm = [] {  // resident CTAs per SM (0: the attributes could not be set)
+    int v = 0;
+    if (set_smem_attrs(learn_bucket_sort_kernel, kBytes, true) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, learn_bucket_sort_kernel, kBsThreads, kBytes) != cudaSuccess)
+      return 0;
+    return v < 1 ? 1 : v;
+  }();
+  if (!per_sm) return cudaErrorInvalidConfiguration;
   const uint64_t want = uint64_t(sms) * per_sm;
   const unsigned grid = unsigned(ngroups < want ? ngroups : want);
   learn_bucket_sort_kernel<<<grid, kBsThreads, kBytes, stream>>>(keys, units);

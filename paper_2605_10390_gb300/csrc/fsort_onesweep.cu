@@ -361,15 +361,8 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
 template <typename K, bool kVals>
 cudaError_t launch_typed(const OnesweepArgs& a, cudaStream_t stream) {
   using L = SmemLayout<K, kVals>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<K, kVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(L::kBytes));
-    if (e == cudaSuccess)  // all of the unified L1/shared capacity as shared memory
-      e = cudaFuncSetAttribute(onesweep_kernel<K, kVals>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static const cudaError_t attr = set_smem_attrs(onesweep_kernel<K, kVals>, L::kBytes, true);
+  if (attr != cudaSuccess) return attr;
   const uint64_t tiles = a.segs ? uint64_t(a.total_tiles) : (a.n + L::kTile - 1) / L::kTile;
   if (!tiles) return cudaSuccess;
   onesweep_kernel<K, kVals><<<unsigned(tiles), L::kBlock, L::kBytes, stream>>>(a);

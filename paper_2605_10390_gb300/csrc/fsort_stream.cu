@@ -21,6 +21,7 @@
 
 #include "../../include/fsort.h"
 #include "fsort_dev.cuh"
+#include "fsort_internal.h"
 
 namespace {
 
@@ -248,13 +249,8 @@ cudaError_t accumulate_typed(fsort_hist* h, const void* keys, uint64_t n, cudaSt
   const K* k = static_cast<const K*>(keys);
   if (h->bins <= uint32_t(kSmemBinsMax)) {
     const size_t bytes = size_t(h->bins) * 4;
-    static bool attr = false;
-    if (!attr) {
-      const cudaError_t e = cudaFuncSetAttribute(shist_smem_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 kSmemBinsMax * 4);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    static const cudaError_t attr = fsort::set_smem_attrs(shist_smem_kernel<K>, size_t(kSmemBinsMax) * 4, false);
+    if (attr != cudaSuccess) return attr;
     // per CTA at most 2^31 keys: its 32-bit counters cannot wrap
     unsigned grid = grid_for(n, kHistThreads, unsigned(h->sms) * 2);
     while (uint64_t(grid) << 31 < n) grid *= 2;
