@@ -96,6 +96,24 @@ def test_batch_autotune_sorts_and_picks_a_config():
         check_batch(kb, p, host, dev)
 
 
+def test_autotune_cache_miss_then_hit(tmp_path):
+    kb, p = 32, 32
+    sizes = [2000, 4000, 9000, 50000, 800, 100000]
+    path = str(tmp_path / "tune.json")
+    host, dev = make_batch(kb, sizes, True, seed=8)
+    with fs.Plan(sum(sizes) + 64, kb, has_values=True, max_segments=16) as plan:
+        cfg, ms, hit = fs.autotune_cached(plan.handle, dev, kb, p, has_values=True, path=path)
+        assert not hit and ms > 0
+        check_batch(kb, p, host, dev)  # the timing runs leave the batch sorted
+    host, dev = make_batch(kb, sizes, True, seed=9)
+    with fs.Plan(sum(sizes) + 64, kb, has_values=True, max_segments=16) as plan:
+        cfg2, _, hit = fs.autotune_cached(plan.handle, dev, kb, p, has_values=True, path=path)
+        assert hit and cfg2 == cfg and fs.fsort_batch_get_config(plan.handle) == cfg
+        plan.sort_batch(dev, precision_bits=p)
+        plan.sync()
+        check_batch(kb, p, host, dev)
+
+
 def test_batch_invalid_arguments():
     k = torch.zeros(5000, dtype=torch.uint32, device="cuda")
     v = torch.zeros(5000, dtype=torch.uint32, device="cuda")
