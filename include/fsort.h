@@ -325,7 +325,9 @@ typedef struct fsort_serve_stats {
   uint64_t bytes_in_use, peak_bytes, budget_bytes;
   uint32_t max_inflight; /* most requests admitted at once */
   uint32_t reserved;
-  double p50_ms, p99_ms, mean_ms, max_ms; /* latency over completed requests */
+  double p50_ms, p99_ms;                  /* latency percentiles (nearest rank) over the most recent
+                                             1,048,576 completed requests */
+  double mean_ms, max_ms;                 /* latency over all completed requests */
   double span_s;                          /* first submit -> last completion */
   double keys_per_s;                      /* keys_completed / span_s */
 } fsort_serve_stats;

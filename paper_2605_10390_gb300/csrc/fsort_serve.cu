@@ -18,7 +18,6 @@
 #include <cstdint>
 #include <cstring>
 #include <deque>
-#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -26,6 +25,7 @@
 #include <vector>
 
 #include "../../include/fsort.h"
+#include "fsort_serve_host.h"
 
 namespace {
 
@@ -35,56 +35,8 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
-// First-fit allocator over [0, size) in 256-byte granules.
-class Arena {
- public:
-  void reset(size_t size) {
-    size_ = size;
-    free_.clear();
-    if (size) free_[0] = size;
-    used_ = peak_ = 0;
-  }
-  bool alloc(size_t bytes, size_t* off) {
-    bytes = round(bytes);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < bytes) continue;
-      *off = it->first;
-      const size_t rest = it->second - bytes;
-      const size_t at = it->first + bytes;
-      free_.erase(it);
-      if (rest) free_[at] = rest;
-      used_ += bytes;
-      peak_ = std::max(peak_, used_);
-      return true;
-    }
-    return false;
-  }
-  void release(size_t off, size_t bytes) {
-    bytes = round(bytes);
-    used_ -= bytes;
-    auto it = free_.emplace(off, bytes).first;
-    auto next = std::next(it);
-    if (next != free_.end() && it->first + it->second == next->first) {
-      it->second += next->second;
-      free_.erase(next);
-    }
-    if (it != free_.begin()) {
-      auto prev = std::prev(it);
-      if (prev->first + prev->second == it->first) {
-        prev->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-  static size_t round(size_t b) { return (b + 255) / 256 * 256; }
-  size_t size() const { return size_; }
-  size_t used() const { return used_; }
-  size_t peak() const { return peak_; }
-
- private:
-  size_t size_ = 0, used_ = 0, peak_ = 0;
-  std::map<size_t, size_t> free_;  // offset -> length
-};
+using fsort_serve::Arena;
+using fsort_serve::LatencyLog;
 
 struct Req {
   uint64_t ticket = 0;
@@ -121,7 +73,7 @@ struct fsort_server {
   // statistics
   uint64_t submitted = 0, completed = 0, keys_completed = 0, batches = 0;
   uint32_t inflight = 0, max_inflight = 0;
-  std::vector<double> latencies;
+  LatencyLog latencies;  // ms, submit -> completion
   bool any = false;
   Clock::time_point t_first, t_last;
 };
@@ -134,9 +86,9 @@ size_t request_bytes(const fsort_server* s, const fsort_request& r) {
   return Arena::round(size_t(r.n) * key_bytes(s)) + (r.vals_host ? Arena::round(size_t(r.n) * 4) : 0);
 }
 
-// Run admitted requests on one lane: copy in, sort (alone or as one batch),
-// copy out, wait.
-fsort_status run_requests(fsort_server* s, Lane& lane, std::vector<Req*>& batch) {
+// Enqueue admitted requests on one lane: copy in, sort (alone or as one
+// batch), copy out.
+fsort_status enqueue_requests(fsort_server* s, Lane& lane, std::vector<Req*>& batch) {
   const size_t kb = key_bytes(s);
   cudaError_t e = cudaSuccess;
   std::vector<fsort_segment> segs;
@@ -166,7 +118,17 @@ fsort_status run_requests(fsort_server* s, Lane& lane, std::vector<Req*>& batch)
     if (e == cudaSuccess && segs[i].vals)
       e = cudaMemcpyAsync(q->r.vals_out_host, segs[i].vals, size_t(q->r.n) * 4, cudaMemcpyDeviceToHost, lane.stream);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(lane.stream);
+  return e == cudaSuccess ? FSORT_OK : FSORT_ERR_CUDA;
+}
+
+// Run admitted requests on one lane and wait for them.  The lane's stream is
+// drained on every outcome: the requests' arena blocks are freed next and may
+// go to another lane at once, so no copy or kernel of this batch may still be
+// in flight, even after a failed enqueue.
+fsort_status run_requests(fsort_server* s, Lane& lane, std::vector<Req*>& batch) {
+  const fsort_status st = enqueue_requests(s, lane, batch);
+  const cudaError_t e = cudaStreamSynchronize(lane.stream);
+  if (st != FSORT_OK) return st;
   if (e != cudaSuccess) return FSORT_ERR_CUDA;
   return fsort_plan_sync(lane.plan);
 }
@@ -233,7 +195,7 @@ void lane_main(fsort_server* s, size_t li) {
         s->arena.release(q->off, q->bytes);
         ++s->completed;
         s->keys_completed += q->r.n;
-        s->latencies.push_back(ms_between(q->t_submit, now));
+        s->latencies.record(ms_between(q->t_submit, now));
       }
       s->inflight -= uint32_t(batch.size());
       s->t_last = now;
@@ -373,7 +335,7 @@ fsort_status fsort_serve_submit(fsort_server* s, const fsort_request* req, uint6
       q->done = true;
       q->t_admit = q->t_done = q->t_submit;
       ++s->completed;
-      s->latencies.push_back(0.0);
+      s->latencies.record(0.0);
       s->t_last = q->t_done;
     } else {
       s->pending.push_back(q);
@@ -419,21 +381,12 @@ fsort_status fsort_serve_stats_get(fsort_server* s, fsort_serve_stats* out) {
   out->peak_bytes = s->arena.peak();
   out->budget_bytes = s->arena.size();
   out->max_inflight = s->max_inflight;
-  if (!s->latencies.empty()) {
-    std::vector<double> v = s->latencies;
-    std::sort(v.begin(), v.end());
-    auto pct = [&](double p) {  // nearest rank
-      size_t i = size_t(p * double(v.size()) + 0.999999);
-      if (i < 1) i = 1;
-      if (i > v.size()) i = v.size();
-      return v[i - 1];
-    };
-    out->p50_ms = pct(0.50);
-    out->p99_ms = pct(0.99);
-    out->max_ms = v.back();
-    double sum = 0;
-    for (double x : v) sum += x;
-    out->mean_ms = sum / double(v.size());
+  if (s->latencies.count()) {
+    const std::vector<double> p = s->latencies.percentiles({0.50, 0.99});
+    out->p50_ms = p[0];
+    out->p99_ms = p[1];
+    out->max_ms = s->latencies.max();
+    out->mean_ms = s->latencies.mean();
   }
   if (s->any) {
     out->span_s = std::chrono::duration<double>(s->t_last - s->t_first).count();
