@@ -26,7 +26,11 @@
  *   - Pointers named keys/vals/counts/... are DEVICE pointers (e.g. a torch
  *     tensor's data_ptr()) unless the name ends in _host.  Key arrays hold
  *     uint16_t, uint32_t or uint64_t elements for key_bits 16, 32, 64; values
- *     are uint32_t.  Key and value arrays must be 16-byte aligned.
+ *     are uint32_t.  Key and value arrays given to the sorts and the scatter
+ *     pass must be 16-byte aligned; every other device array (histogram
+ *     counts and offsets, ranks, bucket ids, the streaming histogram's keys,
+ *     the model's inputs) must be aligned to its element size.  A pointer
+ *     that breaks either rule is FSORT_ERR_INVALID_ARG.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls are stream-ordered: they enqueue work and return; the
  *     caller owns and keeps alive every buffer until the stream reaches it.
@@ -477,10 +481,12 @@ FSORT_API fsort_status fsort_plan_timing_report(fsort_plan* plan, fsort_kernel_t
  *     stream capture.
  *   - The call is synchronous: it enqueues its kernels on `stream`, waits for
  *     them, and returns FSORT_ERR_TIMEOUT if a device-side wait gave up.
- *   - All calls share the one array and it keeps the last call's contents (the
- *     call clears what must start at zero).  Calls that overlap on the GPU --
- *     from several host threads, or alongside another call on another stream --
- *     race on it and give wrong results; serialise them. */
+ *   - All calls on one device share its array, which keeps the last call's
+ *     contents (the call clears what must start at zero).  The library lets
+ *     one call at a time per device use it: calls from several host threads
+ *     of a process take turns (each waits until the previous one has
+ *     returned).  Devices with an index of 64 or more return
+ *     FSORT_ERR_UNSUPPORTED. */
 #define FSORT_NOALLOC_MAX_KEYS 16777216ull
 #define FSORT_NOALLOC_SCRATCH_BYTES 4199168ull
 FSORT_API fsort_status fsort_scatter_pass_noalloc(const void* keys_in, const uint32_t* vals_in, void* keys_out,

@@ -328,7 +328,7 @@ def fsort_scatter_pass_noalloc(keys_in, vals_in, keys_out, vals_out, shift: int,
                                stream=None) -> None:
     """One stable scatter pass without any allocation: its scratch is a fixed
     device array owned by the library (for callers that cannot cudaMalloc).
-    Synchronous; n <= FSORT_NOALLOC_MAX_KEYS; concurrent calls race."""
+    Synchronous; n <= FSORT_NOALLOC_MAX_KEYS; concurrent calls take turns."""
     kb = _key_bits_of(keys_in, key_bits)
     _check(load_library().fsort_scatter_pass_noalloc(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
                                                      _numel(keys_in, n), kb, shift, width, _stream(stream)),

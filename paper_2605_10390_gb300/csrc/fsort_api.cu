@@ -147,6 +147,9 @@ bool valid_key_bits(int kb) { return kb == 16 || kb == 32 || kb == 64; }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Natural alignment of an array read or written element by element (a must be a power of two).
+bool aligned_to(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
 fsort_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return FSORT_OK;
   if (e == cudaErrorMemoryAllocation) return FSORT_ERR_OOM;
@@ -933,10 +936,10 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     L.loss_log = reinterpret_cast<float*>(w + o_l[21]);
     L.st = reinterpret_cast<LearnedState*>(w + o_l[22]);
     e = cudaMallocHost(reinterpret_cast<void**>(&L.h_st), sizeof(LearnedState));
+    if (e != cudaSuccess) L.h_st = nullptr;
     if (e == cudaSuccess) e = cudaMemset(L.st, 0, sizeof(LearnedState));
     if (e == cudaSuccess) e = cudaMemset(L.heavy, 0, size_t(kLearnMaxHeavy) * 8);
     if (e != cudaSuccess) {
-      L.h_st = nullptr;
       cudaGetLastError();
       fsort_plan_destroy(p);
       return FSORT_ERR_OOM;
@@ -1075,12 +1078,20 @@ fsort_status fsort_sort_pairs_host(fsort_plan* plan, void* keys_host, uint32_t* 
   st = take_latched(plan, false, s);
   if (st != FSORT_OK) return st;
   const size_t kbytes = size_t(n) * (key_bits / 8);
+  // The caller may reuse its host buffers once this returns, on an error too:
+  // every copy enqueued so far is drained before any return.
   cudaError_t e = cudaMemcpyAsync(plan->io_keys, keys_host, kbytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && vals_host) e = cudaMemcpyAsync(plan->io_vals, vals_host, n * 4, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return from_cuda(e);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    return from_cuda(e);
+  }
   st = enqueue_any(plan, plan->io_keys, vals_host ? plan->io_vals : nullptr, plan->io_keys,
                    vals_host ? plan->io_vals : nullptr, n, key_bits, precision_bits, s);
-  if (st != FSORT_OK) return st;
+  if (st != FSORT_OK) {
+    cudaStreamSynchronize(s);
+    return st;
+  }
   e = cudaMemcpyAsync(keys_host, plan->io_keys, kbytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && vals_host) e = cudaMemcpyAsync(vals_host, plan->io_vals, n * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1092,7 +1103,7 @@ fsort_status fsort_histogram(fsort_plan* plan, const void* keys, uint64_t n, int
                              int digit_bits, uint64_t* counts_out, void* stream) {
   fsort_status st = check_call(plan, n, key_bits, precision_bits, false);
   if (st != FSORT_OK) return st;
-  if (!counts_out || (n && (!keys || !aligned16(keys)))) return FSORT_ERR_INVALID_ARG;
+  if (!counts_out || !aligned_to(counts_out, 8) || (n && (!keys || !aligned16(keys)))) return FSORT_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   st = take_latched(plan, false, s);
   if (st != FSORT_OK) return st;
@@ -1115,7 +1126,8 @@ fsort_status fsort_histogram(fsort_plan* plan, const void* keys, uint64_t n, int
 
 fsort_status fsort_exclusive_scan(fsort_plan* plan, const uint64_t* counts, uint64_t rows, uint64_t bins,
                                   uint64_t* offsets_out, void* stream) {
-  if (!plan || !counts || !offsets_out) return FSORT_ERR_INVALID_ARG;
+  if (!plan || !counts || !offsets_out || !aligned_to(counts, 8) || !aligned_to(offsets_out, 8))
+    return FSORT_ERR_INVALID_ARG;
   if (bins != (1ull << plan->digit_bits) && bins != 65536) return FSORT_ERR_INVALID_ARG;
   if (rows < 1 || rows > 65535) return FSORT_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1182,7 +1194,7 @@ fsort_status fsort_expand(fsort_plan* plan, const uint64_t* counts, void* keys_o
                           void* stream) {
   fsort_status st = check_call(plan, n, key_bits, key_bits, false);
   if (st != FSORT_OK) return st;
-  if (key_bits != 16 || !counts) return FSORT_ERR_INVALID_ARG;
+  if (key_bits != 16 || !counts || !aligned_to(counts, 8)) return FSORT_ERR_INVALID_ARG;
   if (n == 0) return FSORT_OK;
   if (!keys_out || !aligned16(keys_out)) return FSORT_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1356,7 +1368,7 @@ fsort_status fsort_learned_set_model(fsort_plan* plan, const float* params_host,
 fsort_status fsort_learned_bucket_ids(fsort_plan* plan, const void* keys, uint64_t n, uint32_t* ids, void* stream) {
   if (!plan || !plan->learn || !plan->learn->fitted) return FSORT_ERR_INVALID_ARG;
   if (n == 0) return FSORT_OK;
-  if (!keys || !ids || n >= (1ull << 32)) return FSORT_ERR_INVALID_ARG;
+  if (!keys || !ids || !aligned_to(keys, 8) || !aligned_to(ids, 4) || n >= (1ull << 32)) return FSORT_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const cudaError_t e = launch_learn_bucket_ids(static_cast<const uint64_t*>(keys), n,
                                                 learned_map(*plan->learn, n), ids, s);
@@ -1365,12 +1377,16 @@ fsort_status fsort_learned_bucket_ids(fsort_plan* plan, const void* keys, uint64
 
 fsort_status fsort_mlp_forward(const void* w_bf16, const float* x, uint32_t m, float* out, void* stream) {
   if (!w_bf16 || !x || !out || m < 1) return FSORT_ERR_INVALID_ARG;
+  if (!aligned_to(w_bf16, 2) || !aligned_to(x, 4) || !aligned_to(out, 4)) return FSORT_ERR_INVALID_ARG;
   return from_cuda(launch_mlp_eval(w_bf16, x, m, out, static_cast<cudaStream_t>(stream)));
 }
 
 fsort_status fsort_mlp_grad(const void* w_bf16, const float* x, const float* y, uint32_t m, float* grads, float* loss,
                             void* stream) {
   if (!w_bf16 || !x || !y || !grads || m < 1) return FSORT_ERR_INVALID_ARG;
+  if (!aligned_to(w_bf16, 2) || !aligned_to(x, 4) || !aligned_to(y, 4) || !aligned_to(grads, 4) ||
+      (loss && !aligned_to(loss, 4)))
+    return FSORT_ERR_INVALID_ARG;
   return from_cuda(launch_mlp_grad(w_bf16, x, y, m, grads, loss, static_cast<cudaStream_t>(stream)));
 }
 

@@ -46,17 +46,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_lock;
 void* g_scratch_ptr[kMaxDevices] = {};
+std::mutex g_call_lock[kMaxDevices];  // one call at a time per device: they share the array
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
-cudaError_t scratch_for_current_device(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+// Device address of g_noalloc_scratch on device `dev`, the current device
+// (looked up once).
+cudaError_t scratch_for_device(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> g(g_lock);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = p;
   }
@@ -90,13 +88,16 @@ extern "C" fsort_status fsort_scatter_pass_noalloc(const void* keys_in, const ui
   if (overlaps(keys_in, kbytes, keys_out, kbytes)) return FSORT_ERR_INVALID_ARG;
   if (vals_in && overlaps(vals_in, n * 4, vals_out, n * 4)) return FSORT_ERR_INVALID_ARG;
 
-  unsigned char* w = nullptr;
-  cudaError_t e = scratch_for_current_device(&w);
-  if (e != cudaSuccess) return FSORT_ERR_CUDA;
   int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return FSORT_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FSORT_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return FSORT_ERR_UNSUPPORTED;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FSORT_ERR_CUDA;
+  unsigned char* w = nullptr;
+  cudaError_t e = scratch_for_device(dev, &w);
+  if (e != cudaSuccess) return FSORT_ERR_CUDA;
+  // Calls from several host threads take turns: the call is synchronous, so
+  // holding the lock until it returns keeps every other call off the array.
+  std::lock_guard<std::mutex> turn(g_call_lock[dev]);
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint32_t* counters = reinterpret_cast<uint32_t*>(w + kOffCounters);

@@ -231,6 +231,9 @@ fsort_status from_cuda(cudaError_t e) {
   return FSORT_ERR_CUDA;
 }
 
+// Natural alignment of an array read or written element by element (a must be a power of two).
+bool aligned_to(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
 cudaError_t build_index(fsort_hist* h, cudaStream_t s) {
   if (!h->dirty) return cudaSuccess;
   const uint64_t m = h->bins;
@@ -313,7 +316,7 @@ fsort_status fsort_hist_reset(fsort_hist* h, void* stream) {
 }
 
 fsort_status fsort_hist_accumulate(fsort_hist* h, const void* keys, uint64_t n, void* stream) {
-  if (!h || (n && !keys)) return FSORT_ERR_INVALID_ARG;
+  if (!h || (n && (!keys || !aligned_to(keys, uintptr_t(h->key_bits / 8))))) return FSORT_ERR_INVALID_ARG;
   if (n == 0) return FSORT_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
@@ -333,13 +336,14 @@ fsort_status fsort_hist_total(const fsort_hist* h, uint64_t* total) {
 }
 
 fsort_status fsort_hist_counts(fsort_hist* h, uint64_t* counts_out, void* stream) {
-  if (!h || !counts_out) return FSORT_ERR_INVALID_ARG;
+  if (!h || !counts_out || !aligned_to(counts_out, 8)) return FSORT_ERR_INVALID_ARG;
   return from_cuda(cudaMemcpyAsync(counts_out, h->counts, size_t(h->bins) * 8, cudaMemcpyDeviceToDevice,
                                    static_cast<cudaStream_t>(stream)));
 }
 
 fsort_status fsort_hist_rank(fsort_hist* h, const uint64_t* values, uint64_t count, uint64_t* ranks, void* stream) {
-  if (!h || (count && (!values || !ranks))) return FSORT_ERR_INVALID_ARG;
+  if (!h || (count && (!values || !ranks || !aligned_to(values, 8) || !aligned_to(ranks, 8))))
+    return FSORT_ERR_INVALID_ARG;
   if (count == 0) return FSORT_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = build_index(h, s);
@@ -352,7 +356,8 @@ fsort_status fsort_hist_rank(fsort_hist* h, const uint64_t* values, uint64_t cou
 }
 
 fsort_status fsort_hist_select(fsort_hist* h, const uint64_t* ranks, uint64_t count, uint64_t* values, void* stream) {
-  if (!h || (count && (!values || !ranks))) return FSORT_ERR_INVALID_ARG;
+  if (!h || (count && (!values || !ranks || !aligned_to(values, 8) || !aligned_to(ranks, 8))))
+    return FSORT_ERR_INVALID_ARG;
   if (count == 0) return FSORT_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = build_index(h, s);
@@ -365,7 +370,8 @@ fsort_status fsort_hist_select(fsort_hist* h, const uint64_t* ranks, uint64_t co
 }
 
 fsort_status fsort_hist_expand(fsort_hist* h, void* keys_out, uint64_t n, void* stream) {
-  if (!h || n != h->total || (n && !keys_out)) return FSORT_ERR_INVALID_ARG;
+  if (!h || n != h->total || (n && (!keys_out || !aligned_to(keys_out, uintptr_t(h->key_bits / 8)))))
+    return FSORT_ERR_INVALID_ARG;
   if (n == 0) return FSORT_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = build_index(h, s);

@@ -59,6 +59,23 @@ def test_calls_without_gpu_work():
     assert lib.fsort_sort_pairs(None, None, None, 10, 16, 16, None) == 1
 
 
+def test_misaligned_model_arrays_are_refused_before_any_launch():
+    # every call below has one array off its element alignment, so the host
+    # check refuses it (status 1) before anything reaches a device
+    lib = fs.load_library()
+    w, f, odd = 0x10000, 0x20000, 0x30001  # 0x30001: not 2- or 4-byte aligned
+    fwd = lib.fsort_mlp_forward
+    assert fwd(ctypes.c_void_p(odd), ctypes.c_void_p(f), 8, ctypes.c_void_p(f), None) == 1
+    assert fwd(ctypes.c_void_p(w), ctypes.c_void_p(f + 2), 8, ctypes.c_void_p(f), None) == 1
+    assert fwd(ctypes.c_void_p(w), ctypes.c_void_p(f), 8, ctypes.c_void_p(f + 1), None) == 1
+    grad = lib.fsort_mlp_grad
+    for bad in range(5):
+        ptrs = [w, f, f, f, f]
+        ptrs[bad] = odd
+        args = [ctypes.c_void_p(p) for p in ptrs]
+        assert grad(args[0], args[1], args[2], 8, args[3], args[4], None) == 1, bad
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     from paper_2605_10390_gb300 import _binding
     monkeypatch.setattr(_binding, "_LIB", str(tmp_path / "nope.so"))

@@ -276,6 +276,8 @@ def test_invalid_arguments(plans):
     plan = plans(16, False, 1000)
     k = torch.zeros(2000, dtype=torch.uint16, device="cuda")
     v = torch.zeros(2000, dtype=torch.uint32, device="cuda")
+    c = torch.zeros(1024, dtype=torch.int64, device="cuda")
+    c2 = torch.zeros(1024, dtype=torch.int64, device="cuda")
     bad = [
         lambda: fs.fsort_sort_pairs(plan.handle, k, None, n=1001, key_bits=16, precision_bits=16),  # n > max_n
         lambda: fs.fsort_sort_pairs(plan.handle, k, None, n=10, key_bits=32, precision_bits=16),    # width
@@ -287,6 +289,11 @@ def test_invalid_arguments(plans):
                                         precision_bits=16),  # overlap
         lambda: fs.fsort_sort_pairs_host(plan.handle, np.zeros(10, np.uint16), None, key_bits=16,
                                          precision_bits=16),  # plan without host buffers
+        # count and offset arrays off their 8-byte alignment: refused on the host
+        lambda: fs.fsort_histogram(plan.handle, k, c.data_ptr() + 4, n=100, key_bits=16, precision_bits=16),
+        lambda: fs.fsort_exclusive_scan(plan.handle, c.data_ptr() + 4, 1, 256, c2),
+        lambda: fs.fsort_exclusive_scan(plan.handle, c, 1, 256, c2.data_ptr() + 2),
+        lambda: fs.fsort_expand(plan.handle, c.data_ptr() + 4, k, n=10, key_bits=16),
     ]
     for f in bad:
         with pytest.raises(fs.FsortError) as e:

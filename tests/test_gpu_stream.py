@@ -99,3 +99,23 @@ def test_skewed_stream_all_equal_keys():
         fs.fsort_hist_expand(h.handle, out)
         torch.cuda.synchronize()
     assert torch.all(out == (0xFEDCBA9876543210 >> (64 - p)))
+
+
+def test_misaligned_arrays_are_refused():
+    """Arrays off their element alignment are refused on the host (status 1)."""
+    k = torch.zeros(64, dtype=torch.uint32, device="cuda")
+    v = torch.zeros(64, dtype=torch.int64, device="cuda")
+    with fs.StreamHistogram(32, 12) as h:
+        fs.fsort_hist_accumulate(h.handle, k, n=10)
+        bad = [
+            lambda: fs.fsort_hist_accumulate(h.handle, k.data_ptr() + 2, n=10),
+            lambda: fs.fsort_hist_counts(h.handle, v.data_ptr() + 4),
+            lambda: fs.fsort_hist_rank(h.handle, v.data_ptr() + 4, v, count=4),
+            lambda: fs.fsort_hist_select(h.handle, v, v.data_ptr() + 4, count=4),
+            lambda: fs.fsort_hist_expand(h.handle, k.data_ptr() + 2, n=10),
+        ]
+        for f in bad:
+            with pytest.raises(fs.FsortError) as e:
+                f()
+            assert e.value.status == 1
+        assert fs.fsort_hist_total(h.handle) == 10

@@ -7,9 +7,12 @@ fixed device array inside the library instead of a plan.  This file is named so
 that pytest collects it last; it passes alone in a fresh process and after the
 other tests.  Integer data, so "within tolerance" means bit-exact.
 """
+import threading
+
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 
 torch = pytest.importorskip("torch")
@@ -58,3 +61,41 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         fs.fsort_scatter_pass_noalloc(k, None, torch.empty_like(k), None, 0, 8, n=fs.FSORT_NOALLOC_MAX_KEYS + 1,
                                       key_bits=16)
     assert e.value.status == 1
+
+
+def test_noalloc_calls_from_several_threads_take_turns():
+    """Four host threads, each on its own stream with its own data, call the
+    pass at once: the library runs them one at a time on the shared array, so
+    every result equals the oracle's pass on that thread's input."""
+    n, kb = 2 * 8192 + 1001, 32
+    cases = []
+    for t in range(4):
+        keys = workloads.generate(["uniform", "zipf1.1", "gauss", "presorted"][t], n, kb, seed=5, stream=40 + t)
+        vals = np.arange(n, dtype=np.uint32) + np.uint32(t << 24)
+        shift, width = [(0, 8), (24, 8), (13, 6), (5, 3)][t]
+        cases.append((keys, vals, shift, width, oracle.scatter_pass(keys, vals, kb, shift, width)))
+    results, errors = [None] * 4, []
+
+    def worker(t):
+        try:
+            keys, vals, shift, width, _ = cases[t]
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                dk, dv = _dev(keys), _dev(vals)
+                ok, ov = torch.empty_like(dk), torch.empty_like(dv)
+                stream.synchronize()
+                for _ in range(3):  # repeated calls interleave with the other threads'
+                    fs.fsort_scatter_pass_noalloc(dk, dv, ok, ov, shift, width, key_bits=kb, stream=stream)
+                    results[t] = (ok.cpu().numpy(), ov.cpu().numpy())
+        except Exception as e:  # reported below, on the main thread
+            errors.append((t, e))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=300)
+    assert not errors, errors
+    for t, (_, _, _, _, (wk, wv)) in enumerate(cases):
+        assert np.array_equal(results[t][0], wk), t
+        assert np.array_equal(results[t][1], wv), t
