@@ -100,10 +100,10 @@ def source_hash(paths) -> str:
     return h.hexdigest()
 
 
-def ncu_traffic(n):
+def ncu_traffic(n, path=None):
     """DRAM bytes per scatter launch from the committed ncu summary, if it was
     taken on the current kernel source; scaled to n keys if taken smaller."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = path or os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None, "no ncu capture committed"
     with open(path) as f:
@@ -137,20 +137,27 @@ class ClockSampler:
         time.sleep(0.25)
         self.proc.terminate()
         out, _ = self.proc.communicate(timeout=10)
-        rows = [[c.strip() for c in line.split(",")] for line in out.strip().splitlines() if line.count(",") >= 8]
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            try:
-                sm.append(float(r[1]))
-                mx.append(float(r[2]))
-            except ValueError:
-                continue
-            for name, v in zip(names, r[5:9]):
-                if v.lower() == "active":
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return parse_clock_samples(out)
+
+
+def parse_clock_samples(text: str) -> dict:
+    """Summary of `nvidia-smi --query-gpu=<ClockSampler.FIELDS> --format=csv,noheader,nounits`
+    rows: median SM clock, highest max clock, and every throttle reason seen
+    Active in any sample.  Rows without numeric clocks ([N/A], a header) are skipped."""
+    rows = [[c.strip() for c in line.split(",")] for line in text.strip().splitlines() if line.count(",") >= 8]
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        try:
+            sm.append(float(r[1]))
+            mx.append(float(r[2]))
+        except ValueError:
+            continue
+        for name, v in zip(names, r[5:9]):
+            if v.lower() == "active":
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def run_e2e(fs, workloads, torch, n, rank, world, dist, kb, vb, steps):
