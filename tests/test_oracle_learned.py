@@ -29,13 +29,34 @@ def test_bf16_round_matches_library_cast():
     assert np.array_equal(ol.bf16_round(x), want)
 
 
-def test_forward_single_path_closed_form():
-    a, c, d, e, f = 1.7, -0.3, 0.9, 2.5, -0.4
+def single_path(a, c, d, g, e, f):
+    """Parameters of a network with one path: W1[0], b1[0], W2[0][0], b2[0], W3[0], b3."""
     p = np.zeros(ol.PARAMS)
-    p[0], p[64], p[128], p[128 + 4096 + 64], p[-1] = a, c, d, e, f  # W1[0], b1[0], W2[0][0], W3[0], b3
+    p[0], p[64], p[128], p[128 + 4096], p[128 + 4096 + 64], p[-1] = a, c, d, g, e, f
+    return p
+
+
+def single_path_value(x, a, c, d, g, e, f):
+    return 1.0 / (1.0 + math.exp(-(e * max(0.0, d * max(0.0, a * x + c) + g) + f)))
+
+
+@pytest.mark.parametrize("d,g", [(0.9, 0.2), (-0.9, 0.2), (0.9, -0.5)])
+def test_forward_single_path_closed_form(d, g):
+    # d < 0 or g < 0 drives layer 2 below zero for some x: its ReLU must clip there
+    a, c, e, f = 1.7, -0.3, 2.5, -0.4
     xs = np.linspace(-2, 2, 41)
-    want = [1.0 / (1.0 + math.exp(-(e * max(0.0, d * max(0.0, a * x + c)) + f))) for x in xs]
-    assert np.allclose(ol.forward(p, xs), want, rtol=0, atol=1e-15)
+    want = [single_path_value(x, a, c, d, g, e, f) for x in xs]
+    assert np.allclose(ol.forward(single_path(a, c, d, g, e, f), xs), want, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("d,g", [(0.9, 0.2), (-0.9, 0.2), (0.9, -0.5)])
+def test_loss_single_path_closed_form(d, g):
+    a, c, e, f = 1.7, -0.3, 2.5, -0.4
+    x = np.array([-1.5, -0.2, 0.1, 0.4, 0.9, 1.6])
+    y = np.array([0.1, 0.3, 0.5, 0.7, 0.2, 0.9])
+    want = 0.5 * np.mean([(single_path_value(xi, a, c, d, g, e, f) - yi) ** 2 for xi, yi in zip(x, y)])
+    loss, _ = ol.loss_and_grad(single_path(a, c, d, g, e, f), x, y)
+    assert loss == pytest.approx(want, rel=1e-13)
 
 
 def test_forward_uses_row_j_of_w2_for_unit_j():
@@ -153,3 +174,47 @@ def test_judge_rule():
     keys = np.concatenate([keys, np.full(80, 3, np.uint64)])  # bucket 0 grows to 112 > 8 * 3280 // 256
     ok, mx, limit, _ = ol.judge(keys, t, np.zeros(0, np.uint64))
     assert not ok and mx == 112 and limit == 102
+
+
+def test_judge_ignores_heavy_buckets():
+    # heavy key 10 sits alone in its bucket; its 504 copies must not count as imbalance
+    t = np.zeros((ol.CELLS + 1, 2), dtype=np.uint32)
+    t[:, 0] = np.minimum(np.arange(ol.CELLS + 1, dtype=np.uint64) << np.uint64(21), 0xFFFFFFFF)
+    t[ol.CELLS] = (0xFFFFFFFF, 1)
+    keys = np.concatenate([np.repeat(np.arange(0, 800, dtype=np.uint64), 4), np.full(500, 10, np.uint64)])
+    heavy = np.array([10], dtype=np.uint64)
+    ids = ol.bucket_ids(np.array([9, 10, 11], dtype=np.uint64), t, heavy, keys.size)
+    assert ids.tolist() == [1, 2, 3]  # (k >> 3) + 2 [k > 10] + [k == 10]
+    ok, mx, limit, b = ol.judge(keys, t, heavy)
+    assert (b, limit) == (256, 8 * 3700 // 256) and mx == 32 and ok
+
+
+def test_feature_closed_form():
+    # log2(k + 1) is exact for k + 1 a power of two
+    c, h = 0.25, 0.5
+    k = np.array([0, 1, 3, (1 << 32) - 1, (1 << 64) - 1], dtype=np.uint64)
+    want = [(e / 64 - c) / h for e in (0, 1, 2, 32, 64)]
+    assert np.allclose(ol.feature(k, c, h), want, rtol=0, atol=1e-12)
+
+
+def test_table_of_a_decreasing_network_is_flat():
+    # F(x) = sigmoid(-x) for x >= 0 decreases along the cells; its running maximum stays at
+    # F(x_0) = 1/2.  With center 0 and half 1/64 the feature is log2(start + 1), so the
+    # uniform term is 1/2 at cell 0 and 1 elsewhere: G_0 = 2^32 (15/32 + 1/32) = 2^31 and
+    # G_i = 2^32 (15/32 + 2/32) = 17 * 2^27 for every later cell.
+    p = np.zeros(ol.PARAMS)
+    p[0] = 1.0                     # W1[0]
+    p[128] = 1.0                   # W2[0][0]
+    p[128 + 4096 + 64] = -1.0      # W3[0]
+    t = ol.table(p, np.zeros(0, np.uint64), center=0.0, half=1.0 / 64.0)
+    assert t[0, 0] == 1 << 31
+    assert np.all(t[1:ol.CELLS, 0] == 17 << 27)
+    assert tuple(t[ol.CELLS]) == (0xFFFFFFFF, 0)
+
+
+def test_buckets_for_rounds_up_and_clamps():
+    # B = the smallest power of two >= n / 1024, clamped to [2^8, 2^22]
+    assert ol.buckets_for(1) == 256 and ol.buckets_for(256 * 1024) == 256
+    assert ol.buckets_for(256 * 1024 + 1) == 512
+    assert ol.buckets_for(1 << 30) == 1 << 20 and ol.buckets_for((1 << 30) + 1) == 1 << 21
+    assert ol.buckets_for(1 << 40) == 1 << 22
