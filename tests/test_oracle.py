@@ -270,20 +270,29 @@ _MUTANTS = {
     "rank_wrong_child": ("if (bit) idx += tree[level_base(l + 1) + (prefix << 1)];",
                          "if (bit) idx += tree[level_base(l + 1) + (prefix << 1) + 1];"),
     "sort_key_shift": ("return k >> (key_bits - p);", "return k >> (key_bits - p + 1);"),
+    # the step functions on their own (histograms, one pass, expand, tree build)
+    "hist_one_row_for_all_passes": ("counts[(uint64_t)j * bins + digit_of(s, precision_bits, digit_bits, j)] += 1",
+                                    "counts[digit_of(s, precision_bits, digit_bits, j)] += 1"),
+    "hist_raw_key": ("const uint64_t s = sort_key(get_key(keys, key_bits, i), key_bits, precision_bits);\n    for (int j",
+                     "const uint64_t s = get_key(keys, key_bits, i);\n    for (int j"),
+    "hist_digit_low_bit": ("return (s >> lo) & mask;", "return (s >> (lo + 1)) & mask;"),
+    "pass_mask_off_by_one": ("const uint64_t bins = 1ULL << width, mask = bins - 1;",
+                             "const uint64_t bins = 1ULL << width, mask = (bins >> 1) - 1;"),
+    "expand_drops_last_bin": ("for (uint64_t b = 0; b < bins; ++b)\n", "for (uint64_t b = 0; b + 1 < bins; ++b)\n"),
+    "tree_build_skips_root": ("for (int l = 0; l <= p; ++l) tree", "for (int l = 1; l <= p; ++l) tree"),
+    "tree_build_skips_leaves": ("for (int l = 0; l <= p; ++l) tree", "for (int l = 0; l < p; ++l) tree"),
 }
 
 
-def _mutant_lib(tmp_path, name):
-    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
-    old, new = _MUTANTS[name]
-    assert old in src, name
-    path = tmp_path / f"{name}.c"
-    path.write_text(src.replace(old, new, 1))
-    so = tmp_path / f"{name}.so"
-    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(so), str(path)])
-    lib = ctypes.CDLL(str(so))
+def _bind(so_path):
+    lib = ctypes.CDLL(str(so_path))
     vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
     lib.oracle_sort.argtypes = [vp, vp, vp, vp, u64, i32, i32]
+    lib.oracle_scatter_pass.argtypes = [vp, vp, vp, vp, u64, i32, i32, i32]
+    lib.oracle_digit_histograms.argtypes = [vp, u64, i32, i32, i32, vp]
+    lib.oracle_exclusive_scan.argtypes = [vp, u64, vp]
+    lib.oracle_exclusive_scan.restype = None
+    lib.oracle_expand.argtypes = [vp, u64, i32, vp]
     lib.oracle_tree_build.argtypes = [vp, u64, i32, i32, vp]
     lib.oracle_tree_rank.argtypes = [vp, i32, u64]
     lib.oracle_tree_rank.restype = u64
@@ -292,8 +301,20 @@ def _mutant_lib(tmp_path, name):
     return lib
 
 
+def _mutant_lib(tmp_path, name):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    old, new = _MUTANTS[name]
+    assert src.count(old) == 1, name
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new, 1))
+    so = tmp_path / f"{name}.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(so), str(path)])
+    return _bind(so)
+
+
 def _pins_pass(lib):
-    """The sort, rank and select pins above, run against a given library."""
+    """The pins above (worked example, stable argsort, bincount, cumsum,
+    repeat, brute-force rank and select), run against a given library."""
     g = _golden()
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     keys = np.array([int(x, 16) for x in g["keys"]], dtype=np.uint16)
@@ -308,12 +329,48 @@ def _pins_pass(lib):
         order = _ref_order(k, kb, pb)
         if not np.array_equal(vo, order.astype(np.uint32)):
             return False
+    # histograms against bincount, for a precision below the key width and two digit widths
+    for kb, pb, d in [(16, 13, 8), (32, 20, 11)]:
+        k = _rand_keys(rng, 3000, kb, 2)
+        passes = -(-pb // d)
+        h = np.zeros((passes, 1 << d), dtype=np.uint64)
+        if lib.oracle_digit_histograms(p(k), k.size, kb, pb, d, p(h)) != 0:
+            return False
+        s = k.astype(np.uint64) >> np.uint64(kb - pb)
+        for j in range(passes):
+            dig = (s >> np.uint64(j * d)) & np.uint64((1 << min(d, pb - j * d)) - 1)
+            if not np.array_equal(h[j], np.bincount(dig.astype(np.int64), minlength=1 << d).astype(np.uint64)):
+                return False
+    # scan against cumsum
+    c = rng.integers(0, 1000, size=4096, dtype=np.uint64)
+    b = np.empty_like(c)
+    lib.oracle_exclusive_scan(p(c), c.size, p(b))
+    if not np.array_equal(b, np.concatenate([[0], np.cumsum(c)[:-1]]).astype(np.uint64)):
+        return False
+    # one pass against numpy's stable argsort on the digit
+    k = _rand_keys(rng, 3000, 32, 5)
+    v = rng.integers(0, 2 ** 32, size=3000, dtype=np.uint64).astype(np.uint32)
+    ko, vo = np.empty_like(k), np.empty_like(v)
+    if lib.oracle_scatter_pass(p(k), p(v), p(ko), p(vo), k.size, 32, 5, 11) != 0:
+        return False
+    order = np.argsort((k.astype(np.uint64) >> np.uint64(5)) & np.uint64(2047), kind="stable")
+    if not (np.array_equal(ko, k[order]) and np.array_equal(vo, v[order])):
+        return False
+    # expand against repeat (the last bin non-empty)
+    c = rng.integers(0, 4, size=65536, dtype=np.uint64)
+    c[-1] = 2
+    out = np.empty(int(c.sum()), dtype=np.uint16)
+    if lib.oracle_expand(p(c), c.size, 16, p(out)) != 0:
+        return False
+    if not np.array_equal(out, np.repeat(np.arange(65536, dtype=np.uint16), c.astype(np.int64))):
+        return False
+    # tree rank and select against brute force
     k = _rand_keys(rng, 300, 16, 3)
     tree = np.zeros((1 << 9) - 1, dtype=np.uint64)
     lib.oracle_tree_build(p(k), k.size, 16, 8, p(tree))
     s = k.astype(np.int64) >> 8
-    for v in range(256):
-        if lib.oracle_tree_rank(p(tree), 8, v) != int(np.sum(s < v)):
+    for val in range(256):
+        if lib.oracle_tree_rank(p(tree), 8, val) != int(np.sum(s < val)):
             return False
     srt = np.sort(s)
     for r in range(k.size):
@@ -326,15 +383,7 @@ def test_pins_accept_unmutated_oracle(tmp_path):
     src = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
     so = tmp_path / "clean.so"
     subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(so), src])
-    lib = ctypes.CDLL(str(so))
-    vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
-    lib.oracle_sort.argtypes = [vp, vp, vp, vp, u64, i32, i32]
-    lib.oracle_tree_build.argtypes = [vp, u64, i32, i32, vp]
-    lib.oracle_tree_rank.argtypes = [vp, i32, u64]
-    lib.oracle_tree_rank.restype = u64
-    lib.oracle_tree_select.argtypes = [vp, i32, u64]
-    lib.oracle_tree_select.restype = u64
-    assert _pins_pass(lib)
+    assert _pins_pass(_bind(so))
 
 
 @pytest.mark.parametrize("name", sorted(_MUTANTS))
