@@ -189,14 +189,22 @@ def load_library():
 # ---- marshalling helpers ------------------------------------------------------
 
 def _ptr(x) -> int | None:
-    """Device (or host) address of a torch tensor, numpy array or int; None -> NULL."""
+    """Device (or host) address of a torch tensor, numpy array or int; None -> NULL.
+
+    The library reads every array as dense elements from its address, so a
+    strided view (``keys[::2]``, a column of a row-major matrix) is refused:
+    passing its address would sort the wrong elements without an error."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
     if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor is not contiguous; pass .contiguous() or a dense copy")
         return x.data_ptr()
     if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array is not C-contiguous; pass np.ascontiguousarray(...)")
         return x.ctypes.data
     raise TypeError(f"cannot take the address of {type(x).__name__}")
 
@@ -432,6 +440,13 @@ def fsort_learned_set_model(plan, params=None, cells=None, heavy=None, center: f
     p = None if params is None else np.ascontiguousarray(params, np.float32)
     c = None if cells is None else np.ascontiguousarray(cells, np.uint32)
     h = np.ascontiguousarray(np.zeros(0, np.uint64) if heavy is None else heavy, np.uint64)
+    # the library reads exactly these many elements from the host arrays
+    if p is not None and p.size != FSORT_MLP_PARAMS:
+        raise ValueError(f"params must hold {FSORT_MLP_PARAMS} values, not {p.size}")
+    if c is not None and c.shape != (FSORT_LEARN_CELLS + 1, 2):
+        raise ValueError(f"cells must have shape ({FSORT_LEARN_CELLS + 1}, 2), not {c.shape}")
+    if h.ndim != 1 or h.size > FSORT_LEARN_MAX_HEAVY:
+        raise ValueError(f"heavy must be 1-D with at most {FSORT_LEARN_MAX_HEAVY} keys")
     norm = np.array([center, half], np.float32)
     _check(load_library().fsort_learned_set_model(plan, None if p is None else p.ctypes.data,
                                                   None if c is None else c.ctypes.data,

@@ -82,3 +82,35 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_binding, "_lib", None)
     with pytest.raises(RuntimeError):
         _binding.load_library()
+
+
+def test_strided_arrays_are_refused_before_any_call():
+    """A strided view's address would be read as dense elements: the binding
+    refuses it (no library call is made)."""
+    import numpy as np
+    import torch
+    from paper_2605_10390_gb300 import _binding as b
+    a = np.arange(64, dtype=np.uint32)
+    t = torch.arange(64, dtype=torch.int32)
+    assert b._ptr(a) == a.ctypes.data and b._ptr(t) == t.data_ptr()
+    assert b._ptr(a[8:16]) == a[8:].ctypes.data  # a dense slice is fine
+    assert b._ptr(np.zeros((4, 3), np.uint32)) is not None
+    for bad in (a[::2], np.zeros((4, 3), np.uint32)[:, 1], t[::2], torch.zeros(4, 3)[:, 1]):
+        with pytest.raises(ValueError):
+            b._ptr(bad)
+    with pytest.raises(ValueError):  # through a public entry point: refused before the library is called
+        fs.fsort_sort_pairs(None, a[::2], None, key_bits=32, precision_bits=32)
+
+
+def test_model_arrays_of_the_wrong_shape_are_refused():
+    """fsort_learned_set_model reads fixed-size host arrays: the binding checks
+    their shapes before the library is called."""
+    import numpy as np
+    cells = np.zeros((fs.FSORT_LEARN_CELLS + 1, 2), np.uint32)
+    bad = [dict(params=np.zeros(fs.FSORT_MLP_PARAMS - 1, np.float32)),
+           dict(cells=cells[:-1]),
+           dict(cells=cells.reshape(-1)),
+           dict(cells=cells, heavy=np.arange(fs.FSORT_LEARN_MAX_HEAVY + 1, dtype=np.uint64))]
+    for kw in bad:
+        with pytest.raises(ValueError):
+            fs.fsort_learned_set_model(None, **kw)
