@@ -234,7 +234,8 @@ typedef struct fsort_learned_stats {
 /* Number of MLP parameters and their order in a flat array: W1[64], b1[64],
  * W2[64][64] (row j feeds hidden unit j of layer 2), b2[64], W3[64], b3. */
 #define FSORT_MLP_PARAMS 4353
-#define FSORT_LEARN_CELLS 56320
+#define FSORT_LEARN_CELLS 56320    /* cells of the map table (which has one more, closing entry) */
+#define FSORT_LEARN_MAX_HEAVY 8192 /* most frequent keys a model keeps buckets of their own for */
 
 /* Fit the plan's model to keys[0..n) (64-bit keys, n <= max_n): sample, sort
  * the sample with the plain path, find the frequent keys, train, tabulate the

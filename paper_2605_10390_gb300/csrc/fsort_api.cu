@@ -16,6 +16,11 @@
 
 using namespace fsort;
 
+// The library's own sizes are the ones the header publishes.
+static_assert(kMlpParams == FSORT_MLP_PARAMS, "MLP parameter count");
+static_assert(kLearnCells == FSORT_LEARN_CELLS, "map table cells");
+static_assert(kLearnMaxHeavy == FSORT_LEARN_MAX_HEAVY, "frequent keys with buckets of their own");
+
 namespace {
 
 // Per-kernel timing: events recorded around launches, reported on demand.
