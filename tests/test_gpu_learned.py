@@ -284,3 +284,22 @@ def test_learned_beats_plain_on_the_mixture():
     print(f"learned {t_learned:.2f} ms  plain {t_plain:.2f} ms  ({t_plain / t_learned:.2f}x) imbalance "
           f"{st['imbalance']:.2f}")
     assert t_learned < t_plain
+
+
+def test_saved_model_resumes_in_a_new_plan(tmp_path):
+    """Checkpoint / resume: a model fitted once, saved to a file and installed
+    in a fresh plan, makes the same judged sort as the plan that fitted it."""
+    n = 1 << 20
+    keys = mixture(n, stream=10)
+    path = str(tmp_path / "map.fsm")
+    with learned_plan(n) as plan:
+        plan.learned_fit(torch.from_numpy(keys).cuda(), steps=300, seed=2)
+        fs.save_plan_model(plan.handle, path)
+        sort_and_check(plan, keys)
+        st0 = plan.learned_stats()
+    with learned_plan(n) as plan:
+        fs.load_plan_model(plan.handle, path)
+        assert plan.learned_stats()["fitted"] == 1
+        sort_and_check(plan, keys)
+        st1 = plan.learned_stats()
+    assert (st1["used"], st1["buckets"], st1["max_bucket"]) == (st0["used"], st0["buckets"], st0["max_bucket"])

@@ -323,7 +323,7 @@ def _pins_pass(lib):
     cases += [(_rand_keys(rng, 500, 32, 3), 32, 12), (_rand_keys(rng, 500, 64, 2), 64, 64)]
     for k, kb, pb in cases:
         idx = np.arange(k.size, dtype=np.uint32)
-        ko, vo = np.empty_like(k), np.empty_like(idx)
+        ko, vo = np.zeros_like(k), np.zeros_like(idx)
         if lib.oracle_sort(p(k), p(idx), p(ko), p(vo), k.size, kb, pb) != 0:
             return False
         order = _ref_order(k, kb, pb)
@@ -343,14 +343,14 @@ def _pins_pass(lib):
                 return False
     # scan against cumsum
     c = rng.integers(0, 1000, size=4096, dtype=np.uint64)
-    b = np.empty_like(c)
+    b = np.zeros_like(c)
     lib.oracle_exclusive_scan(p(c), c.size, p(b))
     if not np.array_equal(b, np.concatenate([[0], np.cumsum(c)[:-1]]).astype(np.uint64)):
         return False
     # one pass against numpy's stable argsort on the digit
     k = _rand_keys(rng, 3000, 32, 5)
     v = rng.integers(0, 2 ** 32, size=3000, dtype=np.uint64).astype(np.uint32)
-    ko, vo = np.empty_like(k), np.empty_like(v)
+    ko, vo = np.zeros_like(k), np.zeros_like(v)
     if lib.oracle_scatter_pass(p(k), p(v), p(ko), p(vo), k.size, 32, 5, 11) != 0:
         return False
     order = np.argsort((k.astype(np.uint64) >> np.uint64(5)) & np.uint64(2047), kind="stable")
@@ -359,7 +359,7 @@ def _pins_pass(lib):
     # expand against repeat (the last bin non-empty)
     c = rng.integers(0, 4, size=65536, dtype=np.uint64)
     c[-1] = 2
-    out = np.empty(int(c.sum()), dtype=np.uint16)
+    out = np.zeros(int(c.sum()), dtype=np.uint16)  # not np.empty: unwritten tail must not hold the answer
     if lib.oracle_expand(p(c), c.size, 16, p(out)) != 0:
         return False
     if not np.array_equal(out, np.repeat(np.arange(65536, dtype=np.uint16), c.astype(np.int64))):
