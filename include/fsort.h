@@ -13,10 +13,16 @@
  * The hot path (every step a CUDA kernel of this library):
  *   1. digit plan: least-significant-digit-first passes of d-bit digits over
  *      bits [key_bits - precision_bits, key_bits) (Sec. II);
- *   2. upfront histogram: every pass's digit counts from one read of the keys
- *      (the leaf level of the histogram tree of Sec. III-A/B, with counters
- *      whose width tapers with the size of what they count, Sec. III-D-1);
- *   3. exclusive scan of each histogram (the rank of Alg. 3 for every leaf);
+ *   2. digit histograms (the leaf level of the histogram tree of Sec.
+ *      III-A/B, with counters whose width tapers with the size of what they
+ *      count, Sec. III-D-1).  Sorts of up to 2^32 keys count each pass's
+ *      digits per tile, in one read of that pass's input just before it (the
+ *      first read also marks the passes whose digit is the same for every key);
+ *      larger sorts, and plans with FSORT_FLAG_CHAINED_SCATTER, count every
+ *      pass's digits in one upfront read of the keys;
+ *   3. exclusive scan of each histogram (the rank of Alg. 3 for every leaf):
+ *      per tile from the table of tile counts, or chained between tiles by
+ *      decoupled look-back;
  *   4. one stable scatter per pass (Sec. II), skipped on the device when a
  *      pass's digit is the same for every key;
  *   5. keys-only 16-bit sorts at full precision instead rebuild the output from
@@ -117,7 +123,9 @@ FSORT_API fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan
 FSORT_API fsort_status fsort_plan_destroy(fsort_plan* plan);
 
 /* Wait for all work enqueued by this plan, then return and clear the latched
- * device status (FSORT_OK, FSORT_ERR_TIMEOUT or FSORT_ERR_CUDA). */
+ * device status: FSORT_OK, FSORT_ERR_TIMEOUT (a bounded wait gave up),
+ * FSORT_ERR_INTERNAL (another device check failed; fsort_plan_device_flags
+ * gives the bits) or FSORT_ERR_CUDA. */
 FSORT_API fsort_status fsort_plan_sync(fsort_plan* plan);
 
 /* Describe the schedule of a sort of n keys (no work is enqueued). */
