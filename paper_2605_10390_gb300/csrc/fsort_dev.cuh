@@ -58,7 +58,7 @@ struct Schedule {
 // (input == output): alternate scratch/input; odd k ends in the scratch buffer
 // and needs the copy back.  Out of place: count backwards from the output so
 // the last active pass writes it; k == 0 copies.
-__device__ inline void route_passes(const int* trivial, int passes, int in_place, Schedule* sched) {
+__host__ __device__ inline void route_passes(const int* trivial, int passes, int in_place, Schedule* sched) {
   int k = 0;
   for (int j = 0; j < passes; ++j) k += trivial[j] ? 0 : 1;
   int cur = kBufIn, idx = 0;
