@@ -177,6 +177,11 @@ typedef struct fsort_batch_config {
   int32_t reserved[2];
 } fsort_batch_config;
 
+/* Sort count segments (host array of descriptors; the keys and values are on
+ * the device).  A segment of n == 0 is skipped.  A broken requirement returns
+ * FSORT_ERR_INVALID_ARG and enqueues nothing.  With FSORT_FLAG_GRAPH and a
+ * non-default stream, the first batch of a shape is captured as a CUDA graph
+ * and later batches of that shape replay it. */
 FSORT_API fsort_status fsort_sort_batch(fsort_plan* plan, const fsort_segment* segments, uint32_t count, int key_bits,
                                         int precision_bits, void* stream);
 
@@ -245,9 +250,11 @@ typedef struct fsort_learned_stats {
 #define FSORT_LEARN_CELLS 56320    /* cells of the map table (which has one more, closing entry) */
 #define FSORT_LEARN_MAX_HEAVY 8192 /* most frequent keys a model keeps buckets of their own for */
 
-/* Fit the plan's model to keys[0..n) (64-bit keys, n <= max_n): sample, sort
- * the sample with the plain path, find the frequent keys, train, tabulate the
- * map.  Stream-ordered (no host synchronisation); requires FSORT_FLAG_LEARNED. */
+/* Fit the plan's model to keys[0..n) (64-bit keys, device, 16-byte aligned,
+ * 1 <= n <= max_n): sample, sort the sample with the plain path, find the
+ * frequent keys, train, tabulate the map.  opts may be NULL (all defaults).
+ * Stream-ordered (no host synchronisation).  FSORT_ERR_INVALID_ARG: a plan
+ * without FSORT_FLAG_LEARNED, bad keys or n, or options beyond their limits. */
 FSORT_API fsort_status fsort_learned_fit(fsort_plan* plan, const void* keys, uint64_t n,
                                          const fsort_learned_opts* opts, void* stream);
 
@@ -275,7 +282,8 @@ FSORT_API fsort_status fsort_learned_set_model(fsort_plan* plan, const float* pa
                                                void* stream);
 
 /* ids[i] = bucket id of keys[i] under the fitted map, with the B that a sort
- * of n keys uses (device pointers; uint32_t ids). */
+ * of n keys uses (device pointers: 64-bit keys, uint32_t ids; n < 2^32).
+ * FSORT_ERR_INVALID_ARG without a fitted or installed model. */
 FSORT_API fsort_status fsort_learned_bucket_ids(fsort_plan* plan, const void* keys, uint64_t n, uint32_t* ids,
                                                 void* stream);
 
@@ -345,6 +353,11 @@ typedef struct fsort_serve_stats {
   double keys_per_s;                      /* keys_completed / span_s */
 } fsort_serve_stats;
 
+/* Create a server on the current device: one device arena of hbm_budget_bytes
+ * (rounded up to 256 bytes), and per lane a plan for max_request_keys keys, a
+ * stream and a worker thread.  FSORT_ERR_INVALID_ARG for a bad desc,
+ * FSORT_ERR_OOM when the arena cannot be allocated; *out is set only on
+ * FSORT_OK. */
 FSORT_API fsort_status fsort_serve_create(const fsort_serve_desc* desc, fsort_server** out);
 /* Finishes every admitted and queued request, then frees the server. */
 FSORT_API fsort_status fsort_serve_destroy(fsort_server* server);
@@ -358,6 +371,7 @@ FSORT_API fsort_status fsort_serve_submit(fsort_server* server, const fsort_requ
 FSORT_API fsort_status fsort_serve_poll(fsort_server* server, uint64_t ticket, fsort_result* out);
 /* Like poll, but waits up to timeout_ms (negative: no limit). */
 FSORT_API fsort_status fsort_serve_wait(fsort_server* server, uint64_t ticket, double timeout_ms, fsort_result* out);
+/* Counters and latency statistics so far (does not wait for the device). */
 FSORT_API fsort_status fsort_serve_stats_get(fsort_server* server, fsort_serve_stats* out);
 /* Install the fitted model of `source` (a plan with FSORT_FLAG_LEARNED) on
  * every lane; call while no request runs. */
@@ -378,8 +392,13 @@ FSORT_API fsort_status fsort_serve_set_model(fsort_server* server, fsort_plan* s
  * a time.  The paper defines these on its histogram tree; the GPU keeps the
  * leaf level plus a prefix index rebuilt after each accumulation. */
 typedef struct fsort_hist fsort_hist;
+/* Allocate 2^precision_bits counters (zero) on the current device.
+ * FSORT_ERR_INVALID_ARG for bad widths, FSORT_ERR_UNSUPPORTED for
+ * precision_bits > 24, FSORT_ERR_OOM when the counters cannot be allocated. */
 FSORT_API fsort_status fsort_hist_create(int key_bits, int precision_bits, fsort_hist** out);
+/* Wait for the device, then free the object (NULL: no-op). */
 FSORT_API fsort_status fsort_hist_destroy(fsort_hist* hist);
+/* Zero the counts (stream-ordered); the total restarts at 0. */
 FSORT_API fsort_status fsort_hist_reset(fsort_hist* hist, void* stream);
 /* Add the counts of keys[0..n) (device). */
 FSORT_API fsort_status fsort_hist_accumulate(fsort_hist* hist, const void* keys, uint64_t n, void* stream);
@@ -505,7 +524,9 @@ FSORT_API fsort_status fsort_scatter_pass_noalloc(const void* keys_in, const uin
 /* Raw device flag bits behind the last FSORT_ERR_TIMEOUT / FSORT_ERR_INTERNAL
  * this plan reported (0 if none): 1 look-back wait timed out, 2 bulk-copy wait
  * timed out, 4 tile id beyond the grid, 8 look-back walk found no prefix at its
- * chunk's first tile, 16 scatter target outside the output. */
+ * chunk's first tile, 16 a tile skipped its output after a wait gave up, 32 a
+ * learned-path bucket exceeded the on-chip capacity, 64 a tile-offset table was
+ * incomplete (its scatter wrote nothing). */
 FSORT_API uint32_t fsort_plan_device_flags(const fsort_plan* plan);
 
 /* Human-readable name of a status code (static storage). */
