@@ -331,3 +331,22 @@ def test_repeated_sorts_reuse_plan_state(plans):
         fs.fsort_sort_pairs(plan.handle, dk, dv, key_bits=32, precision_bits=32 - rep * 5)
         plan.sync()
         assert np.array_equal(host(dk), wk) and np.array_equal(host(dv), wv)
+
+
+def test_allocation_failure_is_reported_and_the_device_stays_usable():
+    """A plan or a server whose device memory cannot exist (2^36 64-bit keys
+    with values need over 1 TB of scratch) returns FSORT_ERR_OOM from its one
+    allocation; nothing is left behind and the next plan sorts as usual."""
+    with pytest.raises(fs.FsortError) as e:
+        fs.fsort_plan_create(1 << 36, 64, has_values=True)
+    assert e.value.status == 2
+    with pytest.raises(fs.FsortError) as e:
+        fs.fsort_serve_create(1 << 20, 32, True, hbm_budget_bytes=1 << 41)
+    assert e.value.status == 2
+    keys = gen("uniform", 100_003, 32, stream=13)
+    want, _ = oracle.sort(keys, None, 32, 32)
+    with fs.Plan(keys.size, 32, has_values=False) as plan:
+        dk = dev(keys)
+        plan.sort(dk, None, precision_bits=32)
+        plan.sync()
+        assert np.array_equal(host(dk), want)
