@@ -155,3 +155,28 @@ def test_learned_serving_on_the_mixture():
             for t in tickets:
                 assert srv.wait(t)["status"] == 0
     check(reqs, outs, 64, 64)
+
+
+def test_a_full_queue_refuses_with_busy():
+    """One lane and room for one waiting request: the first request keeps the
+    lane busy (64 MB copied in from pageable memory), so of the two requests
+    submitted right after it at least one finds the queue full and gets
+    FSORT_ERR_BUSY (whichever way the lane's thread is timed).  Every accepted
+    request still completes with the oracle's result."""
+    kb = 32
+    src = [workloads.generate("uniform", 1 << 24, kb, seed=5, stream=0)]
+    src += [workloads.generate("gauss", 1000, kb, seed=5, stream=i) for i in (1, 2)]
+    bufs = [a.copy() for a in src]
+    accepted, busy = [], 0
+    with fs.Server(1 << 24, kb, False, lanes=1, max_queue=1) as srv:
+        for i, b in enumerate(bufs):
+            try:
+                accepted.append((i, srv.submit(b)))
+            except fs.FsortError as e:
+                assert e.status == 5, e  # FSORT_ERR_BUSY
+                busy += 1
+        results = [(i, srv.wait(t)) for i, t in accepted]
+    assert accepted[0][0] == 0 and busy >= 1
+    for i, r in results:
+        assert r["status"] == 0
+        assert np.array_equal(bufs[i], oracle.sort(src[i], None, kb, kb)[0]), i
