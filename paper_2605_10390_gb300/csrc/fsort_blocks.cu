@@ -37,18 +37,26 @@ namespace fsort {
 namespace {
 
 constexpr int kRadix = 256;
-constexpr int kCountThreads = 1024;
 constexpr int kScanThreads = 1024;
 
-// Scatter tiles: threads, keys per thread, CTAs per SM.
+// Scatter tiles: threads, keys per thread, CTAs per SM.  A tile's shared
+// memory is 8 bytes per key for 16-bit keys with values (records, values)
+// plus 17 KB; 23 keys per thread is the most two CTAs per SM can hold.
 template <typename K>
 struct TileShape;
 template <>
-struct TileShape<uint16_t> { static constexpr int kBlock = 512, kIpt = 18, kMinBlocks = 2; };
+struct TileShape<uint16_t> { static constexpr int kBlock = 512, kIpt = 22, kMinBlocks = 2; };
 template <>
-struct TileShape<uint32_t> { static constexpr int kBlock = 512, kIpt = 12, kMinBlocks = 2; };
+struct TileShape<uint32_t> { static constexpr int kBlock = 512, kIpt = 16, kMinBlocks = 2; };
 template <>
 struct TileShape<uint64_t> { static constexpr int kBlock = 512, kIpt = 8, kMinBlocks = 2; };
+
+// Buffer `sel` of a by-BufSel triple, selected without indexing the
+// parameter array (which would copy it to local memory).
+template <typename T>
+__device__ __forceinline__ T* pick(T* const (&b)[3], int sel) {
+  return sel == kBufIn ? b[0] : (sel == kBufAlt ? b[1] : b[2]);
+}
 
 // ------------------------------------------------------------------ KT1 ----
 // One digit (shift, mask) per launch.  CTA c walks the tiles of chunk c in
@@ -59,51 +67,67 @@ struct TileShape<uint64_t> { static constexpr int kBlock = 512, kIpt = 8, kMinBl
 // orand[0] |= k and orand[1] &= k: a pass is trivial (all keys share its
 // digit) exactly when the two agree on the digit's bits, so the schedule needs
 // no histogram of the other passes.  The chunk streams through kCountStages
-// shared-memory buffers of kStepTiles tiles each, filled by bulk copies while
-// earlier steps are counted.
-constexpr int kStepTiles = 2;
-constexpr int kCountStages = 3;
+// shared-memory buffers of one tile each, filled by bulk copies while earlier
+// tiles are counted.  Each thread counts kCountVecs 16-byte vectors of a full
+// tile, so the count CTA has tile / (16-byte vector keys * kCountVecs) threads.
+constexpr int kCountStages = 4;
+constexpr int kCountVecs = 2;
 
-// Count CTAs per SM: two for 16-bit keys (3 x 32 KB of buffers each), one for
+// Count CTAs per SM: two for 16-bit keys (4 x 22 KB of buffers each), one for
 // wider keys.
 template <typename K>
 __host__ __device__ constexpr int count_ctas_per_sm() { return sizeof(K) == 2 ? 2 : 1; }
 template <typename K>
-__host__ __device__ constexpr uint32_t count_step_keys() {
-  return uint32_t(kStepTiles) * TileShape<K>::kBlock * TileShape<K>::kIpt;
+__host__ __device__ constexpr uint32_t count_tile_keys() {
+  return uint32_t(TileShape<K>::kBlock) * TileShape<K>::kIpt;
+}
+template <typename K>
+__host__ __device__ constexpr int count_threads() {
+  return int(count_tile_keys<K>() / (16 / sizeof(K)) / kCountVecs);
 }
 template <typename K>
 __host__ __device__ constexpr size_t count_smem_bytes() {
-  return size_t(kCountStages) * count_step_keys<K>() * sizeof(K);
+  return size_t(kCountStages) * count_tile_keys<K>() * sizeof(K);
+}
+
+// Key e of a 16-byte vector, by shifts (no address taken, so the vector stays
+// in registers).
+template <typename K>
+__device__ __forceinline__ K vec_key(const uint4& q, int e) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  if (sizeof(K) == 2) return K((w[e >> 1] >> ((e & 1) * 16)) & 0xFFFFu);
+  if (sizeof(K) == 4) return K(w[e]);
+  return K(uint64_t(w[2 * e]) | (uint64_t(w[2 * e + 1]) << 32));
 }
 
 template <typename K, bool kOrAnd>
-__global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_count_kernel(TileCountArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];  // [kCountStages][step keys]
-  __shared__ uint32_t s_tile[2][kStepTiles][kRadix];  // the step's tiles; steps alternate between two sets
-  __shared__ uint64_t s_bar[kCountStages];
-  __shared__ uint32_t s_fail[2];  // by step parity: a step reads only its own flag after its barrier
-  constexpr uint32_t kStepKeys = count_step_keys<K>();
+__global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) tile_count_kernel(TileCountArgs a) {
+  constexpr int kThreads = count_threads<K>();
+  constexpr uint32_t kTileKeys = count_tile_keys<K>();
   constexpr uint32_t kVec = 16 / sizeof(K);
-  static_assert(kStepTiles == 2, "a key's tile within the step is one comparison");
+  static_assert(kThreads >= kRadix && kThreads % 32 == 0 && kThreads <= 1024, "one thread per digit");
+  static_assert(uint32_t(kThreads) * kVec * kCountVecs == kTileKeys, "threads cover a tile exactly");
+  extern __shared__ __align__(128) unsigned char smem[];  // [kCountStages][tile keys]
+  __shared__ uint32_t s_tile[2][kRadix];  // a tile's counts; tiles alternate between two sets
+  __shared__ uint64_t s_bar[kCountStages];
+  __shared__ uint32_t s_fail[2];  // by tile parity: a tile reads only its own flag after its barrier
   K* buf = reinterpret_cast<K*>(smem);
   const K* keys;
   if (a.sched) {
     const PassDesc pd = a.sched->pass[a.pass];
     if (!pd.active) return;
-    keys = static_cast<const K*>(a.keys[pd.src]);
+    keys = static_cast<const K*>(pick(a.keys, pd.src));
   } else {
     keys = static_cast<const K*>(a.keys[kBufIn]);
   }
   const int tid = threadIdx.x;
   const uint32_t t_begin = blockIdx.x * a.chunk_tiles;
   const uint32_t t_end = (t_begin + a.chunk_tiles < a.tiles) ? t_begin + a.chunk_tiles : a.tiles;
-  const uint64_t k_end = (uint64_t(t_end) * a.tile < a.n) ? uint64_t(t_end) * a.tile : a.n;
-  const uint32_t steps = (t_end - t_begin + kStepTiles - 1) / kStepTiles;
-  // step s covers keys [e0, e1); its body of whole 16-byte vectors is copied in bulk
+  const uint32_t steps = t_end - t_begin;
+  // step s counts tile t_begin + s: keys [e0, e1); its body of whole 16-byte vectors is copied in bulk
   auto step_range = [&](uint32_t st, uint64_t& e0, uint64_t& e1) {
-    e0 = uint64_t(t_begin + st * kStepTiles) * a.tile;
-    e1 = (e0 + uint64_t(kStepTiles) * a.tile < k_end) ? e0 + uint64_t(kStepTiles) * a.tile : k_end;
+    e0 = uint64_t(t_begin + st) * kTileKeys;
+    e1 = (e0 + kTileKeys < a.n) ? e0 + kTileKeys : a.n;
   };
   auto issue = [&](uint32_t st) {  // thread 0 only
     uint64_t e0, e1;
@@ -111,7 +135,7 @@ __global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_co
     const uint32_t bytes = uint32_t((e1 - e0) * sizeof(K)) & ~15u;
     uint64_t* bar = &s_bar[st % kCountStages];
     mbar_arrive_expect_tx(bar, bytes);
-    if (bytes) bulk_copy_g2s(buf + size_t(st % kCountStages) * kStepKeys, keys + e0, bytes, bar);
+    if (bytes) bulk_copy_g2s(buf + size_t(st % kCountStages) * kTileKeys, keys + e0, bytes, bar);
   };
   if (tid == 0) {
     for (int i = 0; i < kCountStages; ++i) mbar_init(&s_bar[i], 1);
@@ -119,14 +143,14 @@ __global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_co
     s_fail[0] = s_fail[1] = 0;
     for (uint32_t st = 0; st < steps && st < uint32_t(kCountStages); ++st) issue(st);
   }
-  for (int i = tid; i < 2 * kStepTiles * kRadix; i += kCountThreads) (&s_tile[0][0][0])[i] = 0;
+  for (int i = tid; i < 2 * kRadix; i += kThreads) (&s_tile[0][0])[i] = 0;
   __syncthreads();
 
   const uint32_t shift = a.shift, mask = a.mask;
   uint64_t k_or = 0, k_and = ~0ull;  // this thread's keys folded
   uint32_t set = 0;
-  auto count_key = [&](K k, uint32_t slot) {
-    atomicAdd(&s_tile[set][slot][dig(k, shift, mask)], 1u);
+  auto count_key = [&](K k) {
+    atomicAdd(&s_tile[set][dig(k, shift, mask)], 1u);
     if (kOrAnd) {
       k_or |= uint64_t(k);
       k_and &= uint64_t(k);
@@ -139,29 +163,35 @@ __global__ void __launch_bounds__(kCountThreads, count_ctas_per_sm<K>()) tile_co
     const uint32_t keys_n = uint32_t(e1 - e0);
     const uint32_t body = (keys_n * uint32_t(sizeof(K)) & ~15u) / sizeof(K);
     if (!mbar_wait_bounded(&s_bar[st % kCountStages], (st / kCountStages) & 1u)) s_fail[st & 1u] = 1;
-    const K* b = buf + size_t(st % kCountStages) * kStepKeys;
-    const uint4* bv = reinterpret_cast<const uint4*>(b);
-    for (uint32_t v = tid; v < body / kVec; v += kCountThreads) {
-      const uint4 q = bv[v];
-      const uint32_t slot = (v * kVec >= a.tile) ? 1u : 0u;  // vectors never straddle tiles
-      const K* kk = reinterpret_cast<const K*>(&q);
+    const uint4* bv = reinterpret_cast<const uint4*>(buf + size_t(st % kCountStages) * kTileKeys);
+    if (body == kTileKeys) {
 #pragma unroll
-      for (int e = 0; e < int(kVec); ++e) count_key(kk[e], slot);
+      for (int j = 0; j < kCountVecs; ++j) {
+        const uint4 q = bv[tid + j * kThreads];
+#pragma unroll
+        for (int e = 0; e < int(kVec); ++e) count_key(vec_key<K>(q, e));
+      }
+    } else {  // the last, short tile
+      for (uint32_t v = tid; v < body / kVec; v += kThreads) {
+        const uint4 q = bv[v];
+#pragma unroll
+        for (int e = 0; e < int(kVec); ++e) count_key(vec_key<K>(q, e));
+      }
+      for (uint32_t i = body + tid; i < keys_n; i += kThreads) count_key(keys[e0 + i]);  // ragged end
     }
-    for (uint32_t i = body + tid; i < keys_n; i += kCountThreads)  // ragged end of the keys
-      count_key(keys[e0 + i], i >= a.tile ? 1u : 0u);
     __syncthreads();
     if (s_fail[st & 1u]) {  // the table would be wrong: mark it so that no scatter uses it
       if (tid == 0) atomicOr(a.status, kDevTimeoutLoad | kDevBadTable);
+      // copies still in flight get a second bounded wait before this CTA exits
+      if (tid == 0)
+        for (uint32_t q = st; q < steps && q < st + kCountStages; ++q)
+          mbar_wait_bounded(&s_bar[q % kCountStages], (q / kCountStages) & 1u);
       return;
     }
-    if (tid < kRadix) {  // meanwhile the next step counts into the other set
-#pragma unroll
-      for (int j = 0; j < kStepTiles; ++j) {
-        if (t_begin + st * kStepTiles + j < t_end) a.tilerel[uint64_t(t_begin + st * kStepTiles + j) * kRadix + tid] = acc;
-        acc += s_tile[set][j][tid];
-        s_tile[set][j][tid] = 0;  // cleared before this thread reaches the next barrier, so before step st + 2 counts
-      }
+    if (tid < kRadix) {  // meanwhile the next tile counts into the other set
+      a.tilerel[uint64_t(t_begin + st) * kRadix + tid] = acc;
+      acc += s_tile[set][tid];
+      s_tile[set][tid] = 0;  // cleared before this thread reaches the next barrier, so before tile st + 2 counts
     }
     if (tid == 0 && st + kCountStages < steps) {  // every thread has read this buffer (barrier above)
       fence_proxy_async_smem();
@@ -251,16 +281,18 @@ struct TileSmem {
   static constexpr int kIpt = TileShape<K>::kIpt;
   static constexpr int kTile = kBlock * kIpt;
   static constexpr int kWarps = kBlock / 32;
-  // The staged keys, then (16-bit keys) records key | source slot << 16 over
+  // The staged keys, later (16-bit keys) records key | source slot << 16 over
   // the keys and source areas together, or (wider keys) the keys in digit
-  // order plus their 16-bit source slots.
+  // order plus their 16-bit source slots; the staged values; per-warp digit
+  // counters; per-warp digit-group tables (winner bytes, group masks); the
+  // tile's output offsets; scan scratch; the copy barrier.
   static constexpr size_t kKeys = 0;
   static constexpr size_t kSrc = kKeys + size_t(kTile) * sizeof(K);
   static constexpr size_t kVals_ = kSrc + size_t(kTile) * 2;
-  static constexpr size_t kMask = kVals_ + (kVals ? size_t(kTile) * 4 : 0);
-  static constexpr size_t kMaskWords = size_t(kWarps) * kRadix;  // peer masks
-  static constexpr size_t kWcnt = kMask + kMaskWords * 4;
-  static constexpr size_t kOff = kWcnt + size_t(kWarps) * kRadix * 4;
+  static constexpr size_t kWcnt = kVals_ + (kVals ? size_t(kTile) * 4 : 0);
+  static constexpr size_t kWin = kWcnt + size_t(kWarps) * kRadix * 4;
+  static constexpr size_t kGrp = kWin + size_t(kWarps) * kRadix;
+  static constexpr size_t kOff = kGrp + size_t(kWarps) * 32 * 4;
   static constexpr size_t kScan = kOff + kRadix * 4;
   static constexpr size_t kBar = kScan + 16 * 4;
   static constexpr size_t kBytes = kBar + 16;
@@ -283,13 +315,6 @@ struct KeyRegs<uint16_t, kIpt> {
   __device__ __forceinline__ uint16_t get(int i) const { return uint16_t((i & 1) ? (w[i >> 1] >> 16) : (w[i >> 1] & 0xFFFFu)); }
 };
 
-// Buffer `sel` of a by-BufSel triple, selected without indexing the
-// parameter array (which would copy it to local memory).
-template <typename T>
-__device__ __forceinline__ T* pick(T* const (&b)[3], int sel) {
-  return sel == kBufIn ? b[0] : (sel == kBufAlt ? b[1] : b[2]);
-}
-
 template <typename K, bool kVals>
 __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks)
     tile_scatter_kernel(const TileScatterArgs a) {
@@ -299,11 +324,11 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   constexpr int kTile = L::kTile;
   constexpr int kWarps = L::kWarps;
   static_assert(kTile <= 65536, "in-warp ranks and source positions are kept in 16 bits");
-  static_assert(L::kMask % 16 == 0, "16-byte clears");
+  static_assert(L::kVals_ % 16 == 0 && L::kWcnt % 16 == 0 && L::kGrp % 128 == 0,
+                "bulk-copy targets, 16-byte clears, one bank per group word");
   extern __shared__ __align__(1024) unsigned char smem[];
   K* s_keys = reinterpret_cast<K*>(smem + L::kKeys);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + L::kVals_);
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem + L::kMask);
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem + L::kWcnt);
   uint32_t* s_off = reinterpret_cast<uint32_t*>(smem + L::kOff);
   uint32_t* s_scan = reinterpret_cast<uint32_t*>(smem + L::kScan);
@@ -325,7 +350,8 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   const uint32_t tile_n = uint32_t((a.n - t0 < uint64_t(kTile)) ? (a.n - t0) : uint64_t(kTile));
 
   // 1. stage the tile: bulk copies for the 16-byte-aligned body, plain loads
-  // for a ragged end; meanwhile clear the peer masks and warp counters.
+  // for a ragged end; meanwhile clear the warp counters and read the tile's
+  // offsets from the table.
   const uint32_t kbody = (tile_n * uint32_t(sizeof(K))) & ~15u;
   const uint32_t vbody = kVals ? ((tile_n * 4u) & ~15u) : 0u;
   const K* kin = static_cast<const K*>(pick(a.keys, src));
@@ -338,8 +364,8 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
     if (vbody) bulk_copy_g2s(s_vals, vin + t0, vbody, s_bar);
   }
   {
-    uint4* z = reinterpret_cast<uint4*>(s_mask);
-    for (int i = tid; i < int((L::kMaskWords + size_t(kWarps) * kRadix) / 4); i += kBlock) z[i] = make_uint4(0, 0, 0, 0);
+    uint4* z = reinterpret_cast<uint4*>(s_wcnt);
+    for (int i = tid; i < kWarps * kRadix / 4; i += kBlock) z[i] = make_uint4(0, 0, 0, 0);
   }
   if (tid < kRadix)  // lands while the copy does
     s_off[tid] = a.chunkoff[uint64_t(tile / a.chunk_tiles) * kRadix + tid] + a.tilerel[uint64_t(tile) * kRadix + tid];
@@ -347,15 +373,19 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   if (kVals)
     for (uint32_t i = vbody / 4 + tid; i < tile_n; i += kBlock) s_vals[i] = vin[t0 + i];
   __syncthreads();  // the mbarrier's init is visible before anyone waits on it
-  if (!mbar_wait_bounded(s_bar, 0)) {  // staged data not known complete: write nothing
+  const bool landed = mbar_wait_bounded(s_bar, 0);
+  if (__syncthreads_or(!landed)) {
+    // Staged data not known complete: write nothing.  Give the copies still in
+    // flight a second bounded wait, so that none lands in shared memory after
+    // this CTA has exited and its space has gone to another CTA.
     if (tid == 0) atomicOr(a.status, kDevTimeoutLoad | kDevBadOutput);
+    if (!landed) mbar_wait_bounded(s_bar, 0);
     return;
   }
 
   // 2. each warp counts the digits of its strip (item i of lane l is the key
   // at wbase + i*32 + l); the keys stay in registers
   const uint32_t shift = a.shift, mask = a.mask;
-  uint32_t* wmask = s_mask + warp * kRadix;
   uint32_t* wcnt = s_wcnt + warp * kRadix;
   const int wbase = warp * 32 * kIpt;
   KeyRegs<K, kIpt> kr;
@@ -375,38 +405,46 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   // start inside the tile, modulo 2^32)
   {
     const int d = tid;
+    uint32_t c[kWarps];
     uint32_t run = 0;
     if (d < kRadix) {
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_wcnt[w * kRadix + d];
-        s_wcnt[w * kRadix + d] = run;
-        run += c;
+        c[w] = s_wcnt[w * kRadix + d];
+        run += c[w];
       }
     }
     const uint32_t ex = digit_excl_scan<kBlock>(run, s_scan);
     if (d < kRadix) {
+      uint32_t acc = ex;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) s_wcnt[w * kRadix + d] += ex;
+      for (int w = 0; w < kWarps; ++w) {
+        s_wcnt[w * kRadix + d] = acc;
+        acc += c[w];
+      }
       s_off[d] -= ex;
     }
   }
   __syncthreads();
 
   // 4. stable ranks, straight to the key's slot in digit order: per round of
-  // 32 keys each lane adds its lane bit to the warp's word of its digit (the
-  // word is then the lane's peer mask, as __match_any_sync would give); the
-  // lowest peer takes the group's slots from the warp's running position of
-  // the digit.  Locally skewed strips (presorted runs, constant digits) use
-  // the hardware match.any instead, which is fast when a round has few
-  // distinct digits (the choice changes speed only).
+  // 32 keys the lanes that share a digit form a group (digit_group: its
+  // winner and peer mask; the hardware match.any on locally skewed strips,
+  // where it is the faster one); the winner takes the group's slots from the warp's
+  // running position of the digit, and each lane's slot is the first one plus
+  // its peers below it.  16-bit keys are stored as one record
+  // key | source slot << 16 over the keys and source areas, wider keys in
+  // place plus a 16-bit source slot; values stay where they are and are
+  // gathered once, in the write-out.
   {
-    const uint32_t lt = lanemask_lt(), me = 1u << lane;
-    bool use_match;
+    const uint32_t lt = lanemask_lt();
+    bool skewed;
     {
       const uint32_t d0 = uint32_t(wbase + lane) < tile_n ? dig(kr.get(0), shift, mask) : 0xFFFFFFFFu;
-      use_match = __popc(__ballot_sync(0xffffffffu, d0 == __shfl_sync(0xffffffffu, d0, 0))) >= 16;
+      skewed = __popc(__ballot_sync(0xffffffffu, d0 == __shfl_sync(0xffffffffu, d0, 0))) >= 16;
     }
+    uint8_t* win = reinterpret_cast<uint8_t*>(smem + L::kWin) + warp * kRadix;
+    uint32_t* grp = reinterpret_cast<uint32_t*>(smem + L::kGrp) + warp * 32;
     uint32_t* s_rec32 = reinterpret_cast<uint32_t*>(smem + L::kKeys);
     uint16_t* s_src = reinterpret_cast<uint16_t*>(smem + L::kSrc);
 #pragma unroll
@@ -415,24 +453,13 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
       const bool valid = uint32_t(pos) < tile_n;
       const K k = kr.get(i);
       const uint32_t d = dig(k, shift, mask);
-      uint32_t peers;
-      if (use_match) {
-        peers = __match_any_sync(0xffffffffu, valid ? d : (0x100u + lane));  // invalid lanes match nobody
-        if (!valid) peers = 0;
-      } else {
-        if (valid) atomicAdd(&wmask[d], me);
-        __syncwarp();
-        peers = valid ? wmask[d] : 0u;
-        __syncwarp();
-        if (valid && (peers & lt) == 0) wmask[d] = 0;  // the word is zero again before the next round
-        __syncwarp();
-      }
-      const uint32_t below = __popc(peers & lt);
+      uint32_t w;
+      const uint32_t peers = digit_group_any(skewed, d, valid, win, grp, &w);
       uint32_t base = 0;
-      if (valid && below == 0) base = atomicAdd(&wcnt[d], uint32_t(__popc(peers)));  // the group's leader
-      base = __shfl_sync(0xffffffffu, base, valid ? (__ffs(peers) - 1) : lane);
+      if (valid && w == uint32_t(lane)) base = atomicAdd(&wcnt[d], uint32_t(__popc(peers)));
+      base = __shfl_sync(0xffffffffu, base, w);
       if (valid) {
-        const uint32_t p = base + below;
+        const uint32_t p = base + __popc(peers & lt);
         if (sizeof(K) == 2) {
           s_rec32[p] = uint32_t(k) | (uint32_t(pos) << 16);
         } else {
@@ -480,7 +507,7 @@ template <typename K, bool kOrAnd>
 cudaError_t launch_count_variant(const TileCountArgs& a, uint32_t grid, cudaStream_t stream) {
   static const cudaError_t attr = set_smem_attrs(tile_count_kernel<K, kOrAnd>, count_smem_bytes<K>(), false);
   if (attr != cudaSuccess) return attr;
-  tile_count_kernel<K, kOrAnd><<<grid, kCountThreads, count_smem_bytes<K>(), stream>>>(a);
+  tile_count_kernel<K, kOrAnd><<<grid, count_threads<K>(), count_smem_bytes<K>(), stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -508,7 +535,6 @@ TableGeom table_geometry(uint64_t n, int key_bits, int sms) {
   const int per_sm = key_bits == 16 ? count_ctas_per_sm<uint16_t>() : count_ctas_per_sm<uint64_t>();
   const uint32_t want = uint32_t(sms) * uint32_t(per_sm);  // one chunk per resident count CTA
   g.chunk_tiles = (g.tiles + want - 1) / want;
-  g.chunk_tiles = (g.chunk_tiles + kStepTiles - 1) / kStepTiles * kStepTiles;  // whole steps
   g.chunks = (g.tiles + g.chunk_tiles - 1) / g.chunk_tiles;
   return g;
 }

@@ -7,13 +7,12 @@
 //  1. A bulk async copy (cp.async.bulk + mbarrier) stages the tile's keys and
 //     values in shared memory.
 //  2. Stable rank within each warp's strip of the tile: for every round of 32
-//     keys, each lane adds its lane bit to a warp-private shared word of its
-//     digit; the word then holds exactly the __match_any_sync peer mask of the
-//     lane (lanes with the same digit).  The lowest peer adds the group size to
-//     the warp's digit counter and broadcasts the old value; a lane's rank is
-//     that value plus its peers below it.  (The hardware match.any instruction
-//     computes the same mask but measured 5-6x slower on uniform 8-bit digits
-//     on GB300.)
+//     keys, the lanes that share a digit form a group (the __match_any_sync
+//     peer mask, found through two small warp-private tables, see
+//     digit_group); the group's winner adds the group size to the warp's digit
+//     counter and broadcasts the old value; a lane's rank is that value plus
+//     its peers below it.  (The hardware match.any instruction computes the
+//     same mask but measured 6-7x slower on uniform 8-bit digits on GB300.)
 //  3. Warp counters -> per-warp exclusive prefixes and the tile's digit counts,
 //     published at once to the decoupled look-back (2-bit flag | 30-bit count,
 //     the tapered counter width of Sec. III-D-1: a chunk never holds 2^30 keys).
@@ -60,9 +59,13 @@ struct SmemLayout {
   static constexpr int kWarps = kBlock / 32;
   static constexpr size_t kKeys = 0;
   static constexpr size_t kVals_ = kKeys + size_t(kTile) * sizeof(K);
-  static constexpr size_t kMask = kVals_ + (kVals ? size_t(kTile) * 4 : 0);
-  static constexpr size_t kWcnt = kMask + 2 * size_t(kWarps) * kRadix * 4;  // masks double-buffered
-  static constexpr size_t kExcl = kWcnt + size_t(kWarps) * kRadix * 4;
+  // records in digit order: 16-bit keys packed with their source position
+  // (4 bytes), wider keys permuted in place plus a 16-bit source position
+  static constexpr size_t kRec = kVals_ + (kVals ? size_t(kTile) * 4 : 0);
+  static constexpr size_t kWcnt = kRec + (size_t(kTile) * (sizeof(K) == 2 ? 4 : 2) + 1023) / 1024 * 1024;
+  static constexpr size_t kWin = kWcnt + size_t(kWarps) * kRadix * 4;  // digit-group tables (rank_strip_grouped)
+  static constexpr size_t kGrp = kWin + size_t(kWarps) * kRadix;
+  static constexpr size_t kExcl = kGrp + size_t(kWarps) * 32 * 4;
   static constexpr size_t kCnt = kExcl + kRadix * 4;
   static constexpr size_t kOff = kCnt + kRadix * 4;  // 8-byte aligned: all above are multiples of 1 KB
   static constexpr size_t kScan = kOff + kRadix * 8;
@@ -165,12 +168,11 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   constexpr int kTile = L::kTile;
   constexpr int kWarps = L::kWarps;
   static_assert(kTile <= 65536, "in-warp ranks are kept in 16 bits");
-  static_assert(2 * kWarps * kRadix * 4 >= kTile * (sizeof(K) == 2 ? 4 : 2), "records fit the mask words");
   static_assert(sizeof(K) != 2 || kTile <= 65536, "packed records carry a 16-bit source position");
   extern __shared__ __align__(1024) unsigned char smem[];
   K* s_keys = reinterpret_cast<K*>(smem + L::kKeys);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + L::kVals_);
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem + L::kMask);
+  uint32_t* s_rec = reinterpret_cast<uint32_t*>(smem + L::kRec);
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem + L::kWcnt);
   uint32_t* s_excl = reinterpret_cast<uint32_t*>(smem + L::kExcl);
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + L::kCnt);
@@ -200,7 +202,6 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
     mbar_init(s_bar, 1);
     fence_mbar_init();
   }
-  for (int i = tid; i < 2 * kWarps * kRadix; i += kBlock) s_mask[i] = 0;
   for (int i = tid; i < kWarps * kRadix; i += kBlock) s_wcnt[i] = 0;
   __syncthreads();
 
@@ -261,21 +262,23 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   for (uint32_t i = kbody / sizeof(K) + tid; i < tile_n; i += kBlock) s_keys[i] = kin[t0 + i];
   if (kVals)
     for (uint32_t i = vbody / 4 + tid; i < tile_n; i += kBlock) s_vals[i] = vin[t0 + i];
-  if (!mbar_wait_bounded(s_bar, 0)) atomicOr(a.status, kDevTimeoutLoad);
+  // A copy that has not landed within the bound: the tile still ranks and
+  // publishes (so that later tiles do not wait on it) but writes nothing.
+  const bool landed = mbar_wait_bounded(s_bar, 0);
+  if (!landed) {
+    atomicOr(a.status, kDevTimeoutLoad);
+    s_tile[1] = 1;
+  }
   __syncthreads();
 
   // 2. stable in-warp ranks
   const uint32_t shift = a.shift, mask = a.mask;
   (void)lane;
-  // Peer-mask words alternate between two buffers by item parity: a word
-  // cleared by its group leader in item i is reused at item i + 2, after the
-  // warp barriers of item i + 1 have ordered the clear before the reuse.
-  uint32_t* wmask0 = s_mask + warp * kRadix;
-  uint32_t* wmask1 = s_mask + (kWarps + warp) * kRadix;
   uint32_t* wcnt = s_wcnt + warp * kRadix;
   const int wbase = warp * 32 * kIpt;
   Item<K> it[kIpt];
-  rank_strip<K, kIpt>(s_keys, tile_n, wbase, shift, mask, wmask0, wmask1, wcnt, it);
+  rank_strip_grouped<K, kIpt>(s_keys, tile_n, wbase, shift, mask, reinterpret_cast<uint8_t*>(smem + L::kWin) + warp * kRadix,
+                              reinterpret_cast<uint32_t*>(smem + L::kGrp) + warp * 32, wcnt, it);
   __syncthreads();
 
   // 3. per-digit: warp prefixes, tile count, publish, tile-exclusive prefix
@@ -304,12 +307,12 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   }
   __syncthreads();
 
-  // 4. permute into digit order in shared memory.  The peer-mask words are
-  // dead now; their space holds the sorted records: 16-bit keys packed with
+  // 4. permute into digit order in shared memory.  The record area holds the
+  // sorted records: 16-bit keys packed with
   // their source position, wider keys in place plus a 16-bit source position.
   // Values stay where they are and are gathered once, in the output loop.
-  uint32_t* s_rec32 = s_mask;
-  uint16_t* s_src16 = reinterpret_cast<uint16_t*>(s_mask);
+  uint32_t* s_rec32 = s_rec;
+  uint16_t* s_src16 = reinterpret_cast<uint16_t*>(s_rec);
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
     const int pos = wbase + i * 32 + lane;
@@ -338,6 +341,9 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   // tile writes nothing, so a partial prefix can never address past it.
   if (s_tile[1]) {
     if (tid == 0) atomicOr(a.status, kDevBadOutput);
+    // a copy that had not landed gets a second bounded wait, so that it cannot
+    // land in shared memory that another CTA has been given after this one exits
+    if (!landed) mbar_wait_bounded(s_bar, 0);
     return;
   }
 #pragma unroll 4
