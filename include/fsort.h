@@ -505,10 +505,14 @@ FSORT_API fsort_status fsort_plan_timing_report(fsort_plan* plan, fsort_kernel_t
  *   - n must not exceed FSORT_NOALLOC_MAX_KEYS; larger n returns
  *     FSORT_ERR_INVALID_ARG without doing anything.
  *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture.
- *   - The call is synchronous: it enqueues its kernels on `stream`, waits for
- *     them, and returns FSORT_ERR_TIMEOUT if a device-side wait gave up.
+ *     per device, with that device current) and keeps it for the life of the
+ *     process; after a device or primary-context reset (cudaDeviceReset) the
+ *     address is stale and calls are not supported.
+ *   - The call is synchronous: it enqueues its kernels and the read-back of
+ *     its status word on `stream`, waits for that stream (and for nothing
+ *     else), and returns FSORT_ERR_TIMEOUT if a device-side wait gave up.
+ *     Because it waits, it must not be called on a stream that is capturing
+ *     a CUDA graph.
  *   - All calls on one device share its array, which keeps the last call's
  *     contents (the call clears what must start at zero).  The library lets
  *     one call at a time per device use it: calls from several host threads
@@ -520,6 +524,21 @@ FSORT_API fsort_status fsort_plan_timing_report(fsort_plan* plan, fsort_kernel_t
 FSORT_API fsort_status fsort_scatter_pass_noalloc(const void* keys_in, const uint32_t* vals_in, void* keys_out,
                                                   uint32_t* vals_out, uint64_t n, int key_bits, int shift, int width,
                                                   void* stream);
+
+/* Failure-detection test hook, for tests of the error path only (no paper
+ * counterpart).  After this call, scatter tile `withhold_tile` of every
+ * chained-form scatter pass of this plan (FSORT_FLAG_CHAINED_SCATTER plans,
+ * sorts of more than 2^32 keys, batched and one-pass calls) never publishes
+ * its look-back words, so the tiles after it wait for a flag that nothing
+ * sets.  Each such wait gives up after `wait_limit_ns` nanoseconds of the
+ * device's global timer (0 restores the default bound of 2 s) and sets status
+ * bit 1; a wait that sees the bit set by another gives up at once, so the whole
+ * pass ends within about one bound.  The tiles that gave up write nothing, and
+ * the next fsort_plan_sync (or call) returns FSORT_ERR_TIMEOUT.  No wait is
+ * unbounded and nothing faults: the plan and the CUDA context stay usable.
+ * withhold_tile = 0xFFFFFFFF removes the hook.  Not stream-ordered: set it
+ * while no call of this plan is in flight. */
+FSORT_API fsort_status fsort_plan_set_fault_hook(fsort_plan* plan, uint32_t withhold_tile, uint64_t wait_limit_ns);
 
 /* Raw device flag bits behind the last FSORT_ERR_TIMEOUT / FSORT_ERR_INTERNAL
  * this plan reported (0 if none): 1 look-back wait timed out, 2 bulk-copy wait

@@ -146,6 +146,7 @@ def load_library():
             "fsort_plan_timing_report": ([vp, ctypes.POINTER(FsortKernelTime), ctypes.c_uint32,
                                           ctypes.POINTER(ctypes.c_uint32)], st),
             "fsort_plan_device_flags": ([vp], ctypes.c_uint32),
+            "fsort_plan_set_fault_hook": ([vp, ctypes.c_uint32, ctypes.c_uint64], st),
             "fsort_scatter_pass_noalloc": ([vp, vp, vp, vp, u64, i32, i32, i32, vp], st),
             "fsort_sort_batch": ([vp, ctypes.POINTER(FsortSegment), ctypes.c_uint32, i32, i32, vp], st),
             "fsort_batch_set_config": ([vp, ctypes.POINTER(FsortBatchConfig)], st),
@@ -276,6 +277,14 @@ def fsort_plan_sync(plan) -> None:
 
 def fsort_plan_device_flags(plan) -> int:
     return int(load_library().fsort_plan_device_flags(plan))
+
+
+def fsort_plan_set_fault_hook(plan, withhold_tile: int, wait_limit_ns: int = 0) -> None:
+    """Failure-detection test hook: chained-form scatter tile `withhold_tile`
+    never publishes its look-back words (0xFFFFFFFF removes the hook); device
+    waits of the plan give up after wait_limit_ns (0: the default bound)."""
+    _check(load_library().fsort_plan_set_fault_hook(plan, withhold_tile & 0xFFFFFFFF, int(wait_limit_ns)),
+           "fsort_plan_set_fault_hook")
 
 
 def fsort_plan_describe(plan, n: int, key_bits: int, precision_bits: int, has_values: bool) -> dict:

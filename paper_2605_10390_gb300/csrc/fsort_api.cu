@@ -116,6 +116,8 @@ struct fsort_plan {
   cudaEvent_t done = nullptr;
   bool pending = false;
   uint32_t last_device_flags = 0;  // raw bits of the last latched device error
+  uint32_t withhold_tile = 0xFFFFFFFFu;  // failure-detection test hook (fsort_plan_set_fault_hook)
+  uint64_t wait_limit_ns = 0;            // 0: the kernels' default bound
 
   // batched sorts (max_segments > 0)
   uint32_t max_segments = 0;
@@ -387,6 +389,8 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
     a.pass = j;
     a.tiles_per_chunk = uint32_t(p->chunk_keys / p->tile);
     a.status = p->status;
+    a.withhold_tile = p->withhold_tile;
+    a.wait_limit_ns = p->wait_limit_ns;
     e = launch_onesweep(a, key_bits, has_vals, s);
     tm.mark(FSORT_KERNEL_SCATTER, j);
   }
@@ -595,6 +599,8 @@ cudaError_t enqueue_batch(fsort_plan* p, const BatchShape& b, int key_bits, int 
       a.tile_seg = p->d_tile_seg;
       a.passes = uint32_t(plan.passes);
       a.total_tiles = b.total_tiles;
+      a.withhold_tile = p->withhold_tile;
+      a.wait_limit_ns = p->wait_limit_ns;
       e = launch_onesweep(a, key_bits, b.has_vals, s);
     }
     if (e == cudaSuccess && (plan.passes & 1))
@@ -1189,6 +1195,8 @@ fsort_status fsort_scatter_pass(fsort_plan* plan, const void* keys_in, const uin
     a.pass = 0;
     a.tiles_per_chunk = uint32_t(plan->chunk_keys / plan->tile);
     a.status = plan->status;
+    a.withhold_tile = plan->withhold_tile;
+    a.wait_limit_ns = plan->wait_limit_ns;
     e = launch_onesweep(a, key_bits, vals_in != nullptr, s);
   }
   if (e != cudaSuccess) return from_cuda(e);
@@ -1393,6 +1401,13 @@ fsort_status fsort_mlp_grad(const void* w_bf16, const float* x, const float* y, 
       (loss && !aligned_to(loss, 4)))
     return FSORT_ERR_INVALID_ARG;
   return from_cuda(launch_mlp_grad(w_bf16, x, y, m, grads, loss, static_cast<cudaStream_t>(stream)));
+}
+
+fsort_status fsort_plan_set_fault_hook(fsort_plan* plan, uint32_t withhold_tile, uint64_t wait_limit_ns) {
+  if (!plan) return FSORT_ERR_INVALID_ARG;
+  plan->withhold_tile = withhold_tile;
+  plan->wait_limit_ns = wait_limit_ns;
+  return FSORT_OK;
 }
 
 fsort_status fsort_plan_set_timing(fsort_plan* plan, int enable) {

@@ -88,6 +88,13 @@ struct OnesweepArgs {
   const uint32_t* tile_seg;
   uint32_t passes;
   uint32_t total_tiles;  // segmented mode: tiles over all segments (the grid)
+  // Failure-detection test hook: tile `withhold_tile` never publishes its
+  // look-back words (0xFFFFFFFF: none).  Look-back waits give up after
+  // wait_limit_ns (0: kWaitLimitNs), and at once when another wait of this
+  // plan already gave up.
+  uint32_t withhold_tile = 0xFFFFFFFFu;
+  uint32_t pad3 = 0;
+  uint64_t wait_limit_ns = 0;
 };
 cudaError_t launch_onesweep(const OnesweepArgs& args, int key_bits, bool has_vals, cudaStream_t stream);
 

@@ -15,7 +15,9 @@
 // that loads the library holds it until the process exits.  Host code must
 // not pass the array's name to a kernel: in host code it is a host-side
 // stand-in, not a device address.  The device address is looked up once per
-// device with cudaGetSymbolAddress, with that device current.
+// device with cudaGetSymbolAddress, with that device current.  A device reset
+// (cudaDeviceReset, or a reset of the primary context) reloads the module and
+// invalidates the cached address: calls after one are not supported.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -141,10 +143,12 @@ extern "C" fsort_status fsort_scatter_pass_noalloc(const void* keys_in, const ui
     e = launch_onesweep(a, key_bits, vals_in != nullptr, s);
   }
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FSORT_ERR_OOM : FSORT_ERR_CUDA;
-  // Synchronous: wait for the pass, then report a device-side error.
-  if (cudaStreamSynchronize(s) != cudaSuccess) return FSORT_ERR_CUDA;
+  // Synchronous: read the status word back on the caller's stream (no
+  // legacy-stream copy, which would wait for every blocking stream of the
+  // device), wait for the stream, then report a device-side error.
   uint32_t flags = 0;
-  if (cudaMemcpy(&flags, status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return FSORT_ERR_CUDA;
+  if (cudaMemcpyAsync(&flags, status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return FSORT_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FSORT_ERR_CUDA;
   if (flags & (kDevTimeoutLookback | kDevTimeoutLoad)) return FSORT_ERR_TIMEOUT;
   return flags ? FSORT_ERR_INTERNAL : FSORT_OK;
 }

@@ -85,6 +85,8 @@ __device__ __forceinline__ bool digit_offset(const OnesweepArgs& a, uint32_t til
                                              uint32_t tile_excl, uint32_t* lb, unsigned long long* s_off) {
   bool ok = true;
   uint32_t excl = 0;
+  const uint64_t limit = a.wait_limit_ns ? a.wait_limit_ns : kWaitLimitNs;
+  const bool publish = tile != a.withhold_tile;
   if (!first_in_chunk) {
     uint32_t t = tile;  // tiles [chunk_first, t) are still to the left
     uint64_t t_wait = 0;
@@ -120,8 +122,11 @@ __device__ __forceinline__ bool digit_offset(const OnesweepArgs& a, uint32_t til
       if (used < w) {  // blocked on an unpublished predecessor
         if (t_wait == 0) {
           t_wait = global_timer_ns();
-        } else if (global_timer_ns() - t_wait > kWaitLimitNs) {
+        } else if (global_timer_ns() - t_wait > limit) {
           atomicOr(a.status, kDevTimeoutLookback);
+          ok = false;
+          break;
+        } else if (ld_relaxed_gpu(a.status) & kDevTimeoutLookback) {  // another wait gave up: so do we
           ok = false;
           break;
         }
@@ -130,7 +135,7 @@ __device__ __forceinline__ bool digit_offset(const OnesweepArgs& a, uint32_t til
         t_wait = 0;
       }
     }
-    st_relaxed_gpu(lb + d, kFlagPrefix | (excl + cnt));
+    if (publish) st_relaxed_gpu(lb + d, kFlagPrefix | (excl + cnt));
   }
   // 64-bit base of this digit in this chunk.
   unsigned long long base;
@@ -141,8 +146,12 @@ __device__ __forceinline__ bool digit_offset(const OnesweepArgs& a, uint32_t til
     if (!ld_acquire_gpu(flag)) {
       const uint64_t t_wait = global_timer_ns();
       while (!ld_acquire_gpu(flag)) {
-        if (global_timer_ns() - t_wait > kWaitLimitNs) {
+        if (global_timer_ns() - t_wait > limit) {
           atomicOr(a.status, kDevTimeoutLookback);
+          ok = false;
+          break;
+        }
+        if (ld_relaxed_gpu(a.status) & kDevTimeoutLookback) {
           ok = false;
           break;
         }
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
         run += c;
       }
       s_cnt[d] = run;
-      st_relaxed_gpu(lb + d, (first_in_chunk ? kFlagPrefix : kFlagAggregate) | run);
+      if (tile != a.withhold_tile) st_relaxed_gpu(lb + d, (first_in_chunk ? kFlagPrefix : kFlagAggregate) | run);
     }
     const uint32_t ex = digit_excl_scan<kBlock>(run, s_scan);
     if (d < kRadix) {

@@ -1,29 +1,36 @@
 """Parity at the full sizes of the measured workloads, in the launch
-configuration bench.py times, through properties that fix the result at any
-size (the oracle cannot sort billions of keys in a test):
+configuration bench.py times.
 
+Element by element against the oracle, in slab mode (oracle/slab.py): the
+input is regenerated on the host from the counter-based generator, the keys of
+chosen slab-key ranges are collected in input order, and the oracle's stable
+sort of each slab must equal the GPU output over the slab's contiguous range.
+- 32 GB, 2^32 uint64 keys at 16, 32 and 64 bits, uniform and Zipf on the top
+  16 bits: slabs of the top 16 bits -- the first (for Zipf the head bucket,
+  13.7 % of all keys), the last, and seeded ones in between;
+- the learned workload (2^30 uint64 mixture keys at 64 bits): slabs of the full
+  key -- the lowest and highest percent, one in the middle, and the most
+  frequent key.
+Before the oracle runs, properties that fix the result at any size are checked
+on the device as fast pre-checks (order, permutation, sampled stability).
+
+Through properties alone (exact at any size, no oracle needed):
 - 32 GB, 2^34 uint16 keys at 16-bit precision (the expand path): the output is
   non-decreasing and has exactly the input's 65,536-bin histogram, so it is the
-  sorted multiset;
-- 32 GB, 2^32 uint64 keys at 16, 32 and 64 bits: the output's sort keys
-  s(k) = k >> (64 - p) are non-decreasing, the output is a permutation of the
-  input (order-independent hash sums), and for sampled s-values v the block of
-  keys with s = v sits at the position the definition fixes (the count of keys
-  with s < v) and holds them in input order (stability);
+  sorted multiset (complete for keys only at full width);
 - the batched workload (4,096 uint32 key + index sorts, 2^10..2^24 keys each,
   autotuned, CUDA graph captured and replayed): in every segment the values
   are indices into its input, the keys follow them, and (key, index) strictly
-  increases, which makes the result the unique stable sort;
-- the learned workload (2^30 uint64 mixture keys at 64 bits): the learned
-  path's output equals the plain path's bit for bit, and sampled positions
-  hold the value the definition of the sorted multiset gives.
+  increases, which makes the result the unique stable sort.
 
-Each property check runs in torch on the device, chunk by chunk; none of it
-uses this library's kernels.
+The device-side property checks use torch, never this library's kernels.
 """
+import os
+
 import numpy as np
 import pytest
 
+import oracle.slab as slab
 import workloads
 
 torch = pytest.importorskip("torch")
@@ -65,6 +72,31 @@ def device_keys(dist, n, kb, stream_id, dtype):
     return keys
 
 
+WORKERS = max(1, min(16, os.cpu_count() or 1))
+HOST_CHUNK = 1 << 24  # 128 MB of 64-bit keys per worker at a time
+
+
+def host_slabs(dist, n, kb, stream_id, slab_bits, ranges):
+    """Slab-mode gather over the host regeneration of the workload that
+    device_keys(dist, n, kb, stream_id, ...) writes on the device."""
+    workloads.params_for(dist, n, kb, 0, stream_id)  # build the tables once, before the threads
+
+    def chunk(c):
+        st = c * HOST_CHUNK
+        return workloads.generate(dist, min(HOST_CHUNK, n - st), kb, seed=0, stream=stream_id, start=st, n_total=n)
+
+    return slab.slab_gather(chunk, (n + HOST_CHUNK - 1) // HOST_CHUNK, kb, slab_bits, ranges, workers=WORKERS)
+
+
+def assert_slabs(out_dev, gathered, kb, p, what):
+    """The device output over each slab's range equals the oracle's sort of the slab."""
+    for first, keys in gathered:
+        got = out_dev[first:first + keys.size].cpu().numpy().view(keys.dtype)
+        want = slab.slab_expected(keys, kb, p)
+        assert np.array_equal(got, want), (what, p, first, keys.size)
+        del got, want
+
+
 @pytest.mark.parametrize("dist", ["uniform", "zipf1.1"])
 def test_2pow34_uint16_expand_is_the_sorted_multiset(dist):
     n = 1 << 34
@@ -93,41 +125,35 @@ def test_2pow34_uint16_expand_is_the_sorted_multiset(dist):
 
 
 @pytest.mark.parametrize("dist", ["uniform", "zipf1.1"])
-def test_2pow32_uint64_every_precision(dist):
+def test_2pow32_uint64_every_precision_against_oracle_slabs(dist):
     n = 1 << 32
+    # slabs of the top 16 bits: first (for Zipf the head bucket), last, and seeded ones between
+    width = 1 if dist == "zipf1.1" else 64
+    rng = np.random.default_rng(21)
+    mids = sorted(int(x) for x in rng.integers(1, 65535 - 64, 2))
+    ranges = [(0, width), (65536 - 64, None)] + [(m, m + 64) for m in mids]
+    gathered = host_slabs(dist, n, 64, 7, 16, ranges)
+    assert sum(k.size for _, k in gathered) > (n // 8 if dist == "zipf1.1" else n // 300)
     keys = device_keys(dist, n, 64, 7, torch.int64)
     out = torch.empty_like(keys)
     want = sum(mix_sums(keys[st:st + CHUNK]) for st in range(0, n, CHUNK))
-    rng = np.random.default_rng(11)
     with fs.Plan(n, 64, has_values=False) as plan:
         for p in (16, 32, 64):
             plan.sort_out(keys.view(torch.uint64), None, out.view(torch.uint64), None, precision_bits=p)
             plan.sync()
             torch.cuda.synchronize()
+            # fast pre-checks on the device: a permutation of the input, ordered on s(k)
             got = sum(mix_sums(out[st:st + CHUNK]) for st in range(0, n, CHUNK))
-            assert torch.equal(got, want), p  # a permutation of the input
+            assert torch.equal(got, want), p
             last = None
             for st in range(0, n, CHUNK):
                 s = s64(out[st:st + CHUNK], p)
                 assert bool((s[1:] >= s[:-1]).all()) and (last is None or int(s[0]) >= last), (p, st)
                 last = int(s[-1])
                 del s
-            if p == 64:
-                continue  # keys-only at full width: equal keys are indistinguishable
-            for i in rng.integers(0, n, 3).tolist():
-                v = int(s64(out[i:i + 1], p)[0])
-                below, block = 0, []
-                for st in range(0, n, CHUNK):
-                    s = s64(keys[st:st + CHUNK], p)
-                    below += int((s < v).sum())
-                    block.append(torch.masked_select(keys[st:st + CHUNK], s == v))
-                    del s
-                block = torch.cat(block)
-                assert below <= i < below + block.numel(), (p, i)
-                # the keys with s = v, in input order, at the position the definition fixes
-                assert torch.equal(out[below:below + block.numel()], block), (p, v)
-                del block
-    del keys, out
+            # element by element against the oracle, slab by slab
+            assert_slabs(out, gathered, 64, p, dist)
+    del keys, out, gathered
     free()
 
 
@@ -183,7 +209,7 @@ def test_batched_4096_sorts_full_size_graph_replay():
     free()
 
 
-def test_learned_2pow30_mixture_matches_plain_and_definition():
+def test_learned_2pow30_mixture_against_oracle_slabs():
     n = 1 << 30
     quant, hot, table = workloads.mixture_tables(0)
     t = [torch.from_numpy(a.view(np.int64)).cuda() for a in (table, quant, hot)]
@@ -203,12 +229,18 @@ def test_learned_2pow30_mixture_matches_plain_and_definition():
     with fs.Plan(n, 64, has_values=False) as pp:
         pp.sort(out_p.view(torch.uint64), precision_bits=64)
         pp.sync()
-    assert torch.equal(out_l, out_p)
-    del out_p
-    u = keys ^ SIGN
-    for i in np.random.default_rng(6).integers(0, n, 8).tolist() + [0, n - 1]:
-        v = int(out_l[i]) ^ SIGN
-        below = int((u < v).sum())
-        assert below <= i < below + int((u == v).sum()), i
-    del keys, out_l, u
+    assert torch.equal(out_l, out_p)  # fast pre-check against the plain path
+    del out_p, keys
+    free()
+    # slabs of the full key, from quantiles of the first chunk: the lowest and
+    # highest percent, one in the middle, and the most frequent key's slab
+    sample = np.sort(workloads.generate("mixture", 1 << 20, 64, seed=0, stream=9, n_total=n))
+    q = [int(sample[int(f * sample.size)]) for f in (0.01, 0.5, 0.51, 0.99)]
+    vals, counts = np.unique(sample, return_counts=True)
+    hot = int(vals[np.argmax(counts)])
+    ranges = [(0, q[0]), (q[1], q[2]), (q[3], None), (hot, hot + 1)]
+    gathered = host_slabs("mixture", n, 64, 9, 64, ranges)
+    assert gathered[3][1].size > n // 100  # the most frequent key's slab holds over 1 % of the keys
+    assert_slabs(out_l, gathered, 64, 64, "learned")
+    del out_l, gathered
     free()

@@ -51,8 +51,47 @@ def test_noalloc_matches_plan_based_pass_twice(key_bits, with_vals):
             assert torch.equal(got_k, ref_k), call
             if with_vals:
                 assert torch.equal(got_v, ref_v), call
+            # and both equal the oracle's pass on the same input
+            want_k, want_v = oracle.scatter_pass(keys, vals, key_bits, shift, width)
+            assert np.array_equal(got_k.cpu().numpy(), want_k), call
+            if with_vals:
+                assert np.array_equal(got_v.cpu().numpy(), want_v), call
     finally:
         plan.close()
+
+
+def test_noalloc_at_its_largest_size_with_64_bit_keys_and_values():
+    """n = FSORT_NOALLOC_MAX_KEYS with 64-bit keys: the look-back region of the
+    fixed scratch is completely full (one row per 4,096-key tile) and abuts the
+    histogram; the result must equal the plan-based pass bit for bit on two
+    calls in a row, and satisfy the definition of a stable pass (checked on the
+    device: digits non-decreasing, input positions increasing within a digit,
+    every key taken from its position)."""
+    n, kb, shift, width = fs.FSORT_NOALLOC_MAX_KEYS, 64, 56, 8
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    workloads.generate_device("uniform", keys.data_ptr(), n, kb, seed=1, stream=77,
+                              cuda_stream=torch.cuda.current_stream().cuda_stream)
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    with fs.Plan(n, kb, has_values=True) as plan:
+        ref_k, ref_v = torch.empty_like(keys), torch.empty_like(vals)
+        fs.fsort_scatter_pass(plan.handle, keys.view(torch.uint64), vals, ref_k.view(torch.uint64), ref_v,
+                              shift, width, key_bits=kb)
+        plan.sync()
+    got_k, got_v = torch.empty_like(keys), torch.empty_like(vals)
+    for _ in range(2):
+        got_k.zero_()
+        got_v.zero_()
+        fs.fsort_scatter_pass_noalloc(keys.view(torch.uint64), vals, got_k.view(torch.uint64), got_v, shift, width,
+                                      key_bits=kb)
+        torch.cuda.synchronize()
+        assert torch.equal(got_k, ref_k) and torch.equal(got_v, ref_v)
+    # the definition on the device: stable by the top byte, values are the input positions
+    d = (got_k >> 56) & 0xFF
+    assert bool((d[1:] >= d[:-1]).all())
+    same = d[1:] == d[:-1]
+    assert bool((got_v[1:][same] > got_v[:-1][same]).all())
+    assert torch.equal(keys[got_v.long()], got_k)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
