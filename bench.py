@@ -60,8 +60,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 32 GB arbitrary-precision configurations")
-    ap.add_argument("--only", choices=["secondary", "batched", "learned", "serving"],
-                    help="run one secondary section alone and print its JSON (profiling and debugging)")
+    ap.add_argument("--only", choices=["secondary", "expand", "batched", "learned", "serving"],
+                    help="run one secondary section alone and print its JSON (profiling and debugging); "
+                         "expand: the expand-path cases of the secondary section at --expand-log2n keys")
+    ap.add_argument("--expand-log2n", type=int, default=34, help="keys of the expand-path cases (log2)")
+    ap.add_argument("--reps", type=int, default=3, help="timed repetitions per case of --only sections")
     ap.add_argument("--learned-log2n", type=int, default=30, help="keys of the learned section (log2)")
     return ap.parse_args()
 
@@ -255,13 +258,15 @@ def cpu_baseline(seconds: float = 10.0, log2n: int = 24):
                       f"single-threaded C LSD counting sort on {os.cpu_count()} host cores (1 used)"}
 
 
-def run_secondary(fs, workloads, torch, stream, peak, reps: int = 3):
+def run_secondary(fs, workloads, torch, stream, peak, reps: int = 3, expand_log2n: int = 34, u64: bool = True):
     """The 32 GB arbitrary-precision configurations, keys only, out of place:
     2^34 uint16 keys at 16-bit precision (the expand path), and 2^32 uint64 keys
-    at 16, 32 and 64 bits, each uniform and Zipf s=1.1 on the top 16 bits."""
+    at 16, 32 and 64 bits, each uniform and Zipf s=1.1 on the top 16 bits.
+    expand_log2n and u64 shrink it for profiling (the expand cases alone)."""
     out = []
-    cases = [(16, 34, 16, d) for d in ("uniform", "zipf1.1")]
-    cases += [(64, 32, p, d) for p in (16, 32, 64) for d in ("uniform", "zipf1.1")]
+    cases = [(16, expand_log2n, 16, d) for d in ("uniform", "zipf1.1")]
+    if u64:
+        cases += [(64, 32, p, d) for p in (16, 32, 64) for d in ("uniform", "zipf1.1")]
     dtypes = {16: torch.uint16, 64: torch.uint64}
     cur = None
     for kb, log2n, p, dist in cases:
@@ -385,9 +390,14 @@ def run_batched(fs, workloads, torch, stream, peak, reps: int = 2):
     pplan.close()
     pms = float(np.median(times[1:]))
     alg = sum(4 * n + 4 * 2 * 8 * n for n in sizes)  # plain path's bytes: key read + 4 passes of keys+values
+    # the batched path's own algorithmic bytes: segments sorted on chip move their keys and
+    # values once in and once out (16 n); the others take the plain path's 68 n
+    cap = int(cfg.get("small_capacity", 0)) if isinstance(cfg, dict) else 0
+    balg = sum(16 * n if n <= cap else 68 * n for n in sizes)
     out.update({"batched_ms": bms, "batched_gkeys_per_s": total / bms / 1e6, "plain_ms": pms,
                 "plain_gkeys_per_s": total / pms / 1e6, "speedup": pms / bms, "autotuned": cfg,
-                "plain_path_algorithmic_bytes": alg, "plain_path_frac": alg / pms / 1e6 / peak})
+                "plain_path_algorithmic_bytes": alg, "plain_path_frac": alg / pms / 1e6 / peak,
+                "batched_algorithmic_bytes": balg, "batched_frac": balg / bms / 1e6 / peak})
     del keys, vals
     torch.cuda.empty_cache()
     return out
@@ -461,7 +471,9 @@ def run_learned(fs, workloads, torch, stream, peak, log2n: int = 30, reps: int =
                         f"10% Zipf s=1.3 over 65,536 hot keys",
             "learned_ms": lms, "plain_ms": pms, "learned_gkeys_per_s": n / lms / 1e6,
             "plain_gkeys_per_s": n / pms / 1e6, "speedup": pms / lms, "identical_output": same,
-            "fit_s": fit_s, "judge": {k: st[k] for k in ("used", "imbalance", "tau", "buckets", "max_bucket",
+            "fit_s": fit_s,
+            "break_even_sorts": (fit_s * 1e3 / (pms - lms)) if pms > lms else None,
+            "judge": {k: st[k] for k in ("used", "imbalance", "tau", "buckets", "max_bucket",
                                                          "limit", "heavy_keys")},
             "training": {k: st[k] for k in ("sample_keys", "train_keys", "steps", "loss_first", "loss_last")},
             "learned_kernel_ms": lkern, "plain_kernel_ms": pkern,
@@ -534,12 +546,44 @@ def run_serving(fs, workloads, torch, stream, requests: int = 48, lo: int = 16, 
     return {"workload": f"{requests} requests, uint64 keys-only 64-bit sorts of the mixture, sizes log-uniform "
                         f"2^{lo}..2^{hi} (total {sum(sizes)} keys), Poisson arrivals at {rate:.1f}/s "
                         f"(~{int(util * 100)}% of the calibrated service rate)",
-            "lanes": lanes, "hbm_budget_bytes": budget, "p50_ms": rank(0.50), "p99_ms": rank(0.99),
+            "requests": requests, "lanes": lanes, "hbm_budget_bytes": budget, "p50_ms": rank(0.50), "p99_ms": rank(0.99),
             "mean_ms": float(np.mean(lat)), "max_ms": lat[-1], "keys_per_s": sum(sizes) / span, "span_s": span,
             "queue_ms_mean": float(np.mean([r["queue_ms"] for r in results.values()])),
             "batched_requests": sum(1 for r in results.values() if r["batched"]),
             "max_inflight": st["max_inflight"], "peak_bytes": st["peak_bytes"], "outputs_sorted": ok,
             "api": "fsort_serve_submit / fsort_serve_wait (pinned host buffers; copies in the latency)"}
+
+
+def summary(result: dict) -> dict:
+    """The headline and every secondary section in a few hundred characters,
+    placed last on the JSON line so that a reader that keeps only its tail
+    still has them."""
+    r = lambda x, d=3: None if x is None else round(float(x), d)
+    out = {"gkeys_per_s": r(result["value"], 2), "scatter_frac": r(result["roofline"]["frac"])}
+    sec = result.get("secondary") or []
+    if sec:
+        out["gb32"] = {f"{'u16e' if 'uint16' in c['workload'] else 'u64'}"
+                       f"{'' if 'uint16' in c['workload'] else '-p' + c['workload'].split('-bit')[0].split()[-1]}"
+                       f"-{'zipf' if 'zipf' in c['workload'] else 'unif'}": [r(c["gkeys_per_s"], 1), r(c["frac"])]
+                       for c in sec}
+    b = result.get("batched")
+    if b:
+        out["batched"] = {"ms": r(b["batched_ms"], 1), "speedup": r(b["speedup"], 2), "frac": r(b.get("batched_frac")),
+                          "cfg": b.get("autotuned")}
+    lr = result.get("learned")
+    if lr:
+        out["learned"] = {"ms": r(lr["learned_ms"], 2), "plain_ms": r(lr["plain_ms"], 2), "speedup": r(lr["speedup"], 2),
+                          "fit_s": r(lr["fit_s"], 2), "break_even": r(lr.get("break_even_sorts"), 1),
+                          "identical": lr["identical_output"]}
+        for k in ("model_free_ms", "vs_model_free"):
+            if k in lr:
+                out["learned"][k] = r(lr[k], 3)
+    sv = result.get("serving")
+    if sv:
+        out["serving"] = {"p50_ms": r(sv["p50_ms"], 1), "p99_ms": r(sv["p99_ms"], 1),
+                          "batched": sv["batched_requests"], "requests": sv.get("requests"),
+                          "gkeys_per_s": r(sv["keys_per_s"] / 1e9, 2)}
+    return out
 
 
 def run_reference(args, rank: int):
@@ -599,6 +643,9 @@ def main():
         peak = measured_peaks()[0]
         if args.only == "secondary":
             out = run_secondary(fs, workloads, torch, stream, peak)
+        elif args.only == "expand":
+            out = run_secondary(fs, workloads, torch, stream, peak, reps=args.reps, expand_log2n=args.expand_log2n,
+                                u64=False)
         elif args.only == "batched":
             out = run_batched(fs, workloads, torch, stream, peak)
         elif args.only == "learned":
@@ -739,6 +786,7 @@ def main():
             result["cpu_baseline"] = cpu_baseline()
         else:
             result["cpu_baseline"] = None
+        result["summary"] = summary(result)  # last key: kept by readers of the line's tail
         print(json.dumps(result), flush=True)
     if dist:
         dist.barrier()

@@ -70,11 +70,11 @@ __device__ __forceinline__ T* pick(T* const (&b)[3], int sel) {
 // shared-memory buffers of one tile each, filled by bulk copies while earlier
 // tiles are counted.  Each thread counts kCountVecs 16-byte vectors of a full
 // tile, so the count CTA has tile / (16-byte vector keys * kCountVecs) threads.
-constexpr int kCountStages = 4;
+constexpr int kCountStages = 3;
 constexpr int kCountVecs = 2;
 
-// Count CTAs per SM: two for 16-bit keys (4 x 22 KB of buffers each), one for
-// wider keys.
+// Count CTAs per SM: two for 16-bit keys (3 x 22 KB of buffers and 32 KB of
+// counters each), one for wider keys.
 template <typename K>
 __host__ __device__ constexpr int count_ctas_per_sm() { return sizeof(K) == 2 ? 2 : 1; }
 template <typename K>
@@ -108,7 +108,14 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
   static_assert(kThreads >= kRadix && kThreads % 32 == 0 && kThreads <= 1024, "one thread per digit");
   static_assert(uint32_t(kThreads) * kVec * kCountVecs == kTileKeys, "threads cover a tile exactly");
   extern __shared__ __align__(128) unsigned char smem[];  // [kCountStages][tile keys]
-  __shared__ uint32_t s_tile[2][kRadix];  // a tile's counts; tiles alternate between two sets
+  // Running counts of the chunk's tiles so far, tiles alternating between two
+  // sets.  Each digit has 16 copies, one per lane & 15: word [d][c] sits in
+  // bank 16 (d & 1) + c, so of a warp's 32 additions only lanes l and l + 16
+  // can meet in a bank (when their digits have the same parity).  The counts
+  // are never cleared: the thread of digit d sums its 16 copies after each
+  // tile and subtracts the sum it saw two tiles earlier (same set).  Sums stay
+  // below 2^32: a chunk holds fewer than 2^32 keys.
+  __shared__ __align__(128) uint32_t s_cnt[2][kRadix][16];
   __shared__ uint64_t s_bar[kCountStages];
   __shared__ uint32_t s_fail[2];  // by tile parity: a tile reads only its own flag after its barrier
   K* buf = reinterpret_cast<K*>(smem);
@@ -143,14 +150,29 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
     s_fail[0] = s_fail[1] = 0;
     for (uint32_t st = 0; st < steps && st < uint32_t(kCountStages); ++st) issue(st);
   }
-  for (int i = tid; i < 2 * kRadix; i += kThreads) (&s_tile[0][0])[i] = 0;
+  for (int i = tid; i < 2 * kRadix * 16; i += kThreads) (&s_cnt[0][0][0])[i] = 0;
   __syncthreads();
 
   const uint32_t shift = a.shift, mask = a.mask;
-  uint64_t k_or = 0, k_and = ~0ull;  // this thread's keys folded
+  const uint32_t copy = uint32_t(tid) & 15u;
+  uint64_t k_or = 0, k_and = ~0ull;  // this thread's keys of ragged ends folded
+  // Whole 16-byte vectors are folded word by word: w_or[h] / w_and[h] cover the
+  // vector words of parity h (for 64-bit keys the low and high halves; for
+  // narrower keys both hold whole keys, two 16-bit keys to a word).
+  uint32_t w_or[2] = {0u, 0u}, w_and[2] = {~0u, ~0u};
+  auto fold_vec = [&](const uint4& q) {
+    if (kOrAnd) {
+      w_or[0] |= q.x | q.z;
+      w_or[1] |= q.y | q.w;
+      w_and[0] &= q.x & q.z;
+      w_and[1] &= q.y & q.w;
+    }
+  };
   uint32_t set = 0;
-  auto count_key = [&](K k) {
-    atomicAdd(&s_tile[set][dig(k, shift, mask)], 1u);
+  uint32_t seen0 = 0, seen1 = 0;  // thread d < 256: digit d's sum over set 0's / set 1's copies at its last tile
+  auto count_key = [&](K k) { atomicAdd(&s_cnt[set][dig(k, shift, mask)][copy], 1u); };
+  auto count_ragged = [&](K k) {
+    count_key(k);
     if (kOrAnd) {
       k_or |= uint64_t(k);
       k_and &= uint64_t(k);
@@ -168,16 +190,18 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
 #pragma unroll
       for (int j = 0; j < kCountVecs; ++j) {
         const uint4 q = bv[tid + j * kThreads];
+        fold_vec(q);
 #pragma unroll
         for (int e = 0; e < int(kVec); ++e) count_key(vec_key<K>(q, e));
       }
     } else {  // the last, short tile
       for (uint32_t v = tid; v < body / kVec; v += kThreads) {
         const uint4 q = bv[v];
+        fold_vec(q);
 #pragma unroll
         for (int e = 0; e < int(kVec); ++e) count_key(vec_key<K>(q, e));
       }
-      for (uint32_t i = body + tid; i < keys_n; i += kThreads) count_key(keys[e0 + i]);  // ragged end
+      for (uint32_t i = body + tid; i < keys_n; i += kThreads) count_ragged(keys[e0 + i]);  // ragged end
     }
     __syncthreads();
     if (s_fail[st & 1u]) {  // the table would be wrong: mark it so that no scatter uses it
@@ -190,8 +214,15 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
     }
     if (tid < kRadix) {  // meanwhile the next tile counts into the other set
       a.tilerel[uint64_t(t_begin + st) * kRadix + tid] = acc;
-      acc += s_tile[set][tid];
-      s_tile[set][tid] = 0;  // cleared before this thread reaches the next barrier, so before tile st + 2 counts
+      // digit tid's 16 copies, visited in a rotated order so that the warp's
+      // 32 reads fall in 32 banks (bank 16 (tid & 1) + copy)
+      const uint32_t* row = s_cnt[set][tid];
+      uint32_t c = 0;
+#pragma unroll
+      for (uint32_t l = 0; l < 16; ++l) c += row[(l + (uint32_t(tid) >> 1)) & 15u];
+      acc += c - (set ? seen1 : seen0);
+      if (set) seen1 = c;
+      else seen0 = c;
     }
     if (tid == 0 && st + kCountStages < steps) {  // every thread has read this buffer (barrier above)
       fence_proxy_async_smem();
@@ -204,6 +235,18 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
     if (acc) atomicAdd(&a.totals[tid], acc);
   }
   if (kOrAnd) {
+    if (sizeof(K) == 8) {
+      k_or |= uint64_t(w_or[0]) | (uint64_t(w_or[1]) << 32);
+      k_and &= uint64_t(w_and[0]) | (uint64_t(w_and[1]) << 32);
+    } else {
+      uint32_t o = w_or[0] | w_or[1], n = w_and[0] & w_and[1];
+      if (sizeof(K) == 2) {
+        o = (o | (o >> 16)) & 0xFFFFu;
+        n = n & (n >> 16) & 0xFFFFu;
+      }
+      k_or |= uint64_t(o);
+      k_and &= uint64_t(n) | (sizeof(K) == 2 ? ~0xFFFFull : ~0xFFFFFFFFull);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       k_or |= __shfl_xor_sync(0xffffffffu, k_or, o);

@@ -211,19 +211,26 @@ __global__ void schedule_copy_kernel(const K* k0, const K* k1, const K* k2, cons
 }
 
 // --------------------------------------------------------------- K1' -------
-// 65,536 counters of 16 bits, two per 32-bit shared-memory word (128 KB).
-// Counters are added with red.shared (no return value).  Every round of
-// kLeafRound keys per CTA is followed by a drain: any counter that reached
-// 2^15 hands 2^15 to its global 64-bit spill counter.  After a drain every
-// counter is below 2^15, and a round adds at most kLeafRound = 2^15 to any
-// counter, so no counter ever exceeds 2^16 - 1 (no carry into the neighbour
-// half) -- the counter width follows the size of what one round can count,
-// as the tapering of Sec. III-D-1 asks, and overflow is exact.
+// 65,536 counters of 16 bits, two per 32-bit shared-memory word (128 KB):
+// word w holds key w in its low half and key w + 32768 in its high half, so
+// the small, frequent keys of skewed inputs sit in different words, and the
+// lanes that count the same key add the same value to the same word, which
+// the shared-memory units combine.  Counters are added with red.shared (no
+// return value).
+//
+// Overflow is exact (the tapered width of Sec. III-D-1 with an exact spill):
+// a drain after every two rounds hands each counter's multiples of 2^14 to its
+// global 64-bit spill counter, leaving every counter below 2^14.  Two rounds
+// add at most 2 * kLeafRound = 49,152 keys to any counter, so no counter ever
+// exceeds 2^14 - 1 + 49,152 = 65,535 (no carry into the neighbouring half).
+// The drain reads the counters 16 bytes at a time and touches only words with
+// a counter at or above 2^14.
 constexpr int kLeafThreads = 1024;
 constexpr int kLeafWords = 32768;
-constexpr int kLeafVecPerThread = 4;                                   // uint4 = 8 keys each
-constexpr int kLeafRound = kLeafThreads * kLeafVecPerThread * 8;       // 32768 keys
-static_assert(kLeafRound <= 32768, "a round must not be able to overflow a drained 16-bit counter");
+constexpr int kLeafVecPerThread = 3;                                   // uint4 = 8 keys each
+constexpr int kLeafRound = kLeafThreads * kLeafVecPerThread * 8;       // 24,576 keys
+constexpr uint32_t kLeafDrainBits = 0xC000C000u;                       // 2^14 and 2^15 of either half
+static_assert((1 << 14) - 1 + 2 * kLeafRound <= 65535, "two rounds must not overflow a drained 16-bit counter");
 
 __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16_t* __restrict__ keys, uint64_t n,
                                                                     uint32_t* __restrict__ partials,
@@ -232,10 +239,10 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
   for (int i = threadIdx.x; i < kLeafWords; i += blockDim.x) hw[i] = 0;
   __syncthreads();
   // Rounds are dealt to CTAs round-robin over the whole input; the next
-  // round's keys are loaded into registers before this round's drain, so the
-  // loads overlap the drain and its barriers.
+  // round's keys are loaded into registers before this round's keys are
+  // counted, so the loads overlap the counting and the drains.
   const uint64_t rounds = (n + kLeafRound - 1) / kLeafRound;
-  auto add = [&](uint32_t k) { atomicAdd(&hw[k >> 1], 1u << ((k & 1) * 16)); };
+  auto add = [&](uint32_t k) { atomicAdd(&hw[k & 32767u], 1u << ((k >> 15) * 16)); };
   auto full = [&](uint64_t r) { return (r + 1) * kLeafRound <= n; };
   uint4 q[kLeafVecPerThread];
   auto load = [&](uint64_t r) {
@@ -245,6 +252,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
   };
   uint64_t r = blockIdx.x;
   if (r < rounds && full(r)) load(r);
+  uint32_t done = 0;  // rounds this CTA has counted
   for (; r < rounds; r += gridDim.x) {
     const uint64_t next = r + gridDim.x;
     if (full(r)) {
@@ -264,38 +272,43 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
     } else {
       for (uint64_t i = r * kLeafRound + threadIdx.x; i < n; i += blockDim.x) add(keys[i]);
     }
+    if (++done & 1u) continue;  // drain after every second round
     __syncthreads();
-    for (int i = threadIdx.x; i < kLeafWords; i += blockDim.x) {
-      uint32_t w = hw[i];
-      if ((w & 0x8000u) | (w & 0x80000000u)) {
-        if (w & 0x8000u) {
-          atomicAdd(&spill[2 * i], 0x8000ull);
-          w -= 0x8000u;
-        }
-        if (w & 0x80000000u) {
-          atomicAdd(&spill[2 * i + 1], 0x8000ull);
-          w -= 0x80000000u;
-        }
-        hw[i] = w;
+    uint4* hv = reinterpret_cast<uint4*>(hw);
+    for (int i = threadIdx.x; i < kLeafWords / 4; i += blockDim.x) {
+      const uint4 v = hv[i];
+      if (((v.x | v.y | v.z | v.w) & kLeafDrainBits) == 0) continue;
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t wd = w4[e], take = wd & kLeafDrainBits;
+        if (!take) continue;
+        const uint32_t word = 4 * i + e;
+        if (take & 0xFFFFu) atomicAdd(&spill[word], (unsigned long long)(take & 0xFFFFu));
+        if (take >> 16) atomicAdd(&spill[word + 32768], (unsigned long long)(take >> 16));
+        hw[word] = wd - take;
       }
     }
     __syncthreads();
   }
+  __syncthreads();  // a last round without a drain has no barrier of its own: every add lands before the copy
   for (int i = threadIdx.x; i < kLeafWords; i += blockDim.x) partials[uint64_t(blockIdx.x) * kLeafWords + i] = hw[i];
 }
 
+// counts[k] = spill[k] + the CTAs' partial counters of key k (word k & 32767,
+// low half for k < 32768, high half above).
 __global__ void leaf_reduce_kernel(const uint32_t* __restrict__ partials, const uint64_t* __restrict__ spill,
                                    int grid, uint64_t* __restrict__ counts) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= kLeafWords) return;
-  uint64_t lo = spill[2 * w], hi = spill[2 * w + 1];
+  uint64_t lo = spill[w], hi = spill[w + 32768];
   for (int c = 0; c < grid; ++c) {
     const uint32_t x = partials[uint64_t(c) * kLeafWords + w];
     lo += x & 0xFFFFu;
     hi += x >> 16;
   }
-  counts[2 * w] = lo;
-  counts[2 * w + 1] = hi;
+  counts[w] = lo;
+  counts[w + 32768] = hi;
 }
 
 // ---------------------------------------------------------------- K4 -------
