@@ -41,6 +41,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "fsort_dev.cuh"
 #include "fsort_internal.h"
@@ -50,7 +51,6 @@ namespace fsort {
 namespace {
 
 constexpr int kH = kMlpHidden;  // 64
-constexpr int kGradThreads = 64;
 constexpr uint32_t kFillSplit = 32768;  // heavy buckets above this are filled by every CTA
 
 struct Layout {
@@ -75,22 +75,6 @@ __device__ __forceinline__ float raw_feature(uint64_t k) {
 // Key feature, non-decreasing in the key.
 __device__ __forceinline__ float key_feature(uint64_t k, float center, float half) {
   return (raw_feature(k) - center) / half;
-}
-
-// Forward one input; h1/h2 receive the post-ReLU activations.
-__device__ __forceinline__ float mlp_forward(const __nv_bfloat16* w, float x, float* h1, float* h2) {
-#pragma unroll
-  for (int i = 0; i < kH; ++i) h1[i] = fmaxf(0.f, fmaf(bf(w, Layout::W1 + i), x, bf(w, Layout::B1 + i)));
-  float z = bf(w, Layout::B3);
-#pragma unroll 4
-  for (int j = 0; j < kH; ++j) {
-    float a = bf(w, Layout::B2 + j);
-#pragma unroll
-    for (int i = 0; i < kH; ++i) a = fmaf(bf(w, Layout::W2 + j * kH + i), h1[i], a);
-    h2[j] = fmaxf(0.f, a);
-    z = fmaf(bf(w, Layout::W3 + j), h2[j], z);
-  }
-  return z;
 }
 
 __device__ __forceinline__ float sigmoid(float z) { return 1.f / (1.f + expf(-z)); }
@@ -127,86 +111,6 @@ struct SampleIn {
   }
 };
 
-// grads (FP32) += d(loss)/d(params), loss = 1/(2m) sum (sigmoid(z) - y)^2 over
-// the m inputs.  One thread per input; its h1 and h2 (later dL/dh2) rows live
-// in shared memory (odd row stride: no bank conflicts); every parameter's
-// gradient is summed over the block before one atomic add per warp or block.
-template <typename In>
-__global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(const __nv_bfloat16* __restrict__ w, In in, uint32_t m,
-                                                                float* __restrict__ grads, float* __restrict__ loss) {
-  __shared__ float s_h1[kGradThreads][kH + 1];
-  __shared__ float s_d2[kGradThreads][kH + 1];
-  __shared__ float s_red[kGradThreads / 32];
-  const int t = threadIdx.x;
-  const uint32_t s = blockIdx.x * kGradThreads + t;
-  float xs = 0.f, ys = 0.f;
-  const bool valid = in.get(s, m, xs, ys);
-  if (!valid) xs = 0.f;
-  float* h1 = s_h1[t];
-  float* h2 = s_d2[t];
-  // forward
-#pragma unroll 8
-  for (int i = 0; i < kH; ++i) h1[i] = fmaxf(0.f, fmaf(bf(w, Layout::W1 + i), xs, bf(w, Layout::B1 + i)));
-  float z = bf(w, Layout::B3);
-#pragma unroll 1
-  for (int j = 0; j < kH; ++j) {
-    float a = bf(w, Layout::B2 + j);
-#pragma unroll 16
-    for (int i = 0; i < kH; ++i) a = fmaf(bf(w, Layout::W2 + j * kH + i), h1[i], a);
-    h2[j] = fmaxf(0.f, a);
-    z = fmaf(bf(w, Layout::W3 + j), h2[j], z);
-  }
-  const float f = sigmoid(z);
-  const float err = valid ? (f - ys) : 0.f;
-  const float inv_m = 1.f / float(m);
-  const float dz = err * f * (1.f - f) * inv_m;
-  auto block_add = [&](float v, int idx) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((t & 31) == 0) atomicAdd(&grads[idx], v);
-  };
-  // output layer, then dL/dh2 replaces h2 in place
-#pragma unroll 1
-  for (int j = 0; j < kH; ++j) {
-    const float hj = h2[j];
-    block_add(dz * hj, Layout::W3 + j);
-    const float d = (hj > 0.f) ? dz * bf(w, Layout::W3 + j) : 0.f;
-    h2[j] = d;
-    block_add(d, Layout::B2 + j);
-  }
-  block_add(dz, Layout::B3);
-  // first layer: dL/dh1_i = relu'(h1_i) * sum_j dL/dh2_j W2[j][i]
-#pragma unroll 1
-  for (int i = 0; i < kH; ++i) {
-    float a = 0.f;
-#pragma unroll 16
-    for (int j = 0; j < kH; ++j) a = fmaf(h2[j], bf(w, Layout::W2 + j * kH + i), a);
-    const float d1 = (h1[i] > 0.f) ? a : 0.f;
-    block_add(d1 * xs, Layout::W1 + i);
-    block_add(d1, Layout::B1 + i);
-  }
-  {
-    float l = 0.5f * err * err * inv_m;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-    if ((t & 31) == 0) s_red[t >> 5] = l;
-  }
-  __syncthreads();
-  if (t == 0 && loss) {
-    float l = 0.f;
-    for (int k = 0; k < kGradThreads / 32; ++k) l += s_red[k];
-    atomicAdd(loss, l);
-  }
-  // dW2[j][i] = sum over the block's inputs of dL/dh2_j * h1_i
-  for (int e = t; e < kH * kH; e += kGradThreads) {
-    const int j = e / kH, i = e % kH;
-    float acc = 0.f;
-#pragma unroll 8
-    for (int r = 0; r < kGradThreads; ++r) acc = fmaf(s_d2[r][j], s_h1[r][i], acc);
-    atomicAdd(&grads[Layout::W2 + e], acc);
-  }
-}
-
 __global__ void mlp_adam_kernel(float* __restrict__ master, float* __restrict__ grads, float* __restrict__ m1,
                                 float* __restrict__ m2, __nv_bfloat16* __restrict__ w, float lr, float beta1,
                                 float beta2, float eps, float bias1, float bias2, LearnedState* st,
@@ -228,17 +132,372 @@ __global__ void mlp_adam_kernel(float* __restrict__ master, float* __restrict__ 
   w[i] = __float2bfloat16_rn(p);
 }
 
-__global__ void mlp_eval_kernel(const __nv_bfloat16* __restrict__ w, const float* __restrict__ x, uint32_t m,
-                                float* __restrict__ out) {
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= m) return;
-  float h1[kH], h2[kH];
-  out[s] = sigmoid(mlp_forward(w, x[s], h1, h2));
-}
-
 __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// ------------------------------------------------------ tensor-core MLP ----
+// The 64-wide products of the MLP run on the tensor cores: mma.sync m16n8k16
+// with BF16 operands and FP32 accumulation.  The weights are BF16 already.  An
+// FP32 activation v enters as two BF16 parts, hi = bf16(v) and
+// lo = bf16(v - hi): BF16 x BF16 products are exact in FP32, so a product
+// taken with both parts keeps about 16 significant bits of v -- the FP32
+// arithmetic of the definition (BF16 weights, FP32 sums) up to FP32 rounding.
+//
+// Fragment layouts of m16n8k16 for lane l = 4 g + t (two BF16 values per
+// 32-bit register, the lower k index in the low half):
+//   A (16 x 16, row-major)  a0 = A[g][2t, 2t+1]    a1 = A[g+8][2t, 2t+1]
+//                            a2 = A[g][2t+8, 2t+9]  a3 = A[g+8][2t+8, 2t+9]
+//   B (16 x 8, k-major)     b0 = B[2t, 2t+1][g]    b1 = B[2t+8, 2t+9][g]
+//   C (16 x 8)              c0, c1 = C[g][2t, 2t+1]   c2, c3 = C[g+8][2t, 2t+1]
+// The accumulators of two adjacent 8-column tiles are, row by row, the B
+// fragment of the transposed matrix over one 16-wide k step; the backward pass
+// feeds dL/da2 from its accumulators into the next product that way.
+constexpr int kTcThreads = 128;  // 4 warps
+constexpr int kTcTile = 64;      // samples per CTA step, 16 per warp
+constexpr int kTcStride = 72;    // padded row (BF16) of the shared 64 x 64 matrices: conflict-free fragment loads
+
+struct TcSmem {
+  __nv_bfloat16 w2[kH * kTcStride];   // W2[j][i] at [j][i]
+  __nv_bfloat16 w2t[kH * kTcStride];  // W2[j][i] at [i][j]
+  __nv_bfloat16 d2h[kH * kTcStride];  // dL/da2 of the step's samples at [j][sample], high part
+  __nv_bfloat16 d2l[kH * kTcStride];  // low part
+  float w1[kH], b1[kH], b2[kH], w3[kH];
+  float x[kTcTile], y[kTcTile], valid[kTcTile];
+  float b3;
+};
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
+  uint32_t r;
+  memcpy(&r, &v, 4);
+  return r;
+}
+
+// (v0, v1) -> high parts and low parts, v0 in the low halves.
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+  const float2 hf = __bfloat1622float2(h);
+  hi = bf16x2_bits(h);
+  lo = bf16x2_bits(__floats2bfloat162_rn(v0 - hf.x, v1 - hf.y));
+}
+
+__device__ __forceinline__ uint32_t ld_bf16x2(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// The CTA's copy of the BF16 weights (W2 twice: as is and transposed).
+__device__ __forceinline__ void tc_load_weights(const __nv_bfloat16* __restrict__ w, TcSmem& S) {
+  for (int e = threadIdx.x; e < kH * kH; e += blockDim.x) {
+    const int j = e / kH, i = e % kH;
+    const __nv_bfloat16 v = w[Layout::W2 + e];
+    S.w2[j * kTcStride + i] = v;
+    S.w2t[i * kTcStride + j] = v;
+  }
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    S.w1[i] = bf(w, Layout::W1 + i);
+    S.b1[i] = bf(w, Layout::B1 + i);
+    S.b2[i] = bf(w, Layout::B2 + i);
+    S.w3[i] = bf(w, Layout::W3 + i);
+  }
+  if (threadIdx.x == 0) S.b3 = bf(w, Layout::B3);
+}
+
+// acc = the layer-2 products (without b2) of the warp's 16 inputs: x0 in row
+// g, x1 in row g + 8; columns j = 8 nt + 2t (+1).
+__device__ __forceinline__ void tc_layer2(const TcSmem& S, float x0, float x1, float (&acc)[8][4]) {
+  const int l = threadIdx.x & 31, g = l >> 2, t = l & 3;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    const int i0 = 16 * kk + 2 * t;
+    float h[2][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = i0 + (c & 1) + (c >> 1) * 8;
+      h[0][c] = fmaxf(0.f, fmaf(S.w1[i], x0, S.b1[i]));
+      h[1][c] = fmaxf(0.f, fmaf(S.w1[i], x1, S.b1[i]));
+    }
+    uint32_t ah[4], al[4];
+    split2(h[0][0], h[0][1], ah[0], al[0]);
+    split2(h[1][0], h[1][1], ah[1], al[1]);
+    split2(h[0][2], h[0][3], ah[2], al[2]);
+    split2(h[1][2], h[1][3], ah[3], al[3]);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const __nv_bfloat16* wr = S.w2 + (8 * nt + g) * kTcStride + i0;  // B[k = i][n = j] = W2[j][i]
+      const uint32_t b0 = ld_bf16x2(wr), b1 = ld_bf16x2(wr + 8);
+      mma_bf16(acc[nt], ah[0], ah[1], ah[2], ah[3], b0, b1);
+      mma_bf16(acc[nt], al[0], al[1], al[2], al[3], b0, b1);
+    }
+  }
+}
+
+// z of rows g and g + 8 from the layer-2 products (every lane of the quad gets both).
+__device__ __forceinline__ void tc_output(const TcSmem& S, const float (&acc)[8][4], float& z0, float& z1) {
+  const int t = threadIdx.x & 3;
+  z0 = z1 = 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int j = 8 * nt + 2 * t + e;
+      z0 = fmaf(S.w3[j], fmaxf(0.f, acc[nt][e] + S.b2[j]), z0);
+      z1 = fmaf(S.w3[j], fmaxf(0.f, acc[nt][2 + e] + S.b2[j]), z1);
+    }
+  z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
+  z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
+  z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
+  z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
+  z0 += S.b3;
+  z1 += S.b3;
+}
+
+// grads (FP32) += d(loss)/d(params), loss += 1/(2m) sum (sigmoid(z) - y)^2
+// over the m inputs.  Persistent CTAs walk steps of 64 samples; a warp runs
+// the forward pass, dL/dz, dL/da2 and dL/da1 of its 16 samples, then each warp
+// adds rows 16 w .. 16 w + 15 of dL/dW2 over all 64 samples.  Every gradient
+// stays in registers over the CTA's steps; each CTA adds it to `grads` once.
+template <typename In>
+__global__ void __launch_bounds__(kTcThreads) mlp_grad_tc_kernel(const __nv_bfloat16* __restrict__ w, In in,
+                                                                 uint32_t m, float* __restrict__ grads,
+                                                                 float* __restrict__ loss) {
+  __shared__ TcSmem S;
+  tc_load_weights(w, S);
+  const int warp = threadIdx.x >> 5, l = threadIdx.x & 31, g = l >> 2, t = l & 3;
+  float gw2[8][4];        // dW2[j][i], j = 16 warp + g (+8), i = 8 nt + 2t (+1)
+  float gw1[4][2], gb1[4][2];  // dW1, db1 at i = 16 mt + g (+8): this lane's samples
+  float gb2[8][2], gw3[8][2];  // db2, dW3 at j = 8 nt + 2t + e: this lane's rows
+  float gb3 = 0.f, lsum = 0.f;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    gw2[a][0] = gw2[a][1] = gw2[a][2] = gw2[a][3] = 0.f;
+    gb2[a][0] = gb2[a][1] = gw3[a][0] = gw3[a][1] = 0.f;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) gw1[a][0] = gw1[a][1] = gb1[a][0] = gb1[a][1] = 0.f;
+  const float inv_m = 1.f / float(m);
+  const uint32_t steps = (m + kTcTile - 1) / kTcTile;
+  for (uint32_t step = blockIdx.x; step < steps; step += gridDim.x) {
+    __syncthreads();  // the weights, and the previous step's use of x and d2, are done
+    if (threadIdx.x < kTcTile) {
+      float xs = 0.f, ys = 0.f;
+      const bool v = in.get(step * kTcTile + threadIdx.x, m, xs, ys);
+      S.x[threadIdx.x] = v ? xs : 0.f;
+      S.y[threadIdx.x] = v ? ys : 0.f;
+      S.valid[threadIdx.x] = v ? 1.f : 0.f;
+    }
+    __syncthreads();
+    // ---- the warp's 16 samples: forward, dL/dz, dL/da2
+    const int r0 = 16 * warp + g, r1 = r0 + 8;
+    const float x0 = S.x[r0], x1 = S.x[r1];
+    float acc[8][4];
+    tc_layer2(S, x0, x1, acc);
+    float z0, z1;
+    tc_output(S, acc, z0, z1);
+    const float f0 = sigmoid(z0), f1 = sigmoid(z1);
+    const float e0 = S.valid[r0] != 0.f ? f0 - S.y[r0] : 0.f;
+    const float e1 = S.valid[r1] != 0.f ? f1 - S.y[r1] : 0.f;
+    const float dz0 = e0 * f0 * (1.f - f0) * inv_m, dz1 = e1 * f1 * (1.f - f1) * inv_m;
+    if (t == 0) {
+      lsum += 0.5f * (e0 * e0 + e1 * e1) * inv_m;
+      gb3 += dz0 + dz1;
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int j = 8 * nt + 2 * t + e;
+        const float a0 = acc[nt][e] + S.b2[j], a1 = acc[nt][2 + e] + S.b2[j];
+        gw3[nt][e] += fmaxf(0.f, a0) * dz0 + fmaxf(0.f, a1) * dz1;
+        const float d0 = a0 > 0.f ? dz0 * S.w3[j] : 0.f, d1 = a1 > 0.f ? dz1 * S.w3[j] : 0.f;
+        gb2[nt][e] += d0 + d1;
+        acc[nt][e] = d0;  // acc now holds dL/da2
+        acc[nt][2 + e] = d1;
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(d0), h1 = __float2bfloat16_rn(d1);
+        S.d2h[j * kTcStride + r0] = h0;
+        S.d2h[j * kTcStride + r1] = h1;
+        S.d2l[j * kTcStride + r0] = __float2bfloat16_rn(d0 - __bfloat162float(h0));
+        S.d2l[j * kTcStride + r1] = __float2bfloat16_rn(d1 - __bfloat162float(h1));
+      }
+    // ---- dL/da1, transposed: d1t[i][sample] = sum_j W2[j][i] dL/da2[sample][j],
+    // rows i = 16 mt + g (+8), columns = the warp's samples 8 ns + 2t (+1)
+    {
+      float d1t[4][2][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) d1t[a][b][0] = d1t[a][b][1] = d1t[a][b][2] = d1t[a][b][3] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        uint32_t bh[2][2], bl[2][2];  // [ns][reg]: B[k = j][n = sample] from the accumulators
+        split2(acc[2 * kk][0], acc[2 * kk][1], bh[0][0], bl[0][0]);
+        split2(acc[2 * kk + 1][0], acc[2 * kk + 1][1], bh[0][1], bl[0][1]);
+        split2(acc[2 * kk][2], acc[2 * kk][3], bh[1][0], bl[1][0]);
+        split2(acc[2 * kk + 1][2], acc[2 * kk + 1][3], bh[1][1], bl[1][1]);
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+          const __nv_bfloat16* ar = S.w2t + (16 * mt + g) * kTcStride + 16 * kk + 2 * t;  // A[i][j] = W2[j][i]
+          const uint32_t a0 = ld_bf16x2(ar), a1 = ld_bf16x2(ar + 8 * kTcStride);
+          const uint32_t a2 = ld_bf16x2(ar + 8), a3 = ld_bf16x2(ar + 8 * kTcStride + 8);
+#pragma unroll
+          for (int ns = 0; ns < 2; ++ns) {
+            mma_bf16(d1t[mt][ns], a0, a1, a2, a3, bh[ns][0], bh[ns][1]);
+            mma_bf16(d1t[mt][ns], a0, a1, a2, a3, bl[ns][0], bl[ns][1]);
+          }
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int ns = 0; ns < 2; ++ns)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float xs = S.x[16 * warp + 8 * ns + 2 * t + e];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int i = 16 * mt + g + 8 * h;
+              const float v = fmaf(S.w1[i], xs, S.b1[i]) > 0.f ? d1t[mt][ns][2 * h + e] : 0.f;
+              gw1[mt][h] = fmaf(v, xs, gw1[mt][h]);
+              gb1[mt][h] += v;
+            }
+          }
+    }
+    __syncthreads();  // every warp's dL/da2 is in shared memory
+    // ---- dW2 rows 16 warp + g (+8): sum over the step's 64 samples of dL/da2[s][j] h1[s][i]
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const int row = (16 * warp + g) * kTcStride + 16 * kk + 2 * t;
+      const uint32_t ah0 = ld_bf16x2(S.d2h + row), ah1 = ld_bf16x2(S.d2h + row + 8 * kTcStride);
+      const uint32_t ah2 = ld_bf16x2(S.d2h + row + 8), ah3 = ld_bf16x2(S.d2h + row + 8 * kTcStride + 8);
+      const uint32_t al0 = ld_bf16x2(S.d2l + row), al1 = ld_bf16x2(S.d2l + row + 8 * kTcStride);
+      const uint32_t al2 = ld_bf16x2(S.d2l + row + 8), al3 = ld_bf16x2(S.d2l + row + 8 * kTcStride + 8);
+      const int s0 = 16 * kk + 2 * t;
+      const float xa = S.x[s0], xb = S.x[s0 + 1], xc = S.x[s0 + 8], xd = S.x[s0 + 9];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int i = 8 * nt + g;
+        const float wi = S.w1[i], bi = S.b1[i];
+        uint32_t bh0, bl0, bh1, bl1;  // B[k = sample][n = i] = h1[sample][i]
+        split2(fmaxf(0.f, fmaf(wi, xa, bi)), fmaxf(0.f, fmaf(wi, xb, bi)), bh0, bl0);
+        split2(fmaxf(0.f, fmaf(wi, xc, bi)), fmaxf(0.f, fmaf(wi, xd, bi)), bh1, bl1);
+        mma_bf16(gw2[nt], ah0, ah1, ah2, ah3, bh0, bh1);
+        mma_bf16(gw2[nt], ah0, ah1, ah2, ah3, bl0, bl1);
+        mma_bf16(gw2[nt], al0, al1, al2, al3, bh0, bh1);
+      }
+    }
+  }
+  // ---- one global addition per parameter per CTA (per warp for the per-warp sums)
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = 16 * warp + g + 8 * (c >> 1), i = 8 * nt + 2 * t + (c & 1);
+      atomicAdd(&grads[Layout::W2 + j * kH + i], gw2[nt][c]);
+    }
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float a = gw1[mt][h], b = gb1[mt][h];
+      a += __shfl_xor_sync(0xffffffffu, a, 1);
+      b += __shfl_xor_sync(0xffffffffu, b, 1);
+      a += __shfl_xor_sync(0xffffffffu, a, 2);
+      b += __shfl_xor_sync(0xffffffffu, b, 2);
+      if (t == 0) {
+        atomicAdd(&grads[Layout::W1 + 16 * mt + g + 8 * h], a);
+        atomicAdd(&grads[Layout::B1 + 16 * mt + g + 8 * h], b);
+      }
+    }
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      float a = gb2[nt][e], b = gw3[nt][e];
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+      }
+      if (g == 0) {
+        atomicAdd(&grads[Layout::B2 + 8 * nt + 2 * t + e], a);
+        atomicAdd(&grads[Layout::W3 + 8 * nt + 2 * t + e], b);
+      }
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gb3 += __shfl_xor_sync(0xffffffffu, gb3, o);
+    lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  }
+  if (l == 0) {
+    atomicAdd(&grads[Layout::B3], gb3);
+    if (loss) atomicAdd(loss, lsum);
+  }
+}
+
+// sigmoid(mlp(x)) for m inputs (x from `in`, see XIn / CellIn), on the tensor cores.
+struct XIn {
+  const float* x;
+  __device__ __forceinline__ bool get(uint32_t s, uint32_t m, float& xs) const {
+    if (s >= m) return false;
+    xs = x[s];
+    return true;
+  }
+};
+
+__device__ __forceinline__ uint64_t cell_start(uint32_t i);  // first key of grid cell i (below)
+
+// The cell starts of the map's grid as inputs.
+struct CellIn {
+  const LearnedState* st;
+  __device__ __forceinline__ bool get(uint32_t s, uint32_t m, float& xs) const {
+    if (s >= m) return false;
+    xs = key_feature(cell_start(s), st->center, st->half);
+    return true;
+  }
+};
+
+// kCells: outputs clamped to [0, 1] (NaN from a diverged model counts as 0)
+// and out[m] = 1, the closing entry of the map's table.
+template <typename In, bool kCells>
+__global__ void __launch_bounds__(kTcThreads) mlp_eval_tc_kernel(const __nv_bfloat16* __restrict__ w, In in,
+                                                                 uint32_t m, float* __restrict__ out) {
+  __shared__ TcSmem S;
+  tc_load_weights(w, S);
+  if (kCells && blockIdx.x == 0 && threadIdx.x == 0) out[m] = 1.f;
+  const int warp = threadIdx.x >> 5, l = threadIdx.x & 31, g = l >> 2, t = l & 3;
+  const uint32_t steps = (m + kTcTile - 1) / kTcTile;
+  for (uint32_t step = blockIdx.x; step < steps; step += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x < kTcTile) {
+      float xs = 0.f;
+      S.x[threadIdx.x] = in.get(step * kTcTile + threadIdx.x, m, xs) ? xs : 0.f;
+    }
+    __syncthreads();
+    const int r0 = 16 * warp + g, r1 = r0 + 8;
+    float acc[8][4];
+    tc_layer2(S, S.x[r0], S.x[r1], acc);
+    float z0, z1;
+    tc_output(S, acc, z0, z1);
+    if (t == 0) {
+      const uint32_t s0 = step * kTcTile + r0, s1 = step * kTcTile + r1;
+      float v0 = sigmoid(z0), v1 = sigmoid(z1);
+      if (kCells) {
+        v0 = (v0 >= 0.f) ? fminf(v0, 1.f) : 0.f;
+        v1 = (v1 >= 0.f) ? fminf(v1, 1.f) : 0.f;
+      }
+      if (s0 < m) out[s0] = v0;
+      if (s1 < m) out[s1] = v1;
+    }
+  }
 }
 
 // ------------------------------------------------------------- sampling ----
@@ -362,22 +621,6 @@ __device__ __forceinline__ uint32_t map_id(uint64_t k, const LearnedMap& mp, boo
   }
   t = c;
   return (f >> mp.shift) + 2u * c + (hit ? 1u : 0u);
-}
-
-// fval[i] = F(x_i), x_i the feature of the cell start; fval[kLearnCells] = 1.
-__global__ void learn_cells_eval_kernel(const __nv_bfloat16* __restrict__ w, const LearnedState* __restrict__ st,
-                                        float* __restrict__ fval) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > uint32_t(kLearnCells)) return;
-  if (i == uint32_t(kLearnCells)) {
-    fval[i] = 1.f;
-    return;
-  }
-  const float x = key_feature(cell_start(i), st->center, st->half);
-  float h1[kH], h2[kH];
-  float v = sigmoid(mlp_forward(w, x, h1, h2));
-  if (!(v >= 0.f)) v = 0.f;  // NaN from a diverged model counts as 0
-  fval[i] = fminf(v, 1.f);
 }
 
 // One block: G_i = (1 - eps) max_{j <= i} F(x_j) + eps clamp((x_i + 1) / 2)
@@ -1203,11 +1446,20 @@ unsigned grid_for(uint64_t n, int threads) { return unsigned((n + threads - 1) /
 }  // namespace
 
 // -------------------------------------------------------------- launchers ----
+// Persistent CTAs for the tensor-core MLP kernels: one per SM at most.
+unsigned tc_grid(uint32_t m) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  const uint32_t steps = (m + kTcTile - 1) / kTcTile;
+  return steps < uint32_t(sms) ? steps : uint32_t(sms);
+}
+
 cudaError_t launch_mlp_grad(const void* w_bf16, const float* x, const float* y, uint32_t m, float* grads, float* loss,
                             cudaStream_t stream) {
   if (!m) return cudaSuccess;
-  mlp_grad_kernel<ArrayIn><<<grid_for(m, kGradThreads), kGradThreads, 0, stream>>>(
-      static_cast<const __nv_bfloat16*>(w_bf16), ArrayIn{x, y}, m, grads, loss);
+  mlp_grad_tc_kernel<ArrayIn><<<tc_grid(m), kTcThreads, 0, stream>>>(static_cast<const __nv_bfloat16*>(w_bf16),
+                                                                      ArrayIn{x, y}, m, grads, loss);
   return cudaGetLastError();
 }
 
@@ -1215,7 +1467,7 @@ cudaError_t launch_mlp_grad_sample(const void* w_bf16, const uint64_t* train, co
                                    uint32_t step, uint64_t seed, float* grads, cudaStream_t stream) {
   if (!m) return cudaSuccess;
   float* loss = const_cast<float*>(&st->loss);
-  mlp_grad_kernel<SampleIn><<<grid_for(m, kGradThreads), kGradThreads, 0, stream>>>(
+  mlp_grad_tc_kernel<SampleIn><<<tc_grid(m), kTcThreads, 0, stream>>>(
       static_cast<const __nv_bfloat16*>(w_bf16), SampleIn{train, st, step, seed}, m, grads, loss);
   return cudaGetLastError();
 }
@@ -1236,7 +1488,8 @@ cudaError_t launch_mlp_adam(float* master, float* grads, float* m1, float* m2, v
 
 cudaError_t launch_mlp_eval(const void* w_bf16, const float* x, uint32_t m, float* out, cudaStream_t stream) {
   if (!m) return cudaSuccess;
-  mlp_eval_kernel<<<grid_for(m, 128), 128, 0, stream>>>(static_cast<const __nv_bfloat16*>(w_bf16), x, m, out);
+  mlp_eval_tc_kernel<XIn, false><<<tc_grid(m), kTcThreads, 0, stream>>>(static_cast<const __nv_bfloat16*>(w_bf16),
+                                                                          XIn{x}, m, out);
   return cudaGetLastError();
 }
 
@@ -1279,8 +1532,8 @@ cudaError_t launch_learn_init_kinks(const uint64_t* train, const LearnedState* s
 
 cudaError_t launch_learn_cells(const void* w_bf16, LearnedState* st, const uint64_t* heavy, float* fval, uint2* cells,
                                cudaStream_t stream) {
-  learn_cells_eval_kernel<<<grid_for(kLearnCells + 1, 128), 128, 0, stream>>>(
-      static_cast<const __nv_bfloat16*>(w_bf16), st, fval);
+  mlp_eval_tc_kernel<CellIn, true><<<tc_grid(kLearnCells), kTcThreads, 0, stream>>>(
+      static_cast<const __nv_bfloat16*>(w_bf16), CellIn{st}, uint32_t(kLearnCells), fval);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   learn_cells_finish_kernel<<<1, kCellThreads, 0, stream>>>(fval, heavy, st, cells);
