@@ -258,6 +258,17 @@ typedef struct fsort_learned_stats {
 FSORT_API fsort_status fsort_learned_fit(fsort_plan* plan, const void* keys, uint64_t n,
                                          const fsort_learned_opts* opts, void* stream);
 
+/* The model-free counterpart of fsort_learned_fit, for measuring what the
+ * network adds (no paper counterpart): the same sample, sorted by the plain
+ * path, the same frequent keys, but the map's table is the sorted sample's
+ * empirical CDF at the cell starts (fraction of its non-frequent keys below
+ * each start) instead of the trained model, with the same uniform floor,
+ * running maximum and judge.  No training runs; the model parameters are left
+ * as they were.  Same arguments, options (steps, batch and lr unused) and
+ * errors as fsort_learned_fit. */
+FSORT_API fsort_status fsort_learned_fit_ecdf(fsort_plan* plan, const void* keys, uint64_t n,
+                                              const fsort_learned_opts* opts, void* stream);
+
 /* Statistics of the last fit and the last judged sort.  Waits for the device. */
 FSORT_API fsort_status fsort_learned_get_stats(fsort_plan* plan, fsort_learned_stats* out);
 

@@ -154,6 +154,7 @@ def load_library():
             "fsort_batch_autotune": ([vp, ctypes.POINTER(FsortSegment), ctypes.c_uint32, i32, i32, vp,
                                       ctypes.POINTER(FsortBatchConfig), ctypes.POINTER(ctypes.c_float)], st),
             "fsort_learned_fit": ([vp, vp, u64, ctypes.POINTER(FsortLearnedOpts), vp], st),
+            "fsort_learned_fit_ecdf": ([vp, vp, u64, ctypes.POINTER(FsortLearnedOpts), vp], st),
             "fsort_learned_get_stats": ([vp, ctypes.POINTER(FsortLearnedStats)], st),
             "fsort_learned_get_model": ([vp, vp, vp, vp, ctypes.POINTER(ctypes.c_uint32), vp], st),
             "fsort_learned_bucket_ids": ([vp, vp, u64, vp, vp], st),
@@ -418,6 +419,13 @@ def fsort_learned_fit(plan, keys, n=None, sample_keys: int = 0, steps: int = 0, 
     o = FsortLearnedOpts(sample_keys, steps, batch, lr, seed)
     _check(load_library().fsort_learned_fit(plan, _ptr(keys), _numel(keys, n), ctypes.byref(o), _stream(stream)),
            "fsort_learned_fit")
+
+
+def fsort_learned_fit_ecdf(plan, keys, n=None, sample_keys: int = 0, seed: int = 0, stream=None) -> None:
+    """Model-free map from the sorted sample's empirical CDF (no training)."""
+    o = FsortLearnedOpts(sample_keys, 0, 0, 0.0, seed)
+    _check(load_library().fsort_learned_fit_ecdf(plan, _ptr(keys), _numel(keys, n), ctypes.byref(o), _stream(stream)),
+           "fsort_learned_fit_ecdf")
 
 
 def fsort_learned_get_stats(plan) -> dict:
@@ -693,6 +701,9 @@ class Plan:
 
     def learned_fit(self, keys, n=None, **opts) -> None:
         fsort_learned_fit(self.handle, keys, n, **opts)
+
+    def learned_fit_ecdf(self, keys, n=None, **opts) -> None:
+        fsort_learned_fit_ecdf(self.handle, keys, n, **opts)
 
     def learned_stats(self) -> dict:
         return fsort_learned_get_stats(self.handle)

@@ -1219,8 +1219,26 @@ fsort_status fsort_expand(fsort_plan* plan, const uint64_t* counts, void* keys_o
   return finish_call(plan, s);
 }
 
+namespace {
+// The learned fit (ecdf false) or its model-free counterpart (ecdf true: the
+// map tabulates the sorted sample's empirical CDF; no training).
+fsort_status learned_fit_impl(fsort_plan* plan, const void* keys, uint64_t n, const fsort_learned_opts* opts,
+                              void* stream, bool ecdf);
+}  // namespace
+
 fsort_status fsort_learned_fit(fsort_plan* plan, const void* keys, uint64_t n, const fsort_learned_opts* opts,
                                void* stream) {
+  return learned_fit_impl(plan, keys, n, opts, stream, false);
+}
+
+fsort_status fsort_learned_fit_ecdf(fsort_plan* plan, const void* keys, uint64_t n, const fsort_learned_opts* opts,
+                                    void* stream) {
+  return learned_fit_impl(plan, keys, n, opts, stream, true);
+}
+
+namespace {
+fsort_status learned_fit_impl(fsort_plan* plan, const void* keys, uint64_t n, const fsort_learned_opts* opts,
+                              void* stream, bool ecdf) {
   if (!plan || !plan->learn) return FSORT_ERR_INVALID_ARG;
   if (!keys || !aligned16(keys) || n < 1 || n > plan->desc.max_n) return FSORT_ERR_INVALID_ARG;
   fsort_learned_opts o{};
@@ -1260,6 +1278,14 @@ fsort_status fsort_learned_fit(fsort_plan* plan, const void* keys, uint64_t n, c
   if (e == cudaSuccess) e = launch_scan_u32(L.flag_hv, S, L.pos_hv, nullptr, L.sums, s);
   if (e == cudaSuccess)
     e = launch_learn_compact(L.sample, S, L.flag_nh, L.pos_nh, L.flag_hv, L.pos_hv, L.train, L.heavy, L.st, s);
+  if (ecdf) {
+    if (e == cudaSuccess) e = launch_learn_cells_ecdf(L.train, L.st, L.heavy, L.fval, L.cells, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    L.fitted = true;
+    L.steps = 0;
+    L.used = -1;
+    return finish_call(plan, s);
+  }
   if (e == cudaSuccess) e = launch_learn_init_kinks(L.train, L.st, L.master, s);
   if (e == cudaSuccess) e = launch_to_bf16(L.master, L.w_bf16, kMlpParams, s);
   // training: Adam on stratified minibatches, cosine decay to lr / 10
@@ -1277,6 +1303,7 @@ fsort_status fsort_learned_fit(fsort_plan* plan, const void* keys, uint64_t n, c
   L.used = -1;
   return finish_call(plan, s);
 }
+}  // namespace
 
 fsort_status fsort_learned_get_stats(fsort_plan* plan, fsort_learned_stats* out) {
   if (!plan || !plan->learn || !out) return FSORT_ERR_INVALID_ARG;

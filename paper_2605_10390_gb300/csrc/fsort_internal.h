@@ -268,6 +268,9 @@ cudaError_t launch_learn_init_kinks(const uint64_t* train, const LearnedState* s
                                     cudaStream_t stream);
 cudaError_t launch_learn_cells(const void* w_bf16, LearnedState* st, const uint64_t* heavy, float* fval, uint2* cells,
                                cudaStream_t stream);
+// The same table from the sorted training sample's empirical CDF (no model).
+cudaError_t launch_learn_cells_ecdf(const uint64_t* train, LearnedState* st, const uint64_t* heavy, float* fval,
+                                    uint2* cells, cudaStream_t stream);
 
 // Exclusive scan of count u32 words (count <= 2^24): out (and out2 if not
 // null); sums: scratch of >= count / 4096 + 1 words.

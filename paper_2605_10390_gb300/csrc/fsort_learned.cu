@@ -685,6 +685,28 @@ __global__ void __launch_bounds__(kCellThreads) learn_cells_finish_kernel(const 
   }
 }
 
+// Model-free map: fval[i] = the empirical CDF of the sorted training sample
+// at cell start i (the fraction of its keys below the start), fval[kLearnCells]
+// = 1.  Followed by the same table kernel as the model's map, it gives the
+// partition the model would give if it matched its training sample exactly.
+__global__ void learn_cells_ecdf_kernel(const uint64_t* __restrict__ train, const LearnedState* __restrict__ st,
+                                        float* __restrict__ fval) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > uint32_t(kLearnCells)) return;
+  if (i == uint32_t(kLearnCells)) {
+    fval[i] = 1.f;
+    return;
+  }
+  const uint32_t cnt = st->train_count;
+  const uint64_t c = cell_start(i);
+  uint32_t lo = 0, hi = cnt;  // first sample key >= c
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (train[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  fval[i] = cnt ? float(double(lo) / double(cnt)) : 0.f;
+}
+
 // --------------------------------------------------------------- sorting ----
 // Bucket id = (super-bucket s = id >> f, fine digit d = id & (2^f - 1)), f in 10..12.  Level 1
 // groups the non-heavy keys by s into the scratch array: each CTA owns a fixed
@@ -1534,6 +1556,15 @@ cudaError_t launch_learn_cells(const void* w_bf16, LearnedState* st, const uint6
                                cudaStream_t stream) {
   mlp_eval_tc_kernel<CellIn, true><<<tc_grid(kLearnCells), kTcThreads, 0, stream>>>(
       static_cast<const __nv_bfloat16*>(w_bf16), CellIn{st}, uint32_t(kLearnCells), fval);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  learn_cells_finish_kernel<<<1, kCellThreads, 0, stream>>>(fval, heavy, st, cells);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_learn_cells_ecdf(const uint64_t* train, LearnedState* st, const uint64_t* heavy, float* fval,
+                                    uint2* cells, cudaStream_t stream) {
+  learn_cells_ecdf_kernel<<<grid_for(kLearnCells + 1, 256), 256, 0, stream>>>(train, st, fval);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   learn_cells_finish_kernel<<<1, kCellThreads, 0, stream>>>(fval, heavy, st, cells);
