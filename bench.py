@@ -60,7 +60,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 32 GB arbitrary-precision configurations")
-    ap.add_argument("--only", choices=["secondary", "expand", "batched", "learned", "serving"],
+    ap.add_argument("--only", choices=["secondary", "expand", "batched", "learned", "serving", "serving_small"],
                     help="run one secondary section alone and print its JSON (profiling and debugging); "
                          "expand: the expand-path cases of the secondary section at --expand-log2n keys")
     ap.add_argument("--expand-log2n", type=int, default=34, help="keys of the expand-path cases (log2)")
@@ -568,6 +568,70 @@ def run_serving(fs, workloads, torch, stream, requests: int = 48, lo: int = 16, 
             "api": "fsort_serve_submit / fsort_serve_wait (pinned host buffers; copies in the latency)"}
 
 
+def run_serving_small(fs, workloads, torch, requests: int = 1024, lo: int = 10, hi: int = 16, load: float = 4.0,
+                      seed: int = 1, lanes: int = 2):
+    """Many small requests (uint64 keys-only 64-bit sorts of the mixture, sizes
+    log-uniform 2^10..2^16 keys) arriving as a Poisson stream at `load` times the
+    rate the loop serves them one at a time (calibrated first, one request in
+    flight): the queue holds several requests whenever a lane frees up, and the
+    loop must batch them to keep up.  Reports the share of requests served in
+    batches and the latency against the single-request service time."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = [int(2 ** (lo + (hi - lo) * u)) for u in rng.random(requests)]
+    maxn = 1 << hi
+    pool = torch.from_numpy(workloads.generate("mixture", 1 << 22, 64, seed=2, stream=11)).pin_memory()
+    ring = 256
+    outs = [torch.empty(maxn, dtype=torch.uint64).pin_memory() for _ in range(ring)]
+    offs = [int(rng.integers(0, pool.numel() - n + 1)) for n in sizes]
+    srv = fs.Server(maxn, 64, False, lanes=lanes, hbm_budget_bytes=64 << 20, batch_keys=maxn, max_batch=64)
+
+    def submit(i, slot):
+        n, o = sizes[i], offs[i]
+        return srv.submit(pool[o:o + n], keys_out_host=outs[slot][:n], n=n, key_bits=64, precision_bits=64)
+
+    cal = list(range(64))
+    for j, i in enumerate(cal):  # untimed: every lane's kernels and buffers in use once
+        srv.wait(submit(i, j % ring))
+    t0 = time.perf_counter()
+    for j, i in enumerate(cal):
+        srv.wait(submit(i, j % ring))
+    service_ms = (time.perf_counter() - t0) * 1e3 / len(cal)
+    rate = load * 1e3 / service_ms
+    gaps = rng.exponential(1.0 / rate, requests)
+    tickets, results = [], {}
+    start = time.perf_counter()
+    at = 0.0
+    for i in range(requests):
+        at += float(gaps[i])
+        if i >= ring:
+            results[i - ring] = srv.wait(tickets[i - ring])
+        delay = start + at - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(submit(i, i % ring))
+    for i in range(max(0, requests - ring), requests):
+        results[i] = srv.wait(tickets[i])
+    span = time.perf_counter() - start
+    st = srv.stats()
+    srv.close()
+    ok = all(bool(np.all(np.diff(outs[i % ring][:sizes[i]].numpy().astype(np.float64)) >= 0))
+             for i in range(max(0, requests - ring), requests))
+    lat = sorted(r["latency_ms"] for r in results.values())
+    rank = lambda q: lat[max(0, min(len(lat), int(np.ceil(q * len(lat)))) - 1)]  # nearest rank
+    batched = sum(1 for r in results.values() if r["batched"])
+    del pool, outs
+    return {"workload": f"{requests} requests, uint64 keys-only 64-bit sorts of the mixture, sizes log-uniform "
+                        f"2^{lo}..2^{hi} (total {sum(sizes)} keys), Poisson arrivals at {rate:.0f}/s "
+                        f"({load:.1f}x the one-at-a-time service rate)",
+            "requests": requests, "lanes": lanes, "single_request_service_ms": service_ms,
+            "p50_ms": rank(0.50), "p99_ms": rank(0.99), "p99_over_service": rank(0.99) / service_ms,
+            "mean_ms": float(np.mean(lat)), "batched_requests": batched, "batched_share": batched / requests,
+            "batches": st.get("batches"), "keys_per_s": sum(sizes) / span, "requests_per_s": requests / span,
+            "outputs_sorted": ok,
+            "api": "fsort_serve_submit / fsort_serve_wait (pinned host buffers; copies in the latency)"}
+
+
 def summary(result: dict) -> dict:
     """The headline and every secondary section in a few hundred characters,
     placed last on the JSON line so that a reader that keeps only its tail
@@ -597,6 +661,11 @@ def summary(result: dict) -> dict:
         out["serving"] = {"p50_ms": r(sv["p50_ms"], 1), "p99_ms": r(sv["p99_ms"], 1),
                           "batched": sv["batched_requests"], "requests": sv.get("requests"),
                           "gkeys_per_s": r(sv["keys_per_s"] / 1e9, 2)}
+    ss = result.get("serving_small")
+    if ss:
+        out["serving_small"] = {"p50_ms": r(ss["p50_ms"], 2), "p99_ms": r(ss["p99_ms"], 2),
+                                "service_ms": r(ss["single_request_service_ms"], 2),
+                                "batched_share": r(ss["batched_share"], 2), "requests": ss["requests"]}
     return out
 
 
@@ -664,6 +733,8 @@ def main():
             out = run_batched(fs, workloads, torch, stream, peak)
         elif args.only == "learned":
             out = run_learned(fs, workloads, torch, stream, peak, log2n=args.learned_log2n)
+        elif args.only == "serving_small":
+            out = run_serving_small(fs, workloads, torch)
         else:
             out = run_serving(fs, workloads, torch, stream)
         print(json.dumps({"section": args.only, "result": out}), flush=True)
@@ -789,6 +860,7 @@ def main():
         result["batched"] = run_batched(fs, workloads, torch, stream, peak)
         result["learned"] = run_learned(fs, workloads, torch, stream, peak)
         result["serving"] = run_serving(fs, workloads, torch, stream)
+        result["serving_small"] = run_serving_small(fs, workloads, torch)
 
     # End to end through the public host-buffer entry point (rank-local).
     e2e = None

@@ -7,8 +7,9 @@
 //             with coalescing on free; a request is admitted when its key
 //             and value buffers fit (admission by free HBM)
 //   queue     FIFO; a free lane takes the head request as soon as it fits,
-//             together with the small requests right behind it (continuous
-//             batching: nothing waits for a batch to fill or to drain)
+//             together with every compatible small request waiting anywhere
+//             behind it that fits too (continuous batching: nothing waits for
+//             a batch to fill or to drain)
 //   latency   steady-clock stamps at submit, admission and completion
 #include <cuda_runtime.h>
 
@@ -156,22 +157,27 @@ void lane_main(fsort_server* s, size_t li) {
         }
         s->cv_work.wait(lk);
       }
-      // small requests right behind a small head join its batch (same precision)
-      // (a batch's keys, each segment rounded up to 8, fit the lane plan's max_n)
+      // A small head takes every compatible small request still waiting into
+      // its batch, in arrival order, as far as each fits the arena (same
+      // precision and values; a batch's keys, each segment rounded up to 8,
+      // fit the lane plan's max_n).  Requests that do not match or do not fit
+      // keep their place in the queue for the next free lane.
       Req* head = batch[0];
       uint64_t total = (head->r.n + 7) / 8 * 8;
       if (head->r.n <= s->desc.batch_keys) {
-        while (batch.size() < max_batch && !s->pending.empty()) {
-          Req* q = s->pending.front();
+        for (auto it = s->pending.begin(); it != s->pending.end() && batch.size() < max_batch;) {
+          Req* q = *it;
+          const uint64_t padded = (q->r.n + 7) / 8 * 8;
+          size_t off = 0;
           if (q->r.n > s->desc.batch_keys || q->r.precision_bits != head->r.precision_bits ||
               (q->r.vals_host == nullptr) != (head->r.vals_host == nullptr) ||
-              total + (q->r.n + 7) / 8 * 8 > s->desc.max_request_keys)
-            break;
-          total += (q->r.n + 7) / 8 * 8;
-          size_t off = 0;
-          if (!s->arena.alloc(q->bytes, &off)) break;
+              total + padded > s->desc.max_request_keys || !s->arena.alloc(q->bytes, &off)) {
+            ++it;
+            continue;
+          }
+          total += padded;
           q->off = off;
-          s->pending.pop_front();
+          it = s->pending.erase(it);
           batch.push_back(q);
         }
       }
