@@ -132,6 +132,13 @@ struct fsort_plan {
   SegDesc* h_seg_large = nullptr;  // pinned staging
   SegDesc* h_seg_small = nullptr;
   HistChunk* h_chunks = nullptr;
+  // table form of the large segments (fsort_batch_config::large_form = 1)
+  uint64_t max_ttiles = 0, max_tchunks = 0;
+  uint32_t* bt_tilerel = nullptr;   // [tiles][256] per-tile digit offsets within the tile's chunk
+  uint32_t* bt_chunksum = nullptr;  // [chunks][256]
+  uint32_t* bt_chunkoff = nullptr;  // [chunks][256], relative to the segment's start
+  uint32_t* d_chunk_seg = nullptr;  // [chunks] segment of each chunk
+  uint32_t* h_chunk_seg = nullptr;  // pinned staging
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   fsort_batch_config bcfg{};
@@ -147,6 +154,7 @@ namespace {
 constexpr int kRadix = 256;
 constexpr size_t kCounterBytes = 256;  // two counters, padded
 constexpr uint64_t kBatchHistChunk = 262144;  // keys per work item of the segmented histogram
+constexpr uint32_t kBatchChunkTiles = 16;     // table form: tiles per count chunk of a large segment
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -508,13 +516,15 @@ void learned_init_params(std::vector<float>& w, uint64_t seed) {
 // batch of the same shape.
 struct BatchShape {
   uint32_t n_large = 0, n_small = 0, n_chunks = 0, total_tiles = 0;
+  uint32_t n_tchunks = 0;  // table form: count chunks over all large segments
   uint64_t alt_total = 0;
   bool has_vals = false;
 };
 
 fsort_status build_batch(fsort_plan* p, const fsort_segment* segs, uint32_t count, int key_bits, BatchShape* out) {
   const int cap = p->bcfg.small_capacity;
-  const uint64_t tile = uint64_t(p->tile);
+  const bool table = p->bcfg.large_form == 1;
+  const uint64_t tile = table ? uint64_t(table_tile_keys_for(key_bits)) : uint64_t(p->tile);
   BatchShape b;
   int vals_state = -1;  // -1 unknown, 0 none, 1 all
   for (uint32_t i = 0; i < count; ++i) {
@@ -539,8 +549,16 @@ fsort_status build_batch(fsort_plan* p, const fsort_segment* segs, uint32_t coun
     b.alt_total += (g.n + 7) / 8 * 8;  // keeps every segment's scratch 16-byte aligned
     if (b.alt_total > p->desc.max_n) return FSORT_ERR_INVALID_ARG;
     const uint64_t tiles = (g.n + tile - 1) / tile;
-    if (uint64_t(b.total_tiles) + tiles > p->max_tiles) return FSORT_ERR_INVALID_ARG;
+    if (uint64_t(b.total_tiles) + tiles > (table ? p->max_ttiles : p->max_tiles)) return FSORT_ERR_INVALID_ARG;
     b.total_tiles += uint32_t(tiles);
+    if (table) {  // count chunks of the segment, and nothing for the segmented histogram
+      const uint64_t nch = (tiles + kBatchChunkTiles - 1) / kBatchChunkTiles;
+      if (uint64_t(b.n_tchunks) + nch > p->max_tchunks) return FSORT_ERR_INVALID_ARG;
+      d.first_chunk = b.n_tchunks;
+      for (uint64_t c = 0; c < nch; ++c) p->h_chunk_seg[b.n_tchunks++] = b.n_large;
+      p->h_seg_large[b.n_large++] = d;
+      continue;
+    }
     for (uint64_t st = 0; st < g.n; st += kBatchHistChunk) {
       if (b.n_chunks >= p->max_hist_chunks) return FSORT_ERR_INVALID_ARG;
       const uint64_t len = (g.n - st < kBatchHistChunk) ? g.n - st : kBatchHistChunk;
@@ -571,7 +589,49 @@ cudaError_t enqueue_batch(fsort_plan* p, const BatchShape& b, int key_bits, int 
                             p->d_small_counter, p->bcfg.small_ctas_per_sm * p->sms, p->side);
     if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->side);
   }
-  if (e == cudaSuccess && b.n_large) {
+  if (e == cudaSuccess && b.n_large && p->bcfg.large_form == 1) {
+    // Table form: per pass, one read of the segments' keys counts every tile
+    // (chunks of kBatchChunkTiles tiles inside one segment), a per-segment
+    // scan turns the counts into offsets, and every tile scatters at once.
+    const uint32_t tile = uint32_t(table_tile_keys_for(key_bits));
+    e = cudaMemcpyAsync(p->d_chunk_seg, p->h_chunk_seg, sizeof(uint32_t) * b.n_tchunks, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_fill_tile_seg(p->d_seg_large, b.n_large, int(tile), p->d_tile_seg, s);
+    for (int j = 0; j < plan.passes && e == cudaSuccess; ++j) {
+      TileCountArgs ca{};
+      ca.keys[kBufAlt] = p->alt_keys;
+      ca.shift = plan.shift[j];
+      ca.mask = plan.mask[j];
+      ca.tile = tile;
+      ca.tiles = b.total_tiles;
+      ca.chunk_tiles = kBatchChunkTiles;
+      ca.tilerel = p->bt_tilerel;
+      ca.chunksum = p->bt_chunksum;
+      ca.pass = j;
+      ca.status = p->status;
+      ca.segs = p->d_seg_large;
+      ca.chunk_seg = p->d_chunk_seg;
+      e = launch_tile_count(ca, key_bits, b.n_tchunks, s);
+      if (e == cudaSuccess)
+        e = launch_seg_chunk_scan(p->bt_chunksum, p->d_seg_large, b.n_large, tile, kBatchChunkTiles, p->bt_chunkoff, s);
+      TileScatterArgs a{};
+      a.keys[kBufAlt] = p->alt_keys;
+      a.vals[kBufAlt] = b.has_vals ? p->alt_vals : nullptr;
+      a.shift = plan.shift[j];
+      a.mask = plan.mask[j];
+      a.tiles = b.total_tiles;
+      a.chunk_tiles = kBatchChunkTiles;
+      a.tilerel = p->bt_tilerel;
+      a.chunkoff = p->bt_chunkoff;
+      a.pass = j;
+      a.status = p->status;
+      a.segs = p->d_seg_large;
+      a.tile_seg = p->d_tile_seg;
+      if (e == cudaSuccess) e = launch_tile_scatter(a, key_bits, b.has_vals, s);
+    }
+    if (e == cudaSuccess && (plan.passes & 1))
+      e = launch_seg_copy_back(p->d_seg_large, b.n_large, p->alt_keys, b.has_vals ? p->alt_vals : nullptr, key_bits,
+                               p->sms, s);
+  } else if (e == cudaSuccess && b.n_large) {  // chained form: segmented decoupled look-back
     e = launch_fill_tile_seg(p->d_seg_large, b.n_large, p->tile, p->d_tile_seg, s);
     if (e == cudaSuccess)
       e = launch_seg_histogram(p->d_seg_large, p->d_chunks, b.n_chunks, key_bits, plan, p->d_bhist, p->counters,
@@ -625,7 +685,8 @@ fsort_status run_batch(fsort_plan* p, const fsort_segment* segs, uint32_t count,
     if (e != cudaSuccess) return from_cuda(e);
     return finish_call(p, s);
   }
-  const uint64_t key[10] = {b.n_large, b.n_small, b.n_chunks, b.total_tiles, b.alt_total, uint64_t(b.has_vals),
+  const uint64_t key[10] = {b.n_large, b.n_small, uint64_t(b.n_chunks) << 32 | b.n_tchunks, b.total_tiles, b.alt_total,
+                            uint64_t(b.has_vals) | uint64_t(p->bcfg.large_form) << 1,
                             uint64_t(key_bits) << 8 | uint64_t(precision_bits), uint64_t(p->bcfg.small_capacity),
                             uint64_t(p->bcfg.small_ctas_per_sm), reinterpret_cast<uint64_t>(s)};
   if (!p->gexec || std::memcmp(key, p->gkey, sizeof(key)) != 0) {
@@ -680,6 +741,7 @@ fsort_status fsort_batch_set_config(fsort_plan* plan, const fsort_batch_config* 
   if (config->small_ctas_per_sm < 1 || config->small_ctas_per_sm > 8) return FSORT_ERR_INVALID_ARG;
   if (c && config->small_ctas_per_sm > small_sort_ctas_per_sm(plan->desc.key_bits, plan->desc.has_values != 0, c))
     return FSORT_ERR_INVALID_ARG;  // more CTAs than shared memory holds at once
+  if (config->large_form != 0 && config->large_form != 1) return FSORT_ERR_INVALID_ARG;
   plan->bcfg = *config;
   return FSORT_OK;
 }
@@ -705,26 +767,46 @@ fsort_status fsort_batch_autotune(fsort_plan* plan, const fsort_segment* segment
   fsort_batch_config winner = saved;
   float winner_ms = -1.f;
   const bool hv = plan->desc.has_values != 0;
+  // one timed batch (after a warm-up one) under the plan's current config
+  auto time_config = [&](float* ms) -> fsort_status {
+    fsort_status r = run_batch(plan, segments, count, key_bits, precision_bits, s, false);  // warm-up
+    if (r == FSORT_OK && cudaEventRecord(e0, s) != cudaSuccess) r = FSORT_ERR_CUDA;
+    if (r == FSORT_OK) r = run_batch(plan, segments, count, key_bits, precision_bits, s, false);
+    if (r == FSORT_OK && cudaEventRecord(e1, s) != cudaSuccess) r = FSORT_ERR_CUDA;
+    if (r == FSORT_OK && cudaEventSynchronize(e1) != cudaSuccess) r = FSORT_ERR_CUDA;
+    if (r == FSORT_OK && cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) r = FSORT_ERR_CUDA;
+    return r;
+  };
+  auto consider = [&](float ms) {
+    if (winner_ms < 0.f || ms < winner_ms) {
+      winner_ms = ms;
+      winner = plan->bcfg;
+    }
+  };
+  // Coordinate search: the large segments' form under the current small-segment
+  // configuration, then every small-segment configuration under that form.
+  for (int form : {1, 0}) {
+    plan->bcfg = saved;
+    plan->bcfg.large_form = form;
+    float ms = 0.f;
+    st = time_config(&ms);
+    if (st != FSORT_OK) break;
+    consider(ms);
+  }
+  const int form = winner.large_form;
   for (int cap : {0, 1024, 2048, 4096}) {
+    if (st != FSORT_OK) break;
     const int most = cap ? small_sort_ctas_per_sm(key_bits, hv, cap) : 1;
     for (int ctas : {most, (most + 1) / 2}) {
       if (cap == 0 && ctas != most) continue;
       plan->bcfg.small_capacity = cap;
       plan->bcfg.small_ctas_per_sm = ctas;
-      st = run_batch(plan, segments, count, key_bits, precision_bits, s, false);  // warm-up
-      if (st == FSORT_OK && cudaEventRecord(e0, s) != cudaSuccess) st = FSORT_ERR_CUDA;
-      if (st == FSORT_OK) st = run_batch(plan, segments, count, key_bits, precision_bits, s, false);
-      if (st == FSORT_OK && cudaEventRecord(e1, s) != cudaSuccess) st = FSORT_ERR_CUDA;
-      if (st == FSORT_OK && cudaEventSynchronize(e1) != cudaSuccess) st = FSORT_ERR_CUDA;
+      plan->bcfg.large_form = form;
       float ms = 0.f;
-      if (st == FSORT_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = FSORT_ERR_CUDA;
+      st = time_config(&ms);
       if (st != FSORT_OK) break;
-      if (winner_ms < 0.f || ms < winner_ms) {
-        winner_ms = ms;
-        winner = plan->bcfg;
-      }
+      consider(ms);
     }
-    if (st != FSORT_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -803,6 +885,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   }
   const int pmax = desc->key_bits / 8;
   size_t o_bsl = 0, o_bss = 0, o_bch = 0, o_bts = 0, o_bh = 0, o_bb = 0, o_bctr = 0;
+  size_t o_btr = 0, o_btcs = 0, o_btco = 0, o_btseg = 0;
   if (batch) {
     p->max_hist_chunks = n / kBatchHistChunk + desc->max_segments + 1;
     o_bsl = take(size_t(desc->max_segments) * sizeof(SegDesc));
@@ -812,6 +895,13 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     o_bh = take(size_t(desc->max_segments) * pmax * kRadix * 8);
     o_bb = take(size_t(desc->max_segments) * pmax * kRadix * 8);
     o_bctr = take(4);
+    const uint64_t tt = uint64_t(table_tile_keys_for(desc->key_bits));
+    p->max_ttiles = n / tt + desc->max_segments + 1;  // every segment may add one partial tile
+    p->max_tchunks = p->max_ttiles / kBatchChunkTiles + desc->max_segments + 1;
+    o_btr = take(size_t(p->max_ttiles) * kRadix * 4);
+    o_btcs = take(size_t(p->max_tchunks) * kRadix * 4);
+    o_btco = take(size_t(p->max_tchunks) * kRadix * 4);
+    o_btseg = take(size_t(p->max_tchunks) * 4);
   }
   const bool leaf = desc->key_bits == 16;
   if (leaf) {
@@ -900,6 +990,10 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     p->d_bhist = reinterpret_cast<uint64_t*>(w + o_bh);
     p->d_bbases = reinterpret_cast<uint64_t*>(w + o_bb);
     p->d_small_counter = reinterpret_cast<uint32_t*>(w + o_bctr);
+    p->bt_tilerel = reinterpret_cast<uint32_t*>(w + o_btr);
+    p->bt_chunksum = reinterpret_cast<uint32_t*>(w + o_btcs);
+    p->bt_chunkoff = reinterpret_cast<uint32_t*>(w + o_btco);
+    p->d_chunk_seg = reinterpret_cast<uint32_t*>(w + o_btseg);
   }
   if (leaf) {
     p->leaf_part = reinterpret_cast<uint32_t*>(w + o_lpart);
@@ -970,6 +1064,8 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     e = cudaMallocHost(reinterpret_cast<void**>(&p->h_seg_small), sizeof(SegDesc) * desc->max_segments);
   if (e == cudaSuccess && batch)
     e = cudaMallocHost(reinterpret_cast<void**>(&p->h_chunks), sizeof(HistChunk) * p->max_hist_chunks);
+  if (e == cudaSuccess && batch)
+    e = cudaMallocHost(reinterpret_cast<void**>(&p->h_chunk_seg), sizeof(uint32_t) * p->max_tchunks);
   if (e == cudaSuccess && batch) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
   if (e == cudaSuccess && batch) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess && batch) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
@@ -985,6 +1081,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   if (batch) {
     p->bcfg.small_capacity = 4096;
     p->bcfg.small_ctas_per_sm = small_sort_ctas_per_sm(desc->key_bits, desc->has_values != 0, 4096);
+    p->bcfg.large_form = 1;
   }
   *out_plan = p;
   return FSORT_OK;
@@ -1002,6 +1099,7 @@ fsort_status fsort_plan_destroy(fsort_plan* plan) {
   if (plan->h_seg_large) cudaFreeHost(plan->h_seg_large);
   if (plan->h_seg_small) cudaFreeHost(plan->h_seg_small);
   if (plan->h_chunks) cudaFreeHost(plan->h_chunks);
+  if (plan->h_chunk_seg) cudaFreeHost(plan->h_chunk_seg);
   if (plan->done) cudaEventDestroy(plan->done);
   if (plan->h_status) cudaFreeHost(plan->h_status);
   fsort_plan_set_timing(plan, 0);

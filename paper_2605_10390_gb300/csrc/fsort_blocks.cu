@@ -119,22 +119,38 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
   __shared__ uint64_t s_bar[kCountStages];
   __shared__ uint32_t s_fail[2];  // by tile parity: a tile reads only its own flag after its barrier
   K* buf = reinterpret_cast<K*>(smem);
+  // The chunk: tiles [t_begin, t_end) of an array of n_keys keys; g_tile0 is
+  // the global index (into tilerel) of tile t_begin.
   const K* keys;
-  if (a.sched) {
-    const PassDesc pd = a.sched->pass[a.pass];
-    if (!pd.active) return;
-    keys = static_cast<const K*>(pick(a.keys, pd.src));
+  uint32_t t_begin, t_end, g_tile0;
+  uint64_t n_keys;
+  if (a.segs) {
+    const SegDesc sd = a.segs[a.chunk_seg[blockIdx.x]];
+    keys = (a.pass & 1) ? static_cast<const K*>(a.keys[kBufAlt]) + sd.alt_off : static_cast<const K*>(sd.keys);
+    n_keys = sd.n;
+    const uint32_t seg_tiles = uint32_t((sd.n + kTileKeys - 1) / kTileKeys);
+    t_begin = (blockIdx.x - sd.first_chunk) * a.chunk_tiles;
+    t_end = (t_begin + a.chunk_tiles < seg_tiles) ? t_begin + a.chunk_tiles : seg_tiles;
+    g_tile0 = sd.first_tile + t_begin;
   } else {
-    keys = static_cast<const K*>(a.keys[kBufIn]);
+    if (a.sched) {
+      const PassDesc pd = a.sched->pass[a.pass];
+      if (!pd.active) return;
+      keys = static_cast<const K*>(pick(a.keys, pd.src));
+    } else {
+      keys = static_cast<const K*>(a.keys[kBufIn]);
+    }
+    n_keys = a.n;
+    t_begin = blockIdx.x * a.chunk_tiles;
+    t_end = (t_begin + a.chunk_tiles < a.tiles) ? t_begin + a.chunk_tiles : a.tiles;
+    g_tile0 = t_begin;
   }
   const int tid = threadIdx.x;
-  const uint32_t t_begin = blockIdx.x * a.chunk_tiles;
-  const uint32_t t_end = (t_begin + a.chunk_tiles < a.tiles) ? t_begin + a.chunk_tiles : a.tiles;
   const uint32_t steps = t_end - t_begin;
   // step s counts tile t_begin + s: keys [e0, e1); its body of whole 16-byte vectors is copied in bulk
   auto step_range = [&](uint32_t st, uint64_t& e0, uint64_t& e1) {
     e0 = uint64_t(t_begin + st) * kTileKeys;
-    e1 = (e0 + kTileKeys < a.n) ? e0 + kTileKeys : a.n;
+    e1 = (e0 + kTileKeys < n_keys) ? e0 + kTileKeys : n_keys;
   };
   auto issue = [&](uint32_t st) {  // thread 0 only
     uint64_t e0, e1;
@@ -213,7 +229,7 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
       return;
     }
     if (tid < kRadix) {  // meanwhile the next tile counts into the other set
-      a.tilerel[uint64_t(t_begin + st) * kRadix + tid] = acc;
+      a.tilerel[uint64_t(g_tile0 + st) * kRadix + tid] = acc;
       // digit tid's 16 copies, visited in a rotated order so that the warp's
       // 32 reads fall in 32 banks (bank 16 (tid & 1) + copy)
       const uint32_t* row = s_cnt[set][tid];
@@ -232,7 +248,7 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
   }
   if (tid < kRadix) {
     a.chunksum[uint64_t(blockIdx.x) * kRadix + tid] = acc;
-    if (acc) atomicAdd(&a.totals[tid], acc);
+    if (acc && a.totals) atomicAdd(&a.totals[tid], acc);
   }
   if (kOrAnd) {
     if (sizeof(K) == 8) {
@@ -317,6 +333,29 @@ __global__ void __launch_bounds__(kScanThreads) chunk_scan_kernel(const uint32_t
   }
 }
 
+// Segmented KT2, one CTA (256 threads, thread d = digit d) per segment: the
+// segment's count of digit d is the sum over its chunks; its exclusive scan
+// over the digits places the segment's digit runs, and each chunk's offset
+// adds the counts of d in the segment's earlier chunks (offsets relative to
+// the segment's start; a segment holds fewer than 2^31 keys).
+__global__ void __launch_bounds__(kRadix) seg_chunk_scan_kernel(const uint32_t* __restrict__ sum,
+                                                               const SegDesc* __restrict__ segs, uint32_t tile,
+                                                               uint32_t chunk_tiles, uint32_t* __restrict__ off) {
+  __shared__ uint32_t s_warp[kRadix / 32];
+  const SegDesc sd = segs[blockIdx.x];
+  const uint32_t d = threadIdx.x;
+  const uint32_t seg_tiles = uint32_t((sd.n + tile - 1) / tile);
+  const uint32_t c0 = sd.first_chunk, c1 = c0 + (seg_tiles + chunk_tiles - 1) / chunk_tiles;
+  uint32_t total = 0;
+  for (uint32_t c = c0; c < c1; ++c) total += sum[uint64_t(c) * kRadix + d];
+  uint32_t run = digit_excl_scan<kRadix>(total, s_warp);
+  for (uint32_t c = c0; c < c1; ++c) {
+    const uint32_t x = sum[uint64_t(c) * kRadix + d];
+    off[uint64_t(c) * kRadix + d] = run;
+    run += x;
+  }
+}
+
 // ------------------------------------------------------------------ KT3 ----
 template <typename K, bool kVals>
 struct TileSmem {
@@ -380,25 +419,52 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
 
   // the chunk scan of this pass has read the totals: leave them zero for the next count
   if (blockIdx.x == 0 && tid < kRadix && a.totals) a.totals[tid] = 0;
-  int src = kBufIn, dst = kBufOut;
-  if (a.sched) {
-    const PassDesc pd = a.sched->pass[a.pass];
-    if (!pd.active) return;
-    src = pd.src;
-    dst = pd.dst;
+  // Where the tile's keys come from and go to: t0 is its first key in an
+  // array of n_keys keys, chunk its count chunk.
+  const uint32_t tile = blockIdx.x;
+  const K* kin;
+  const uint32_t* vin;
+  K* kout;
+  uint32_t* vout;
+  uint64_t t0, n_keys;
+  uint32_t chunk;
+  if (a.segs) {
+    const SegDesc sd = a.segs[a.tile_seg[tile]];
+    K* own_k = static_cast<K*>(sd.keys);
+    K* alt_k = const_cast<K*>(static_cast<const K*>(a.keys[kBufAlt])) + sd.alt_off;
+    uint32_t* alt_v = kVals ? const_cast<uint32_t*>(a.vals[kBufAlt]) + sd.alt_off : nullptr;
+    const bool even = (a.pass & 1) == 0;
+    kin = even ? own_k : alt_k;
+    vin = even ? sd.vals : alt_v;
+    kout = even ? alt_k : own_k;
+    vout = even ? alt_v : sd.vals;
+    t0 = uint64_t(tile - sd.first_tile) * kTile;
+    n_keys = sd.n;
+    chunk = sd.first_chunk + (tile - sd.first_tile) / a.chunk_tiles;
+  } else {
+    int src = kBufIn, dst = kBufOut;
+    if (a.sched) {
+      const PassDesc pd = a.sched->pass[a.pass];
+      if (!pd.active) return;
+      src = pd.src;
+      dst = pd.dst;
+    }
+    kin = static_cast<const K*>(pick(a.keys, src));
+    vin = pick(a.vals, src);
+    kout = const_cast<K*>(static_cast<const K*>(pick(a.keys, dst)));
+    vout = const_cast<uint32_t*>(pick(a.vals, dst));
+    t0 = uint64_t(tile) * kTile;
+    n_keys = a.n;
+    chunk = tile / a.chunk_tiles;
   }
   if (ld_relaxed_gpu(a.status) & kDevBadTable) return;  // the offsets are not trustworthy: write nothing
-  const uint32_t tile = blockIdx.x;
-  const uint64_t t0 = uint64_t(tile) * kTile;
-  const uint32_t tile_n = uint32_t((a.n - t0 < uint64_t(kTile)) ? (a.n - t0) : uint64_t(kTile));
+  const uint32_t tile_n = uint32_t((n_keys - t0 < uint64_t(kTile)) ? (n_keys - t0) : uint64_t(kTile));
 
   // 1. stage the tile: bulk copies for the 16-byte-aligned body, plain loads
   // for a ragged end; meanwhile clear the warp counters and read the tile's
   // offsets from the table.
   const uint32_t kbody = (tile_n * uint32_t(sizeof(K))) & ~15u;
   const uint32_t vbody = kVals ? ((tile_n * 4u) & ~15u) : 0u;
-  const K* kin = static_cast<const K*>(pick(a.keys, src));
-  const uint32_t* vin = pick(a.vals, src);
   if (tid == 0) {
     mbar_init(s_bar, 1);
     fence_mbar_init();
@@ -411,7 +477,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
     for (int i = tid; i < kWarps * kRadix / 4; i += kBlock) z[i] = make_uint4(0, 0, 0, 0);
   }
   if (tid < kRadix)  // lands while the copy does
-    s_off[tid] = a.chunkoff[uint64_t(tile / a.chunk_tiles) * kRadix + tid] + a.tilerel[uint64_t(tile) * kRadix + tid];
+    s_off[tid] = a.chunkoff[uint64_t(chunk) * kRadix + tid] + a.tilerel[uint64_t(tile) * kRadix + tid];
   for (uint32_t i = kbody / sizeof(K) + tid; i < tile_n; i += kBlock) s_keys[i] = kin[t0 + i];
   if (kVals)
     for (uint32_t i = vbody / 4 + tid; i < tile_n; i += kBlock) s_vals[i] = vin[t0 + i];
@@ -515,8 +581,6 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   __syncthreads();
 
   // 5. write-out in digit runs, consecutive threads to consecutive addresses
-  K* kout = const_cast<K*>(static_cast<const K*>(pick(a.keys, dst)));
-  uint32_t* vout = const_cast<uint32_t*>(pick(a.vals, dst));
   const uint32_t* s_rec32 = reinterpret_cast<const uint32_t*>(smem + L::kKeys);
   const uint16_t* s_src = reinterpret_cast<const uint16_t*>(smem + L::kSrc);
 #pragma unroll 4
@@ -602,6 +666,13 @@ cudaError_t launch_chunk_scan(const uint32_t* chunksum, const uint32_t* totals, 
                               const Schedule* sched, int pass, uint32_t* chunkoff, cudaStream_t stream) {
   if (!chunks) return cudaSuccess;
   chunk_scan_kernel<<<kRadix, kScanThreads, 0, stream>>>(chunksum, totals, chunks, sched, pass, chunkoff);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_chunk_scan(const uint32_t* chunksum, const SegDesc* segs, uint32_t nsegs, uint32_t tile,
+                                  uint32_t chunk_tiles, uint32_t* chunkoff, cudaStream_t stream) {
+  if (!nsegs) return cudaSuccess;
+  seg_chunk_scan_kernel<<<nsegs, kRadix, 0, stream>>>(chunksum, segs, tile, chunk_tiles, chunkoff);
   return cudaGetLastError();
 }
 

@@ -58,8 +58,8 @@ struct SegDesc {
   uint32_t* vals;       // the caller's values, or null
   uint64_t n;           // keys in the segment
   uint64_t alt_off;     // element offset of the segment's ping-pong space in the plan scratch
-  uint32_t first_tile;  // global index of the segment's first scatter tile
-  uint32_t pad;
+  uint32_t first_tile;   // global index of the segment's first scatter tile
+  uint32_t first_chunk;  // table form: global index of the segment's first count chunk
 };
 
 // K3: one stable scatter pass.
@@ -134,8 +134,21 @@ struct TileCountArgs {
   int32_t pass;
   int32_t pad2;
   uint32_t* status;  // a failed bounded wait sets kDevBadTable: the scatter then writes nothing
+  // Segmented mode (segs != null; batched sorts): chunk c belongs to segment
+  // chunk_seg[c] and covers chunk_tiles of its tiles (the segment's last chunk
+  // may hold fewer); even passes read the segment's own keys, odd passes its
+  // scratch space keys[kBufAlt] + alt_off; tilerel is indexed by global tile
+  // (SegDesc::first_tile), totals and orand are unused.
+  const SegDesc* segs = nullptr;
+  const uint32_t* chunk_seg = nullptr;
 };
 cudaError_t launch_tile_count(const TileCountArgs& a, int key_bits, uint32_t chunks, cudaStream_t stream);
+// Segmented KT2: for every segment (one CTA each) and digit d, the exclusive
+// scan over digits of the segment's totals (the sums of its chunks' counts)
+// plus the counts of d in its earlier chunks: chunkoff[c][d], relative to the
+// segment's start.
+cudaError_t launch_seg_chunk_scan(const uint32_t* chunksum, const SegDesc* segs, uint32_t nsegs, uint32_t tile,
+                                  uint32_t chunk_tiles, uint32_t* chunkoff, cudaStream_t stream);
 // The pass schedule from the keys' OR and AND (a pass is trivial when they
 // agree on its digit); resets the accumulators.
 cudaError_t launch_table_schedule(uint64_t* orand, const DigitPlan& plan, int in_place, Schedule* sched,
@@ -161,6 +174,11 @@ struct TileScatterArgs {
   int32_t pass;
   int32_t pad2;
   uint32_t* status;
+  // Segmented mode (segs != null): tile t belongs to segment tile_seg[t]; its
+  // offsets are chunkoff[first_chunk + local tile / chunk_tiles] + tilerel[t];
+  // even passes write the segment's scratch space, odd passes its own buffers.
+  const SegDesc* segs = nullptr;
+  const uint32_t* tile_seg = nullptr;
 };
 cudaError_t launch_tile_scatter(const TileScatterArgs& a, int key_bits, bool has_vals, cudaStream_t stream);
 

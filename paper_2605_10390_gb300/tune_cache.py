@@ -27,7 +27,7 @@ import tempfile
 
 from ._binding import _numel, fsort_batch_autotune, fsort_batch_set_config
 
-VERSION = 1
+VERSION = 2
 CAPACITIES = (0, 1024, 2048, 4096)  # 0: no on-chip path
 MAX_CTAS_PER_SM = 8
 SIZE_CLASSES = (1024, 2048, 4096)   # upper bounds of the on-chip classes; larger segments form the last class
@@ -69,13 +69,16 @@ def current_device_key() -> str:
     return device_key(props.name, props.multi_processor_count, props.major, props.minor)
 
 
+CONFIG_KEYS = ("small_capacity", "small_ctas_per_sm", "large_form")
+
+
 def valid_config(cfg) -> bool:
     if not isinstance(cfg, dict):
         return False
-    cap, ctas = cfg.get("small_capacity"), cfg.get("small_ctas_per_sm")
-    if not isinstance(cap, int) or not isinstance(ctas, int) or isinstance(cap, bool) or isinstance(ctas, bool):
+    cap, ctas, form = cfg.get("small_capacity"), cfg.get("small_ctas_per_sm"), cfg.get("large_form")
+    if any(not isinstance(v, int) or isinstance(v, bool) for v in (cap, ctas, form)):
         return False
-    return cap in CAPACITIES and 1 <= ctas <= MAX_CTAS_PER_SM
+    return cap in CAPACITIES and 1 <= ctas <= MAX_CTAS_PER_SM and form in (0, 1)
 
 
 class TuneCache:
@@ -97,13 +100,12 @@ class TuneCache:
 
     def get(self, device: str, cls: str) -> dict | None:
         e = self.entries.get(f"{device}|{cls}")
-        return None if e is None else {"small_capacity": e["small_capacity"],
-                                       "small_ctas_per_sm": e["small_ctas_per_sm"]}
+        return None if e is None else {k: e[k] for k in CONFIG_KEYS}
 
     def put(self, device: str, cls: str, cfg: dict, ms: float | None = None) -> None:
         if not valid_config(cfg):
             raise ValueError(f"not a batch configuration: {cfg!r}")
-        e = {"small_capacity": cfg["small_capacity"], "small_ctas_per_sm": cfg["small_ctas_per_sm"]}
+        e = {k: cfg[k] for k in CONFIG_KEYS}
         if ms is not None:
             e["ms"] = float(ms)
         self.entries[f"{device}|{cls}"] = e
@@ -143,7 +145,7 @@ def autotune_cached(plan, segments, key_bits: int, precision_bits=None, *, has_v
     cache = TuneCache(path)
     cfg = cache.get(dev, cls)
     if cfg is not None:
-        fsort_batch_set_config(plan, cfg["small_capacity"], cfg["small_ctas_per_sm"])
+        fsort_batch_set_config(plan, cfg["small_capacity"], cfg["small_ctas_per_sm"], cfg["large_form"])
         return cfg, cache.entries[f"{dev}|{cls}"].get("ms"), True
     cfg, ms = fsort_batch_autotune(plan, segments, key_bits, precision_bits, stream)
     cache.put(dev, cls, cfg, ms)

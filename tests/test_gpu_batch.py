@@ -48,23 +48,34 @@ def check_batch(kb, p, host, dev):
 SIZES = [0, 1, 7, 100, 1024, 1025, 2048, 4095, 4096, 4097, 6144, 8192, 30011, 100000, 262145, 5, 3000]
 
 
+FORMS = {"table": 1, "chained": 0}  # how the larger segments' passes scatter (fsort_batch_config::large_form)
+
+
+def set_form(plan, form):
+    cfg = fs.fsort_batch_get_config(plan.handle)
+    fs.fsort_batch_set_config(plan.handle, cfg["small_capacity"], cfg["small_ctas_per_sm"], FORMS[form])
+
+
 @pytest.mark.parametrize("kb,p", [(16, 16), (16, 11), (32, 32), (32, 17), (64, 64), (64, 24)])
 @pytest.mark.parametrize("with_vals", [True, False])
-def test_batch_matches_oracle(kb, p, with_vals):
+@pytest.mark.parametrize("form", list(FORMS))
+def test_batch_matches_oracle(kb, p, with_vals, form):
     host, dev = make_batch(kb, SIZES, with_vals, seed=kb + p)
     total = sum(SIZES) + 8 * len(SIZES)
     with fs.Plan(total, kb, has_values=with_vals, max_segments=64) as plan:
+        set_form(plan, form)
         plan.sort_batch(dev, precision_bits=p)
         plan.sync()
         check_batch(kb, p, host, dev)
 
 
 @pytest.mark.parametrize("cap", [0, 1024, 2048, 4096])
-def test_batch_every_small_capacity(cap):
+@pytest.mark.parametrize("form", list(FORMS))
+def test_batch_every_small_capacity(cap, form):
     kb, p = 32, 32
     host, dev = make_batch(kb, SIZES, True, seed=cap)
     with fs.Plan(sum(SIZES) + 8 * len(SIZES), kb, has_values=True, max_segments=64) as plan:
-        fs.fsort_batch_set_config(plan.handle, cap, 1)
+        fs.fsort_batch_set_config(plan.handle, cap, 1, FORMS[form])
         plan.sort_batch(dev, precision_bits=p)
         plan.sync()
         check_batch(kb, p, host, dev)
@@ -91,7 +102,7 @@ def test_batch_autotune_sorts_and_picks_a_config():
     host, dev = make_batch(kb, sizes, True, seed=7)
     with fs.Plan(sum(sizes) + 64, kb, has_values=True, max_segments=16) as plan:
         cfg, ms = fs.fsort_batch_autotune(plan.handle, dev, kb, p)
-        assert cfg["small_capacity"] in (0, 1024, 2048, 4096) and ms > 0
+        assert cfg["small_capacity"] in (0, 1024, 2048, 4096) and cfg["large_form"] in (0, 1) and ms > 0
         assert fs.fsort_batch_get_config(plan.handle) == cfg
         check_batch(kb, p, host, dev)
 
