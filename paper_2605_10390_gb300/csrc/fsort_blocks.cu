@@ -49,7 +49,7 @@ struct TileShape<uint16_t> { static constexpr int kBlock = 512, kIpt = 22, kMinB
 template <>
 struct TileShape<uint32_t> { static constexpr int kBlock = 512, kIpt = 16, kMinBlocks = 2; };
 template <>
-struct TileShape<uint64_t> { static constexpr int kBlock = 512, kIpt = 8, kMinBlocks = 2; };
+struct TileShape<uint64_t> { static constexpr int kBlock = 512, kIpt = 12, kMinBlocks = 2; };
 
 // Buffer `sel` of a by-BufSel triple, selected without indexing the
 // parameter array (which would copy it to local memory).
@@ -68,10 +68,9 @@ __device__ __forceinline__ T* pick(T* const (&b)[3], int sel) {
 // digit) exactly when the two agree on the digit's bits, so the schedule needs
 // no histogram of the other passes.  The chunk streams through kCountStages
 // shared-memory buffers of one tile each, filled by bulk copies while earlier
-// tiles are counted.  Each thread counts kCountVecs 16-byte vectors of a full
-// tile, so the count CTA has tile / (16-byte vector keys * kCountVecs) threads.
+// tiles are counted.  Each thread counts count_vecs 16-byte vectors of a full
+// tile, so the count CTA has tile / (16-byte vector keys * count_vecs) threads.
 constexpr int kCountStages = 3;
-constexpr int kCountVecs = 2;
 
 // Count CTAs per SM: two for 16-bit keys (3 x 22 KB of buffers and 32 KB of
 // counters each), one for wider keys.
@@ -81,9 +80,15 @@ template <typename K>
 __host__ __device__ constexpr uint32_t count_tile_keys() {
   return uint32_t(TileShape<K>::kBlock) * TileShape<K>::kIpt;
 }
+// 16-byte vectors per count thread per tile: the fewest that keep the CTA at
+// 1024 threads or fewer.
+template <typename K>
+__host__ __device__ constexpr int count_vecs() {
+  return int((count_tile_keys<K>() / (16 / sizeof(K)) + 1023) / 1024);
+}
 template <typename K>
 __host__ __device__ constexpr int count_threads() {
-  return int(count_tile_keys<K>() / (16 / sizeof(K)) / kCountVecs);
+  return int(count_tile_keys<K>() / (16 / sizeof(K)) / count_vecs<K>());
 }
 template <typename K>
 __host__ __device__ constexpr size_t count_smem_bytes() {
@@ -106,6 +111,7 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
   constexpr uint32_t kTileKeys = count_tile_keys<K>();
   constexpr uint32_t kVec = 16 / sizeof(K);
   static_assert(kThreads >= kRadix && kThreads % 32 == 0 && kThreads <= 1024, "one thread per digit");
+  constexpr int kCountVecs = count_vecs<K>();
   static_assert(uint32_t(kThreads) * kVec * kCountVecs == kTileKeys, "threads cover a tile exactly");
   extern __shared__ __align__(128) unsigned char smem[];  // [kCountStages][tile keys]
   // Running counts of the chunk's tiles so far, tiles alternating between two

@@ -21,7 +21,7 @@ if not torch.cuda.is_available():  # collected on CPU-only machines, never run t
 import paper_2605_10390_gb300 as fs  # noqa: E402
 
 TILE = {16: 8192, 32: 6144, 64: 4096}        # chained scatter form
-TABLE_TILE = {16: 11264, 32: 8192, 64: 4096}  # scatter form over the tile-offset table
+TABLE_TILE = {16: 11264, 32: 8192, 64: 6144}  # scatter form over the tile-offset table
 DISTS = ["uniform", "zipf1.1", "gauss", "presorted", "equal"]
 
 
