@@ -213,10 +213,16 @@ __global__ void schedule_copy_kernel(const K* k0, const K* k1, const K* k2, cons
 // --------------------------------------------------------------- K1' -------
 // 65,536 counters of 16 bits, two per 32-bit shared-memory word (128 KB):
 // word w holds key w in its low half and key w + 32768 in its high half, so
-// the small, frequent keys of skewed inputs sit in different words, and the
-// lanes that count the same key add the same value to the same word, which
-// the shared-memory units combine.  Counters are added with red.shared (no
-// return value).
+// the small, frequent keys of skewed inputs sit in different words.  Counters
+// are added with red.shared (no return value).  The lanes of one instruction
+// that hit the same word are served one at a time, like a bank conflict, so a
+// key that many lanes share costs as many passes.  So each warp keeps a
+// candidate frequent key: every fourth round it checks the candidate against
+// 32 of its keys (the lanes' first ones) with one ballot, takes the better of
+// two new candidates from rotating lanes when the old one is not among them
+// twice, and, when two or more lanes hold the candidate, counts that key in a
+// register for four rounds (the other keys' additions predicated, no branch
+// per key) and adds it once per warp at each round's end.
 //
 // Overflow is exact (the tapered width of Sec. III-D-1 with an exact spill):
 // a drain after every two rounds hands each counter's multiples of 2^14 to its
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
   // counted, so the loads overlap the counting and the drains.
   const uint64_t rounds = (n + kLeafRound - 1) / kLeafRound;
   auto add = [&](uint32_t k) { atomicAdd(&hw[k & 32767u], 1u << ((k >> 15) * 16)); };
+  const uint32_t hw_s = static_cast<uint32_t>(__cvta_generic_to_shared(hw));
   auto full = [&](uint64_t r) { return (r + 1) * kLeafRound <= n; };
   uint4 q[kLeafVecPerThread];
   auto load = [&](uint64_t r) {
@@ -252,7 +259,9 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
   };
   uint64_t r = blockIdx.x;
   if (r < rounds && full(r)) load(r);
-  uint32_t done = 0;  // rounds this CTA has counted
+  uint32_t done = 0;               // rounds this CTA has counted
+  uint32_t cand = 0xFFFFFFFFu;     // the warp's candidate frequent key (none yet)
+  bool hot_on = false;             // whether this round counts the candidate in a register
   for (; r < rounds; r += gridDim.x) {
     const uint64_t next = r + gridDim.x;
     if (full(r)) {
@@ -260,13 +269,55 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
 #pragma unroll
       for (int u = 0; u < kLeafVecPerThread; ++u) cur[u] = q[u];
       if (next < rounds && full(next)) load(next);
+      if ((done & 3u) == 0) {  // the decision holds for four rounds
+        const uint32_t s0 = cur[0].x & 0xFFFFu;
+        uint32_t seen = __ballot_sync(0xffffffffu, s0 == cand);
+        if (__popc(seen) < 2) {  // two new candidates, from lanes j and j + 16
+          const uint32_t j = (done >> 2) & 15u;
+          const uint32_t c0 = __shfl_sync(0xffffffffu, s0, j), c1 = __shfl_sync(0xffffffffu, s0, j + 16u);
+          const uint32_t n0 = __popc(__ballot_sync(0xffffffffu, s0 == c0));
+          const uint32_t n1 = __popc(__ballot_sync(0xffffffffu, s0 == c1));
+          cand = n1 > n0 ? c1 : c0;
+          seen = n1 > n0 ? n1 : n0;
+        } else {
+          seen = 2;
+        }
+        hot_on = seen >= 2;
+      }
+      if (hot_on) {  // warp-uniform
+        const uint32_t hot = cand;
+        uint32_t ch = 0;
+        // a predicated red (no branch per key) for every other key; a count for the hot one
+        auto add_hot = [&](uint32_t k) {
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "setp.eq.u32 p, %1, %2;\n\t"
+              "@!p red.shared.add.u32 [%3], %4;\n\t"
+              "@p add.u32 %0, %0, 1;\n\t}"
+              : "+r"(ch)
+              : "r"(k), "r"(hot), "r"(hw_s + (k & 32767u) * 4u), "r"(1u << ((k >> 15) * 16)));
+          // no memory clobber: the table is read only after a block barrier, and additions commute
+        };
 #pragma unroll
-      for (int u = 0; u < kLeafVecPerThread; ++u) {
-        const uint32_t w[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
+        for (int u = 0; u < kLeafVecPerThread; ++u) {
+          const uint32_t w[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          add(w[e] & 0xFFFFu);
-          add(w[e] >> 16);
+          for (int e = 0; e < 4; ++e) {
+            add_hot(w[e] & 0xFFFFu);
+            add_hot(w[e] >> 16);
+          }
+        }
+        ch = __reduce_add_sync(0xffffffffu, ch);  // at most 32 x 24 keys of this round
+        if ((threadIdx.x & 31) == 0 && ch) atomicAdd(&hw[hot & 32767u], ch << ((hot >> 15) * 16));
+      } else {
+#pragma unroll
+        for (int u = 0; u < kLeafVecPerThread; ++u) {
+          const uint32_t w[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            add(w[e] & 0xFFFFu);
+            add(w[e] >> 16);
+          }
         }
       }
     } else {
