@@ -1030,9 +1030,10 @@ __global__ void __launch_bounds__(256) learn_fill_kernel(LearnedMap mp, const Le
 
 // On-chip sort of the buckets, one unit per CTA iteration, in place.  A unit
 // is a run of consecutive non-heavy buckets with at most 8192 keys in all
-// (contiguous in memory).  The unit's keys are split into at most 4096
-// sub-buckets by the top 12 bits of key - min in one counting pass through
-// shared memory; a key of a sub-bucket of at most 16 keys finds its place by
+// (contiguous in memory).  The unit's keys are split into at most 8192
+// sub-buckets by the top 13 bits of key - min in one counting pass through
+// shared memory (16-bit counters, two to a word: no count or offset exceeds
+// 8192); a key of a sub-bucket of at most 16 keys finds its place by
 // counting the smaller keys there, and the larger sub-buckets (in practice a
 // moderately frequent key among a few others) are split again by warps.  The
 // next unit's keys are prefetched into shared memory (cp.async) while one is
@@ -1041,11 +1042,12 @@ __global__ void __launch_bounds__(256) learn_fill_kernel(LearnedMap mp, const Le
 constexpr int kBsThreads = 1024;
 constexpr int kBsWarps = kBsThreads / 32;
 constexpr int kBsIpt = kLearnBucketCap / kBsThreads;  // keys per thread
-constexpr int kSubBits = 12;
+constexpr int kSubBits = 13;
 constexpr int kSub = 1 << kSubBits;
 constexpr int kSubPerThread = kSub / kBsThreads;
 constexpr int kGroup = 32;  // ids one unit-list thread packs
-static_assert(kSub % kBsThreads == 0, "sub-bucket ownership");
+static_assert(kSub % kBsThreads == 0 && kSubPerThread == 8, "sub-bucket ownership: four words per thread");
+static_assert(kSub <= 65535 && kLearnBucketCap <= 65535, "16-bit sub-bucket counters and offsets");
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
@@ -1059,7 +1061,7 @@ struct BsShared {
   uint2 big[2][kMaxBig];       // [lo, hi) ranges of more than kBigSub keys: this round's, the next
   uint32_t nbig[2];
   uint32_t bins[kBsWarps][32]; // per-warp bin counters of the split
-  uint32_t sub[kSub + 1];
+  __align__(16) uint32_t sub[kSub / 2 + 4];  // 16-bit counters, then offsets; entry kSub = the unit's size (uint4-aligned clears)
   uint64_t red[2 * kBsWarps];  // per-warp key min / max
   uint32_t warp_sum[kBsWarps]; // per-warp totals of the sub-bucket counts
   uint32_t flag;
@@ -1071,6 +1073,7 @@ struct BsShared {
 __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g, uint32_t cnt,
                           uint64_t* __restrict__ s_out, uint64_t* __restrict__ s_tmp, BsShared& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint16_t* sub16 = reinterpret_cast<const uint16_t*>(sh.sub);  // the offsets, after the scan
   uint32_t v[kBsIpt];  // sub-bucket << 16 | slot
   uint64_t kmn = ~0ull, kmx = 0;
 #pragma unroll
@@ -1120,16 +1123,23 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
     const uint32_t i = uint32_t(j * kBsThreads + tid);
     if (i < cnt) {
       const uint32_t sb = uint32_t((k[j] - kmn) >> shf);
-      v[j] = (sb << 16) | atomicAdd(&sh.sub[sb], 1u);
+      const uint32_t half = (sb & 1u) * 16u;
+      v[j] = (sb << 16) | ((atomicAdd(&sh.sub[sb >> 1], 1u << half) >> half) & 0xFFFFu);
     }
   }
   __syncthreads();
   uint32_t own[kSubPerThread], sum = 0;
+  {
+    const uint4 w = reinterpret_cast<const uint4*>(sh.sub)[tid];
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-  for (int q = 0; q < kSubPerThread; ++q) {
-    own[q] = sh.sub[tid * kSubPerThread + q];
-    sum += own[q];
+    for (int q = 0; q < 4; ++q) {
+      own[2 * q] = ws[q] & 0xFFFFu;
+      own[2 * q + 1] = ws[q] >> 16;
+    }
   }
+#pragma unroll
+  for (int q = 0; q < kSubPerThread; ++q) sum += own[q];
   uint32_t inc = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1150,22 +1160,26 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
     if (warp == 0) before = 0;
   }
   uint32_t run = inc - sum + before;
+  {
+    uint32_t ws[4];
 #pragma unroll
-  for (int q = 0; q < kSubPerThread; ++q) {
-    sh.sub[tid * kSubPerThread + q] = run;
-    run += own[q];
+    for (int q = 0; q < 4; ++q) {
+      ws[q] = run | ((run + own[2 * q]) << 16);
+      run += own[2 * q] + own[2 * q + 1];
+    }
+    reinterpret_cast<uint4*>(sh.sub)[tid] = make_uint4(ws[0], ws[1], ws[2], ws[3]);
   }
-  if (tid == kBsThreads - 1) sh.sub[kSub] = cnt;
+  if (tid == kBsThreads - 1) sh.sub[kSub / 2] = cnt;
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < kBsIpt; ++j) {
     const uint32_t i = uint32_t(j * kBsThreads + tid);
-    if (i < cnt) s_tmp[sh.sub[v[j] >> 16] + (v[j] & 0xFFFFu)] = k[j];
+    if (i < cnt) s_tmp[sub16[v[j] >> 16] + (v[j] & 0xFFFFu)] = k[j];
   }
 #pragma unroll
   for (int q = 0; q < kSubPerThread; ++q) {  // sub-buckets above kBigSub keys go to the warp split below
     const int sb = tid * kSubPerThread + q;
-    const uint32_t lo = sh.sub[sb], hi = sh.sub[sb + 1];
+    const uint32_t lo = sub16[sb], hi = sub16[sb + 1];
     if (hi - lo > kBigSub) {
       const uint32_t at = atomicAdd(&sh.nbig[0], 1u);
       if (at < kMaxBig) sh.big[0][at] = make_uint2(lo, hi); else sh.flag = 1;
@@ -1179,7 +1193,7 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
   for (uint32_t p = uint32_t(tid); p < cnt; p += kBsThreads) {
     const uint64_t key = s_tmp[p];
     const uint32_t sb = uint32_t((key - kmn) >> shf);
-    const uint32_t lo = sh.sub[sb], hi = sh.sub[sb + 1];
+    const uint32_t lo = sub16[sb], hi = sub16[sb + 1];
     if (hi - lo > kBigSub) {
       s_out[p] = key;
       continue;
@@ -1281,7 +1295,7 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
     }
   }
   for (uint32_t i = tid; i < cnt; i += kBsThreads) g[i] = s_out[i];
-  for (int i = tid; i <= kSub; i += kBsThreads) sh.sub[i] = 0;
+  for (int i = tid; i < kSub / 2 + 4; i += kBsThreads) sh.sub[i] = 0;
 }
 
 // The unit list (units + 1; units[0].x counts them; order arbitrary): each
@@ -1324,7 +1338,7 @@ __global__ void __launch_bounds__(kBsThreads, 1) learn_bucket_sort_kernel(uint64
   const int tid = threadIdx.x;
   const uint32_t nunits = units[0].x;
   const uint2* list = units + 1;
-  for (int i = tid; i <= kSub; i += kBsThreads) sh.sub[i] = 0;
+  for (int i = tid; i < kSub / 2 + 4; i += kBsThreads) sh.sub[i] = 0;
   auto prefetch = [&](uint2 x, int buf) {
     uint64_t* dst = s_dyn + (1 + buf) * kLearnBucketCap;
     for (uint32_t i = tid; i < x.y; i += kBsThreads) cp_async8(&dst[i], &keys[x.x + i]);
