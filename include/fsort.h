@@ -176,7 +176,9 @@ typedef struct fsort_batch_config {
   int32_t small_ctas_per_sm; /* CTAs per SM of the persistent small-segment kernel (1..8) */
   int32_t large_form;        /* scatter passes of the larger segments: 1 = from a table of per-tile offsets
                                 (one count read per pass), 0 = chained (decoupled look-back) */
-  int32_t reserved;
+  int32_t digit_bits;        /* digit width of every pass of the batch (both groups): 0 or 8 (the default;
+                                ceil(p / 8) passes), 7 or 6 (ceil(p / 7), ceil(p / 6) passes with fewer
+                                distinct digits each; 16- and 32-bit keys only).  The output is the same. */
 } fsort_batch_config;
 
 /* Sort count segments (host array of descriptors; the keys and values are on
@@ -188,16 +190,18 @@ FSORT_API fsort_status fsort_sort_batch(fsort_plan* plan, const fsort_segment* s
                                         int precision_bits, void* stream);
 
 /* Set / read the batched path's configuration (defaults: 4096 keys, the most
- * CTAs per SM that shared memory allows, the table form). */
+ * CTAs per SM that shared memory allows, the table form, 8-bit digits). */
 FSORT_API fsort_status fsort_batch_set_config(fsort_plan* plan, const fsort_batch_config* config);
 FSORT_API fsort_status fsort_batch_get_config(const fsort_plan* plan, fsort_batch_config* config);
 
 /* Autotuner: time fsort_sort_batch on these segments under candidate
  * configurations -- the larger segments' form (table or chained) under the
- * current small-segment configuration, then every small-segment capacity x
- * CTAs per SM under the faster form -- keep the fastest in the plan and return
- * it (and its time in ms, if best_ms is not NULL).  The segments are sorted in
- * place several times; the result is the sorted batch.  Synchronous. */
+ * current small-segment configuration, then every small-segment capacity (the
+ * on-chip tile) x CTAs per SM under the faster form, then the digit widths 8,
+ * 7 and 6 (16- and 32-bit keys) under the best of those -- keep the fastest in
+ * the plan and return it (and its time in ms, if best_ms is not NULL).  The
+ * segments are sorted in place several times; the result is the sorted batch.
+ * Synchronous. */
 FSORT_API fsort_status fsort_batch_autotune(fsort_plan* plan, const fsort_segment* segments, uint32_t count,
                                             int key_bits, int precision_bits, void* stream,
                                             fsort_batch_config* best, float* best_ms);

@@ -41,11 +41,11 @@ class FsortSegment(ctypes.Structure):
 
 class FsortBatchConfig(ctypes.Structure):
     _fields_ = [("small_capacity", ctypes.c_int32), ("small_ctas_per_sm", ctypes.c_int32),
-                ("large_form", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("large_form", ctypes.c_int32), ("digit_bits", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"small_capacity": self.small_capacity, "small_ctas_per_sm": self.small_ctas_per_sm,
-                "large_form": self.large_form}
+                "large_form": self.large_form, "digit_bits": self.digit_bits or 8}
 
 
 class FsortPlanInfo(ctypes.Structure):
@@ -392,9 +392,12 @@ def fsort_sort_batch(plan, segments, key_bits: int, precision_bits=None, stream=
            "fsort_sort_batch")
 
 
-def fsort_batch_set_config(plan, small_capacity: int, small_ctas_per_sm: int, large_form: int = 1) -> None:
-    """large_form: 1 = the larger segments' passes scatter from a table of per-tile offsets, 0 = chained."""
-    cfg = FsortBatchConfig(small_capacity=small_capacity, small_ctas_per_sm=small_ctas_per_sm, large_form=large_form)
+def fsort_batch_set_config(plan, small_capacity: int, small_ctas_per_sm: int, large_form: int = 1,
+                           digit_bits: int = 8) -> None:
+    """large_form: 1 = the larger segments' passes scatter from a table of per-tile offsets, 0 = chained;
+    digit_bits: width of the batch's radix digits (8, or 7 / 6 for 16- and 32-bit keys)."""
+    cfg = FsortBatchConfig(small_capacity=small_capacity, small_ctas_per_sm=small_ctas_per_sm, large_form=large_form,
+                           digit_bits=digit_bits)
     _check(load_library().fsort_batch_set_config(plan, ctypes.byref(cfg)), "fsort_batch_set_config")
 
 

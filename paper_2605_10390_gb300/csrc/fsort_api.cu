@@ -571,8 +571,15 @@ fsort_status build_batch(fsort_plan* p, const fsort_segment* segs, uint32_t coun
   return FSORT_OK;
 }
 
+// Digit width of the batched path's passes (fsort_batch_config::digit_bits, 0 = 8).
+int batch_digits(const fsort_plan* p) { return p->bcfg.digit_bits ? p->bcfg.digit_bits : 8; }
+
+// Most passes a batch of this key width can take: at 6-bit digits for 16- and
+// 32-bit keys, at 8-bit digits for 64-bit keys.
+int batch_max_passes(int key_bits) { return key_bits == 64 ? 8 : (key_bits + 5) / 6; }
+
 cudaError_t enqueue_batch(fsort_plan* p, const BatchShape& b, int key_bits, int precision_bits, cudaStream_t s) {
-  const DigitPlan plan = make_plan(key_bits, precision_bits, p->digit_bits);
+  const DigitPlan plan = make_plan(key_bits, precision_bits, batch_digits(p));
   cudaError_t e = cudaSuccess;
   if (b.n_large) e = cudaMemcpyAsync(p->d_seg_large, p->h_seg_large, sizeof(SegDesc) * b.n_large,
                                      cudaMemcpyHostToDevice, s);
@@ -688,7 +695,8 @@ fsort_status run_batch(fsort_plan* p, const fsort_segment* segs, uint32_t count,
   const uint64_t key[10] = {b.n_large, b.n_small, uint64_t(b.n_chunks) << 32 | b.n_tchunks, b.total_tiles, b.alt_total,
                             uint64_t(b.has_vals) | uint64_t(p->bcfg.large_form) << 1,
                             uint64_t(key_bits) << 8 | uint64_t(precision_bits), uint64_t(p->bcfg.small_capacity),
-                            uint64_t(p->bcfg.small_ctas_per_sm), reinterpret_cast<uint64_t>(s)};
+                            uint64_t(p->bcfg.small_ctas_per_sm) | uint64_t(batch_digits(p)) << 32,
+                            reinterpret_cast<uint64_t>(s)};
   if (!p->gexec || std::memcmp(key, p->gkey, sizeof(key)) != 0) {
     if (p->gexec) {
       cudaGraphExecDestroy(p->gexec);
@@ -742,6 +750,9 @@ fsort_status fsort_batch_set_config(fsort_plan* plan, const fsort_batch_config* 
   if (c && config->small_ctas_per_sm > small_sort_ctas_per_sm(plan->desc.key_bits, plan->desc.has_values != 0, c))
     return FSORT_ERR_INVALID_ARG;  // more CTAs than shared memory holds at once
   if (config->large_form != 0 && config->large_form != 1) return FSORT_ERR_INVALID_ARG;
+  const int w = config->digit_bits;
+  if (w != 0 && w != 6 && w != 7 && w != 8) return FSORT_ERR_INVALID_ARG;
+  if (plan->desc.key_bits == 64 && w != 0 && w != 8) return FSORT_ERR_INVALID_ARG;  // more passes than the buffers hold
   plan->bcfg = *config;
   return FSORT_OK;
 }
@@ -793,7 +804,7 @@ fsort_status fsort_batch_autotune(fsort_plan* plan, const fsort_segment* segment
     if (st != FSORT_OK) break;
     consider(ms);
   }
-  const int form = winner.large_form;
+  const int form = winner.large_form, width = saved.digit_bits;
   for (int cap : {0, 1024, 2048, 4096}) {
     if (st != FSORT_OK) break;
     const int most = cap ? small_sort_ctas_per_sm(key_bits, hv, cap) : 1;
@@ -802,11 +813,24 @@ fsort_status fsort_batch_autotune(fsort_plan* plan, const fsort_segment* segment
       plan->bcfg.small_capacity = cap;
       plan->bcfg.small_ctas_per_sm = ctas;
       plan->bcfg.large_form = form;
+      plan->bcfg.digit_bits = width;
       float ms = 0.f;
       st = time_config(&ms);
       if (st != FSORT_OK) break;
       consider(ms);
     }
+  }
+  // then the digit width under the best of those (the current width is measured already)
+  const fsort_batch_config best_so_far = winner;
+  for (int w : {8, 7, 6}) {
+    if (st != FSORT_OK || key_bits == 64) break;
+    if (w == (width ? width : 8)) continue;
+    plan->bcfg = best_so_far;
+    plan->bcfg.digit_bits = w;
+    float ms = 0.f;
+    st = time_config(&ms);
+    if (st != FSORT_OK) break;
+    consider(ms);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -883,7 +907,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     delete p;
     return FSORT_ERR_INVALID_ARG;
   }
-  const int pmax = desc->key_bits / 8;
+  const int pmax = batch_max_passes(desc->key_bits);
   size_t o_bsl = 0, o_bss = 0, o_bch = 0, o_bts = 0, o_bh = 0, o_bb = 0, o_bctr = 0;
   size_t o_btr = 0, o_btcs = 0, o_btco = 0, o_btseg = 0;
   if (batch) {
@@ -1082,6 +1106,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     p->bcfg.small_capacity = 4096;
     p->bcfg.small_ctas_per_sm = small_sort_ctas_per_sm(desc->key_bits, desc->has_values != 0, 4096);
     p->bcfg.large_form = 1;
+    p->bcfg.digit_bits = 8;
   }
   *out_plan = p;
   return FSORT_OK;

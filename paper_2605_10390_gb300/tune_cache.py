@@ -1,8 +1,8 @@
 """Persistent cache of the batched path's autotuned configuration.
 
-``fsort_batch_autotune`` times every candidate configuration of the batched
-sort (on-chip segment capacity x CTAs per SM) on the caller's batch and keeps
-the fastest in the plan.  Batch stream sorting is tuned per batch size
+``fsort_batch_autotune`` times the candidate configurations of the batched
+sort (the larger segments' form, on-chip segment capacity x CTAs per SM, digit
+width) on the caller's batch and keeps the fastest in the plan.  Batch stream sorting is tuned per batch size
 (Sec. III-C and IV-D); the choice depends on the device and on the
 batch's shape, not on its data, so this module stores it in a JSON file keyed
 by both.  A later process with a batch of the same shape class sets the stored
@@ -14,7 +14,8 @@ of the batched path (segments sorted whole on chip at capacities 1,024 /
 power of two, plus the total keys rounded up to a power of two.  Batches in
 one class run the same kernels on about the same amount of work.
 
-The file holds ``{"version": 1, "entries": {"<device>|<class>": {...}}}``.
+The file holds ``{"version": 3, "entries": {"<device>|<class>": {...}}}``
+(files of another version are ignored).
 It is replaced atomically (write to a temporary file, then rename), so a
 reader sees either the old or the new file.  Entries that do not name a valid
 configuration are ignored, as is an unreadable file.
@@ -27,7 +28,7 @@ import tempfile
 
 from ._binding import _numel, fsort_batch_autotune, fsort_batch_set_config
 
-VERSION = 2
+VERSION = 3  # entries carry the digit width
 CAPACITIES = (0, 1024, 2048, 4096)  # 0: no on-chip path
 MAX_CTAS_PER_SM = 8
 SIZE_CLASSES = (1024, 2048, 4096)   # upper bounds of the on-chip classes; larger segments form the last class
@@ -69,16 +70,18 @@ def current_device_key() -> str:
     return device_key(props.name, props.multi_processor_count, props.major, props.minor)
 
 
-CONFIG_KEYS = ("small_capacity", "small_ctas_per_sm", "large_form")
+CONFIG_KEYS = ("small_capacity", "small_ctas_per_sm", "large_form", "digit_bits")
+DIGIT_BITS = (6, 7, 8)
 
 
 def valid_config(cfg) -> bool:
     if not isinstance(cfg, dict):
         return False
     cap, ctas, form = cfg.get("small_capacity"), cfg.get("small_ctas_per_sm"), cfg.get("large_form")
-    if any(not isinstance(v, int) or isinstance(v, bool) for v in (cap, ctas, form)):
+    width = cfg.get("digit_bits")
+    if any(not isinstance(v, int) or isinstance(v, bool) for v in (cap, ctas, form, width)):
         return False
-    return cap in CAPACITIES and 1 <= ctas <= MAX_CTAS_PER_SM and form in (0, 1)
+    return cap in CAPACITIES and 1 <= ctas <= MAX_CTAS_PER_SM and form in (0, 1) and width in DIGIT_BITS
 
 
 class TuneCache:
@@ -145,7 +148,8 @@ def autotune_cached(plan, segments, key_bits: int, precision_bits=None, *, has_v
     cache = TuneCache(path)
     cfg = cache.get(dev, cls)
     if cfg is not None:
-        fsort_batch_set_config(plan, cfg["small_capacity"], cfg["small_ctas_per_sm"], cfg["large_form"])
+        fsort_batch_set_config(plan, cfg["small_capacity"], cfg["small_ctas_per_sm"], cfg["large_form"],
+                               cfg["digit_bits"])
         return cfg, cache.entries[f"{dev}|{cls}"].get("ms"), True
     cfg, ms = fsort_batch_autotune(plan, segments, key_bits, precision_bits, stream)
     cache.put(dev, cls, cfg, ms)

@@ -2,8 +2,8 @@
 
 Segments of every size class: empty, on-chip (<= the small-segment capacity),
 one tile, many tiles with a ragged tail; mixed distributions; every key width;
-with and without values; graph replay with new data of the same shape; the
-autotuner.  Integer data: bit-exact.
+with and without values; 6-, 7- and 8-bit digits; graph replay with new data
+of the same shape; the autotuner.  Integer data: bit-exact.
 """
 import numpy as np
 import pytest
@@ -81,6 +81,51 @@ def test_batch_every_small_capacity(cap, form):
         check_batch(kb, p, host, dev)
 
 
+@pytest.mark.parametrize("kb,p", [(16, 16), (16, 11), (32, 32), (32, 17)])
+@pytest.mark.parametrize("width", [6, 7])
+@pytest.mark.parametrize("form", list(FORMS))
+def test_batch_narrower_digits_match_oracle(kb, p, width, form):
+    """Digit widths 6 and 7 (more passes, fewer distinct digits each) give the same output."""
+    host, dev = make_batch(kb, SIZES, True, seed=kb * p + width)
+    with fs.Plan(sum(SIZES) + 8 * len(SIZES), kb, has_values=True, max_segments=64) as plan:
+        cfg = fs.fsort_batch_get_config(plan.handle)
+        fs.fsort_batch_set_config(plan.handle, cfg["small_capacity"], cfg["small_ctas_per_sm"], FORMS[form], width)
+        assert fs.fsort_batch_get_config(plan.handle)["digit_bits"] == width
+        plan.sort_batch(dev, precision_bits=p)
+        plan.sync()
+        check_batch(kb, p, host, dev)
+
+
+def test_batch_digit_width_is_checked():
+    with fs.Plan(1 << 16, 32, has_values=True, max_segments=4) as plan:
+        for bad in (5, 9, 16):
+            with pytest.raises(fs.FsortError):
+                fs.fsort_batch_set_config(plan.handle, 4096, 1, 1, bad)
+    with fs.Plan(1 << 16, 64, has_values=False, max_segments=4) as plan:
+        for bad in (6, 7):  # 64-bit keys would need more passes than the batch buffers hold
+            with pytest.raises(fs.FsortError):
+                fs.fsort_batch_set_config(plan.handle, 1024, 1, 1, bad)
+        fs.fsort_batch_set_config(plan.handle, 1024, 1, 1, 8)
+
+
+def test_batch_graph_is_recaptured_for_another_digit_width():
+    kb, p = 32, 32
+    sizes = [5000, 70000, 300, 4096, 12]
+    stream = torch.cuda.Stream()
+    with fs.Plan(sum(sizes) + 64, kb, has_values=True, flags=fs.FSORT_FLAG_GRAPH, max_segments=16) as plan:
+        for rep, width in enumerate([8, 6, 7, 8]):  # same shape, another pass count each time
+            cfg = fs.fsort_batch_get_config(plan.handle)
+            fs.fsort_batch_set_config(plan.handle, cfg["small_capacity"], cfg["small_ctas_per_sm"],
+                                      cfg["large_form"], width)
+            host, dev = make_batch(kb, sizes, True, seed=200 + rep)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                plan.sort_batch(dev, precision_bits=p, stream=stream)
+            plan.sync()
+            stream.synchronize()
+            check_batch(kb, p, host, dev)
+
+
 def test_batch_graph_replay_with_new_data():
     kb, p = 32, 32
     sizes = [5000, 70000, 300, 4096, 123457, 12]
@@ -103,6 +148,7 @@ def test_batch_autotune_sorts_and_picks_a_config():
     with fs.Plan(sum(sizes) + 64, kb, has_values=True, max_segments=16) as plan:
         cfg, ms = fs.fsort_batch_autotune(plan.handle, dev, kb, p)
         assert cfg["small_capacity"] in (0, 1024, 2048, 4096) and cfg["large_form"] in (0, 1) and ms > 0
+        assert cfg["digit_bits"] in (6, 7, 8)
         assert fs.fsort_batch_get_config(plan.handle) == cfg
         check_batch(kb, p, host, dev)
 

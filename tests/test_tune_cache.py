@@ -38,11 +38,11 @@ def test_round_trip_and_atomic_file(tmp_path):
     path = str(tmp_path / "sub" / "tune.json")
     c = tc.TuneCache(path)
     assert c.get(DEV, "k32") is None
-    c.put(DEV, "k32", {"small_capacity": 2048, "small_ctas_per_sm": 3, "large_form": 1}, 1.25)
-    c.put(DEV, "k16", {"small_capacity": 0, "small_ctas_per_sm": 1, "large_form": 0})
+    c.put(DEV, "k32", {"small_capacity": 2048, "small_ctas_per_sm": 3, "large_form": 1, "digit_bits": 8}, 1.25)
+    c.put(DEV, "k16", {"small_capacity": 0, "small_ctas_per_sm": 1, "large_form": 0, "digit_bits": 8})
     again = tc.TuneCache(path)
-    assert again.get(DEV, "k32") == {"small_capacity": 2048, "small_ctas_per_sm": 3, "large_form": 1}
-    assert again.get(DEV, "k16") == {"small_capacity": 0, "small_ctas_per_sm": 1, "large_form": 0}
+    assert again.get(DEV, "k32") == {"small_capacity": 2048, "small_ctas_per_sm": 3, "large_form": 1, "digit_bits": 8}
+    assert again.get(DEV, "k16") == {"small_capacity": 0, "small_ctas_per_sm": 1, "large_form": 0, "digit_bits": 8}
     assert again.get("other-device", "k32") is None
     assert os.listdir(tmp_path / "sub") == ["tune.json"]  # no temporary file left behind
     d = json.load(open(path))
@@ -50,11 +50,14 @@ def test_round_trip_and_atomic_file(tmp_path):
 
 
 @pytest.mark.parametrize("bad", [
-    {"small_capacity": 3000, "small_ctas_per_sm": 1, "large_form": 1},
-    {"small_capacity": 1024, "small_ctas_per_sm": 0, "large_form": 1},
-    {"small_capacity": 1024, "small_ctas_per_sm": 9, "large_form": 1},
-    {"small_capacity": True, "small_ctas_per_sm": 1, "large_form": 1},
-    {"small_capacity": 1024, "small_ctas_per_sm": 1, "large_form": 2},
+    {"small_capacity": 3000, "small_ctas_per_sm": 1, "large_form": 1, "digit_bits": 8},
+    {"small_capacity": 1024, "small_ctas_per_sm": 0, "large_form": 1, "digit_bits": 8},
+    {"small_capacity": 1024, "small_ctas_per_sm": 9, "large_form": 1, "digit_bits": 8},
+    {"small_capacity": True, "small_ctas_per_sm": 1, "large_form": 1, "digit_bits": 8},
+    {"small_capacity": 1024, "small_ctas_per_sm": 1, "large_form": 2, "digit_bits": 8},
+    {"small_capacity": 1024, "small_ctas_per_sm": 1, "large_form": 1},
+    {"small_capacity": 1024, "small_ctas_per_sm": 1, "large_form": 1, "digit_bits": 5},
+    {"small_capacity": 1024, "small_ctas_per_sm": 1, "large_form": 1, "digit_bits": 9},
     {"small_capacity": 1024, "small_ctas_per_sm": 1},
     {"small_capacity": 1024},
     [1024, 2],
@@ -62,7 +65,7 @@ def test_round_trip_and_atomic_file(tmp_path):
 def test_invalid_entries_are_ignored_and_refused(tmp_path, bad):
     path = tmp_path / "tune.json"
     path.write_text(json.dumps({"version": tc.VERSION, "entries": {
-        f"{DEV}|bad": bad, f"{DEV}|good": {"small_capacity": 4096, "small_ctas_per_sm": 2, "large_form": 1}}}))
+        f"{DEV}|bad": bad, f"{DEV}|good": {"small_capacity": 4096, "small_ctas_per_sm": 2, "large_form": 1, "digit_bits": 8}}}))
     c = tc.TuneCache(str(path))
     assert c.get(DEV, "bad") is None and c.get(DEV, "good") is not None
     if isinstance(bad, dict):
@@ -76,8 +79,8 @@ def test_unreadable_file_is_an_empty_cache(tmp_path, text):
     path.write_text(text)
     c = tc.TuneCache(str(path))
     assert c.entries == {}
-    c.put(DEV, "x", {"small_capacity": 1024, "small_ctas_per_sm": 4, "large_form": 1})  # and is replaced on the next store
-    assert tc.TuneCache(str(path)).get(DEV, "x") == {"small_capacity": 1024, "small_ctas_per_sm": 4, "large_form": 1}
+    c.put(DEV, "x", {"small_capacity": 1024, "small_ctas_per_sm": 4, "large_form": 1, "digit_bits": 8})  # and is replaced on the next store
+    assert tc.TuneCache(str(path)).get(DEV, "x") == {"small_capacity": 1024, "small_ctas_per_sm": 4, "large_form": 1, "digit_bits": 8}
 
 
 def test_miss_tunes_and_stores_then_hit_only_sets(tmp_path, monkeypatch):
@@ -85,23 +88,23 @@ def test_miss_tunes_and_stores_then_hit_only_sets(tmp_path, monkeypatch):
 
     def fake_tune(plan, segments, key_bits, precision_bits, stream):
         calls.append(("tune", plan, len(segments), key_bits, precision_bits))
-        return {"small_capacity": 2048, "small_ctas_per_sm": 5, "large_form": 0}, 3.5
+        return {"small_capacity": 2048, "small_ctas_per_sm": 5, "large_form": 0, "digit_bits": 7}, 3.5
 
-    def fake_set(plan, cap, ctas, form):
-        calls.append(("set", plan, cap, ctas, form))
+    def fake_set(plan, cap, ctas, form, width):
+        calls.append(("set", plan, cap, ctas, form, width))
 
     monkeypatch.setattr(tc, "fsort_batch_autotune", fake_tune)
     monkeypatch.setattr(tc, "fsort_batch_set_config", fake_set)
     path = str(tmp_path / "tune.json")
     segs = [(0x1000, 0x2000, 3000), (0x3000, 0x4000, 70000)]
     cfg, ms, hit = tc.autotune_cached("plan-a", segs, 32, 32, has_values=True, path=path, device=DEV)
-    assert (cfg, ms, hit) == ({"small_capacity": 2048, "small_ctas_per_sm": 5, "large_form": 0}, 3.5, False)
+    assert (cfg, ms, hit) == ({"small_capacity": 2048, "small_ctas_per_sm": 5, "large_form": 0, "digit_bits": 7}, 3.5, False)
     assert calls == [("tune", "plan-a", 2, 32, 32)]
     # same shape class (another 3000-key and 70000-key segment pair): a hit, no timing
     segs2 = [(0x5000, 0x6000, 2500), (0x7000, 0x8000, 65000)]
     cfg, ms, hit = tc.autotune_cached("plan-b", segs2, 32, 32, has_values=True, path=path, device=DEV)
-    assert (cfg, ms, hit) == ({"small_capacity": 2048, "small_ctas_per_sm": 5, "large_form": 0}, 3.5, True)
-    assert calls[1:] == [("set", "plan-b", 2048, 5, 0)]
+    assert (cfg, ms, hit) == ({"small_capacity": 2048, "small_ctas_per_sm": 5, "large_form": 0, "digit_bits": 7}, 3.5, True)
+    assert calls[1:] == [("set", "plan-b", 2048, 5, 0, 7)]
     # another device or another class misses
     tc.autotune_cached("plan-c", segs2, 32, 32, has_values=True, path=path, device="GPU-Y/sm103/152sms")
     tc.autotune_cached("plan-d", segs2 * 3, 32, 32, has_values=True, path=path, device=DEV)
