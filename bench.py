@@ -372,9 +372,25 @@ def run_batched(fs, workloads, torch, stream, peak, reps: int = 2):
             e1.record(side)
         side.synchronize()
         times.append(e0.elapsed_time(e1))
+    bms = float(np.median(times[1:]))
+    # the same batch at each digit width (the tuner's third coordinate), one warm-up and one timed run each
+    width_ms = {}
+    for width in (8, 7, 6):
+        if isinstance(cfg, dict) and width == cfg.get("digit_bits"):
+            width_ms[width] = bms
+            continue
+        fs.fsort_batch_set_config(bplan.handle, cfg["small_capacity"], cfg["small_ctas_per_sm"], cfg["large_form"],
+                                  width)
+        for rep in range(2):
+            regenerate()
+            with torch.cuda.stream(side):
+                e0.record(side)
+                bplan.sort_batch(segs, precision_bits=32, stream=side)
+                e1.record(side)
+            side.synchronize()
+        width_ms[width] = e0.elapsed_time(e1)
     bplan.sync()
     bplan.close()
-    bms = float(np.median(times[1:]))
     # plain: one sort per segment
     pplan = fs.Plan(max(sizes), 32, has_values=True)
     times = []
@@ -396,6 +412,7 @@ def run_batched(fs, workloads, torch, stream, peak, reps: int = 2):
     balg = sum(16 * n if n <= cap else 68 * n for n in sizes)
     out.update({"batched_ms": bms, "batched_gkeys_per_s": total / bms / 1e6, "plain_ms": pms,
                 "plain_gkeys_per_s": total / pms / 1e6, "speedup": pms / bms, "autotuned": cfg,
+                "ms_by_digit_bits": width_ms,
                 "plain_path_algorithmic_bytes": alg, "plain_path_frac": alg / pms / 1e6 / peak,
                 "batched_algorithmic_bytes": balg, "batched_frac": balg / bms / 1e6 / peak})
     del keys, vals
