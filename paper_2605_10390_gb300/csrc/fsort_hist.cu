@@ -21,9 +21,10 @@ constexpr int kRadix = 256;
 // ---------------------------------------------------------------- K1 -------
 // Every CTA owns a slice of the keys and keeps one shared-memory counter per
 // (pass, digit).  Counts are added with shared-memory reductions
-// (red.shared.add: same-address adds from a warp are combined by the
-// hardware, so skewed inputs cost no more than uniform ones), then merged into
-// the global 64-bit histogram with one atomic per non-zero counter.
+// (red.shared.add: the lanes of a warp that add to one counter are served
+// together when no other counter of that bank is hit in the same instruction,
+// so a digit shared by the whole warp costs one pass), then merged into the
+// global 64-bit histogram with one atomic per non-zero counter.
 constexpr int kHistThreads = 512;
 
 // P = number of passes (compile time, so the per-key loop is exactly P
