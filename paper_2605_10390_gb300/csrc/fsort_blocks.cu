@@ -386,6 +386,12 @@ struct TileSmem {
   static constexpr size_t kBytes = kBar + 16;
 };
 
+// Compile-time flag for code paths that differ only for a short last tile.
+template <bool B>
+struct FullTile {
+  static constexpr bool value = B;
+};
+
 // kIpt keys of one thread in registers; 16-bit keys two to a word.
 template <typename K, int kIpt>
 struct KeyRegs {
@@ -504,14 +510,20 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   uint32_t* wcnt = s_wcnt + warp * kRadix;
   const int wbase = warp * 32 * kIpt;
   KeyRegs<K, kIpt> kr;
+  // steps 2 and 4 are compiled twice: for whole tiles (every position valid) and the short last one
+  auto count_step = [&](auto full) {
+    constexpr bool kFull = decltype(full)::value;
 #pragma unroll
-  for (int i = 0; i < kIpt; ++i) {
-    const int pos = wbase + i * 32 + lane;
-    const bool valid = uint32_t(pos) < tile_n;
-    const K k = valid ? s_keys[pos] : K(0);
-    kr.set(i, k);
-    if (valid) atomicAdd(&wcnt[dig(k, shift, mask)], 1u);
-  }
+    for (int i = 0; i < kIpt; ++i) {
+      const int pos = wbase + i * 32 + lane;
+      const bool valid = kFull || uint32_t(pos) < tile_n;
+      const K k = valid ? s_keys[pos] : K(0);
+      kr.set(i, k);
+      if (valid) atomicAdd(&wcnt[dig(k, shift, mask)], 1u);
+    }
+  };
+  if (tile_n == uint32_t(kTile)) count_step(FullTile<true>{});
+  else count_step(FullTile<false>{});
   __syncthreads();
 
   // 3. per digit: each warp's first position of the digit in the tile's
@@ -551,11 +563,12 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   // key | source slot << 16 over the keys and source areas, wider keys in
   // place plus a 16-bit source slot; values stay where they are and are
   // gathered once, in the write-out.
-  {
+  auto rank_step = [&](auto full) {
+    constexpr bool kFull = decltype(full)::value;
     const uint32_t lt = lanemask_lt();
     bool skewed;
     {
-      const uint32_t d0 = uint32_t(wbase + lane) < tile_n ? dig(kr.get(0), shift, mask) : 0xFFFFFFFFu;
+      const uint32_t d0 = (kFull || uint32_t(wbase + lane) < tile_n) ? dig(kr.get(0), shift, mask) : 0xFFFFFFFFu;
       skewed = __popc(__ballot_sync(0xffffffffu, d0 == __shfl_sync(0xffffffffu, d0, 0))) >= 16;
     }
     uint8_t* win = reinterpret_cast<uint8_t*>(smem + L::kWin) + warp * kRadix;
@@ -565,7 +578,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
 #pragma unroll
     for (int i = 0; i < kIpt; ++i) {
       const int pos = wbase + i * 32 + lane;
-      const bool valid = uint32_t(pos) < tile_n;
+      const bool valid = kFull || uint32_t(pos) < tile_n;
       const K k = kr.get(i);
       const uint32_t d = dig(k, shift, mask);
       uint32_t w;
@@ -583,14 +596,15 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
         }
       }
     }
-  }
+  };
+  if (tile_n == uint32_t(kTile)) rank_step(FullTile<true>{});
+  else rank_step(FullTile<false>{});
   __syncthreads();
 
   // 5. write-out in digit runs, consecutive threads to consecutive addresses
   const uint32_t* s_rec32 = reinterpret_cast<const uint32_t*>(smem + L::kKeys);
   const uint16_t* s_src = reinterpret_cast<const uint16_t*>(smem + L::kSrc);
-#pragma unroll 4
-  for (uint32_t s = tid; s < tile_n; s += kBlock) {
+  auto write_slot = [&](uint32_t s) {
     K k;
     uint32_t from = 0;
     if (sizeof(K) == 2) {
@@ -604,6 +618,13 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
     const uint32_t o = s_off[dig(k, shift, mask)] + s;
     kout[o] = k;
     if (kVals) vout[o] = s_vals[from];
+  };
+  if (tile_n == uint32_t(kTile)) {
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) write_slot(uint32_t(tid + j * kBlock));
+  } else {
+#pragma unroll 4
+    for (uint32_t s = tid; s < tile_n; s += kBlock) write_slot(s);
   }
 }
 
