@@ -41,6 +41,7 @@ sys.path.insert(0, ROOT)
 
 DISTS = ["uniform", "zipf1.1", "gauss", "presorted", "equal"]
 LOG2N = 28
+NOMINAL_HBM_GBS = 8000.0  # nominal HBM3e bandwidth of the part, for the second roofline fraction
 KEY_BITS = 16
 PRECISION = 16
 WORKLOAD = ("512 MB: 2^28 uint16 keys + uint32 index values, stable, 16-bit precision, out of place; "
@@ -840,8 +841,14 @@ def main():
             c["bytes"] += 2 * (kb + vb) * n
     job_bytes = sum(c["bytes"] for c in calls.values()) / max(1, args.steps)
     per_dist = {}
+    passes_run = {}  # executed scatter passes per sort of each distribution (trivial passes are skipped)
     for idx, c in calls.items():
         per_dist.setdefault(DISTS[idx % len(DISTS)], []).append(c["ms"])
+    for r in recs:
+        if r["kind"] == "scatter" and r["active"]:
+            d = DISTS[r["call"] % len(DISTS)]
+            passes_run[d] = passes_run.get(d, 0) + 1
+    passes_run = {d: passes_run.get(d, 0) / max(1, len(per_dist.get(d, []))) for d in DISTS}
     per_dist_gkeys = {d: n / (statistics.mean(v) / 1e3) / 1e9 for d, v in per_dist.items()}
 
     result = None
@@ -859,7 +866,11 @@ def main():
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "algorithmic_bytes_per_launch": per_launch, "launches": len(sc),
                          "avg_launch_ms": sc_ms / len(sc) if sc else None, "peak_source": peak_src,
-                         "traffic_note": traffic_note},
+                         "traffic_note": traffic_note,
+                         # Eq. 1's b_eff: algorithmic bytes over the DRAM bytes ncu measured for the launch
+                         "b_eff": (per_launch / traffic) if traffic else None,
+                         "frac_of_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
+                         "nominal_gbs": NOMINAL_HBM_GBS, "passes_run": passes_run},
             "job_hbm": {"algorithmic_bytes_per_step": job_bytes,
                         "achieved_gbs": job_bytes / (ms_per_step / 1e3) / 1e9,
                         "frac": job_bytes / (ms_per_step / 1e3) / 1e9 / peak},

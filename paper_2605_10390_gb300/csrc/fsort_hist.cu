@@ -184,29 +184,43 @@ __global__ void __launch_bounds__(kScanThreads) scan_rows_kernel(const uint64_t*
   }
 }
 
+// dst[i] = src[i] for i < nv (16-byte vectors, distinct buffers), grid-stride,
+// four loads in flight per thread before their stores, with streaming hints
+// (neither side is read again soon).
+__device__ __forceinline__ void copy_vectors(uint4* __restrict__ dst, const uint4* __restrict__ src, uint64_t nv,
+                                             uint64_t tid, uint64_t stride) {
+  constexpr int kInFlight = 4;
+  uint64_t i = tid;
+  for (; i + (kInFlight - 1) * stride < nv; i += kInFlight * stride) {
+    uint4 r[kInFlight];
+#pragma unroll
+    for (int u = 0; u < kInFlight; ++u) r[u] = __ldcs(&src[i + u * stride]);
+#pragma unroll
+    for (int u = 0; u < kInFlight; ++u) __stcs(&dst[i + u * stride], r[u]);
+  }
+  for (; i < nv; i += stride) __stcs(&dst[i], __ldcs(&src[i]));
+}
+
 // Final copy of keys (and values) between buffers when the schedule asks.
 template <typename K>
-__global__ void schedule_copy_kernel(const K* k0, const K* k1, const K* k2, const uint32_t* v0, const uint32_t* v1,
+__global__ void __launch_bounds__(256, 4) schedule_copy_kernel(const K* k0, const K* k1, const K* k2, const uint32_t* v0, const uint32_t* v1,
                                      const uint32_t* v2, uint64_t n, const Schedule* sched) {
   const PassDesc cp = sched->copy;
   if (!cp.active) return;
-  const K* ks[3] = {k0, k1, k2};
-  const uint32_t* vs[3] = {v0, v1, v2};
-  const K* src = ks[cp.src];
-  K* dst = const_cast<K*>(ks[cp.dst]);
-  const uint32_t* vsrc = vs[cp.src];
-  uint32_t* vdst = const_cast<uint32_t*>(vs[cp.dst]);
+  // buffers chosen without indexing a local array (which would live in local memory)
+  const K* src = cp.src == 0 ? k0 : (cp.src == 1 ? k1 : k2);
+  K* dst = const_cast<K*>(cp.dst == 0 ? k0 : (cp.dst == 1 ? k1 : k2));
+  const uint32_t* vsrc = cp.src == 0 ? v0 : (cp.src == 1 ? v1 : v2);
+  uint32_t* vdst = const_cast<uint32_t*>(cp.dst == 0 ? v0 : (cp.dst == 1 ? v1 : v2));
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   constexpr uint64_t kVec = 16 / sizeof(K);
   const uint64_t nv = n / kVec;
-  for (uint64_t i = tid; i < nv; i += stride)
-    reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+  copy_vectors(reinterpret_cast<uint4*>(dst), reinterpret_cast<const uint4*>(src), nv, tid, stride);
   for (uint64_t i = nv * kVec + tid; i < n; i += stride) dst[i] = src[i];
   if (vsrc && vdst) {
     const uint64_t nv4 = n / 4;
-    for (uint64_t i = tid; i < nv4; i += stride)
-      reinterpret_cast<uint4*>(vdst)[i] = reinterpret_cast<const uint4*>(vsrc)[i];
+    copy_vectors(reinterpret_cast<uint4*>(vdst), reinterpret_cast<const uint4*>(vsrc), nv4, tid, stride);
     for (uint64_t i = nv4 * 4 + tid; i < n; i += stride) vdst[i] = vsrc[i];
   }
 }
@@ -501,7 +515,7 @@ cudaError_t launch_scan_rows(const uint64_t* in, uint64_t* out, uint64_t rows, u
 
 cudaError_t launch_schedule_copy(const void* const keys[3], const uint32_t* const vals[3], int key_bits,
                                  bool has_vals, uint64_t n, const Schedule* sched, int sms, cudaStream_t stream) {
-  const unsigned grid = unsigned(sms) * 4;
+  const unsigned grid = unsigned(sms) * 4;  // all resident at once (256 threads, four CTAs per SM)
   const uint32_t* v0 = has_vals ? vals[0] : nullptr;
   const uint32_t* v1 = has_vals ? vals[1] : nullptr;
   const uint32_t* v2 = has_vals ? vals[2] : nullptr;
