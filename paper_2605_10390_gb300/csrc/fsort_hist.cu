@@ -228,30 +228,24 @@ __global__ void __launch_bounds__(256, 4) schedule_copy_kernel(const K* k0, cons
 // --------------------------------------------------------------- K1' -------
 // 65,536 counters of 16 bits, two per 32-bit shared-memory word (128 KB):
 // word w holds key w in its low half and key w + 32768 in its high half, so
-// the small, frequent keys of skewed inputs sit in different words.  Counters
-// are added with red.shared (no return value).  The lanes of one instruction
-// that hit the same word are served one at a time, like a bank conflict, so a
-// key that many lanes share costs as many passes.  So each warp keeps a
-// candidate frequent key: every fourth round it checks the candidate against
-// 32 of its keys (the lanes' first ones) with one ballot, takes the better of
-// two new candidates from rotating lanes when the old one is not among them
-// twice, and, when two or more lanes hold the candidate, counts that key in a
-// register for four rounds (the other keys' additions predicated, no branch
-// per key) and adds it once per warp at each round's end.
+// the small, frequent keys of skewed inputs sit in different words.
 //
 // Overflow is exact (the tapered width of Sec. III-D-1 with an exact spill):
-// a drain after every two rounds hands each counter's multiples of 2^14 to its
-// global 64-bit spill counter, leaving every counter below 2^14.  Two rounds
-// add at most 2 * kLeafRound = 49,152 keys to any counter, so no counter ever
-// exceeds 2^14 - 1 + 49,152 = 65,535 (no carry into the neighbouring half).
-// The drain reads the counters 16 bytes at a time and touches only words with
-// a counter at or above 2^14.
+// every addition returns the counter's old value, and the one addition that
+// takes a counter from below 2^15 to 2^15 subtracts 2^15 from it and adds 2^15
+// to the key's global 64-bit spill counter.  Every round ends at a block
+// barrier, after which every counter is below 2^15 (each crossing's
+// subtraction comes before its thread's barrier); a round adds at most
+// kLeafRound = 24,576 keys to any counter, so a counter stays below
+// 2^15 + 24,576 < 2^16 (no carry into the neighbouring half) and crosses 2^15
+// at most once per round.  No pass over the table is needed (an earlier form
+// read all 128 KB every 49,152 keys to move large counts out).
 constexpr int kLeafThreads = 1024;
 constexpr int kLeafWords = 32768;
 constexpr int kLeafVecPerThread = 3;                                   // uint4 = 8 keys each
 constexpr int kLeafRound = kLeafThreads * kLeafVecPerThread * 8;       // 24,576 keys
-constexpr uint32_t kLeafDrainBits = 0xC000C000u;                       // 2^14 and 2^15 of either half
-static_assert((1 << 14) - 1 + 2 * kLeafRound <= 65535, "two rounds must not overflow a drained 16-bit counter");
+constexpr uint32_t kLeafSpill = 0x8000u;                               // 2^15: moved to the spill on crossing
+static_assert(kLeafSpill + kLeafRound <= 65535, "a round must not carry a counter into its neighbour");
 
 __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16_t* __restrict__ keys, uint64_t n,
                                                                     uint32_t* __restrict__ partials,
@@ -261,10 +255,16 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
   __syncthreads();
   // Rounds are dealt to CTAs round-robin over the whole input; the next
   // round's keys are loaded into registers before this round's keys are
-  // counted, so the loads overlap the counting and the drains.
+  // counted, so the loads overlap the counting.
   const uint64_t rounds = (n + kLeafRound - 1) / kLeafRound;
-  auto add = [&](uint32_t k) { atomicAdd(&hw[k & 32767u], 1u << ((k >> 15) * 16)); };
-  const uint32_t hw_s = static_cast<uint32_t>(__cvta_generic_to_shared(hw));
+  auto add = [&](uint32_t k) {
+    const uint32_t sh = (k >> 15) * 16;
+    const uint32_t old = (atomicAdd(&hw[k & 32767u], 1u << sh) >> sh) & 0xFFFFu;
+    if (old == kLeafSpill - 1u) {  // this addition took the counter to 2^15
+      atomicSub(&hw[k & 32767u], kLeafSpill << sh);
+      atomicAdd(&spill[k], (unsigned long long)kLeafSpill);
+    }
+  };
   auto full = [&](uint64_t r) { return (r + 1) * kLeafRound <= n; };
   uint4 q[kLeafVecPerThread];
   auto load = [&](uint64_t r) {
@@ -274,9 +274,6 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
   };
   uint64_t r = blockIdx.x;
   if (r < rounds && full(r)) load(r);
-  uint32_t done = 0;               // rounds this CTA has counted
-  uint32_t cand = 0xFFFFFFFFu;     // the warp's candidate frequent key (none yet)
-  bool hot_on = false;             // whether this round counts the candidate in a register
   for (; r < rounds; r += gridDim.x) {
     const uint64_t next = r + gridDim.x;
     if (full(r)) {
@@ -284,80 +281,20 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
 #pragma unroll
       for (int u = 0; u < kLeafVecPerThread; ++u) cur[u] = q[u];
       if (next < rounds && full(next)) load(next);
-      if ((done & 3u) == 0) {  // the decision holds for four rounds
-        const uint32_t s0 = cur[0].x & 0xFFFFu;
-        uint32_t seen = __ballot_sync(0xffffffffu, s0 == cand);
-        if (__popc(seen) < 2) {  // two new candidates, from lanes j and j + 16
-          const uint32_t j = (done >> 2) & 15u;
-          const uint32_t c0 = __shfl_sync(0xffffffffu, s0, j), c1 = __shfl_sync(0xffffffffu, s0, j + 16u);
-          const uint32_t n0 = __popc(__ballot_sync(0xffffffffu, s0 == c0));
-          const uint32_t n1 = __popc(__ballot_sync(0xffffffffu, s0 == c1));
-          cand = n1 > n0 ? c1 : c0;
-          seen = n1 > n0 ? n1 : n0;
-        } else {
-          seen = 2;
-        }
-        hot_on = seen >= 2;
-      }
-      if (hot_on) {  // warp-uniform
-        const uint32_t hot = cand;
-        uint32_t ch = 0;
-        // a predicated red (no branch per key) for every other key; a count for the hot one
-        auto add_hot = [&](uint32_t k) {
-          asm volatile(
-              "{\n\t.reg .pred p;\n\t"
-              "setp.eq.u32 p, %1, %2;\n\t"
-              "@!p red.shared.add.u32 [%3], %4;\n\t"
-              "@p add.u32 %0, %0, 1;\n\t}"
-              : "+r"(ch)
-              : "r"(k), "r"(hot), "r"(hw_s + (k & 32767u) * 4u), "r"(1u << ((k >> 15) * 16)));
-          // no memory clobber: the table is read only after a block barrier, and additions commute
-        };
 #pragma unroll
-        for (int u = 0; u < kLeafVecPerThread; ++u) {
-          const uint32_t w[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
+      for (int u = 0; u < kLeafVecPerThread; ++u) {
+        const uint32_t w[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            add_hot(w[e] & 0xFFFFu);
-            add_hot(w[e] >> 16);
-          }
-        }
-        ch = __reduce_add_sync(0xffffffffu, ch);  // at most 32 x 24 keys of this round
-        if ((threadIdx.x & 31) == 0 && ch) atomicAdd(&hw[hot & 32767u], ch << ((hot >> 15) * 16));
-      } else {
-#pragma unroll
-        for (int u = 0; u < kLeafVecPerThread; ++u) {
-          const uint32_t w[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            add(w[e] & 0xFFFFu);
-            add(w[e] >> 16);
-          }
+        for (int e = 0; e < 4; ++e) {
+          add(w[e] & 0xFFFFu);
+          add(w[e] >> 16);
         }
       }
     } else {
       for (uint64_t i = r * kLeafRound + threadIdx.x; i < n; i += blockDim.x) add(keys[i]);
     }
-    if (++done & 1u) continue;  // drain after every second round
-    __syncthreads();
-    uint4* hv = reinterpret_cast<uint4*>(hw);
-    for (int i = threadIdx.x; i < kLeafWords / 4; i += blockDim.x) {
-      const uint4 v = hv[i];
-      if (((v.x | v.y | v.z | v.w) & kLeafDrainBits) == 0) continue;
-      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const uint32_t wd = w4[e], take = wd & kLeafDrainBits;
-        if (!take) continue;
-        const uint32_t word = 4 * i + e;
-        if (take & 0xFFFFu) atomicAdd(&spill[word], (unsigned long long)(take & 0xFFFFu));
-        if (take >> 16) atomicAdd(&spill[word + 32768], (unsigned long long)(take >> 16));
-        hw[word] = wd - take;
-      }
-    }
-    __syncthreads();
+    __syncthreads();  // every counter is below 2^15 again (see above)
   }
-  __syncthreads();  // a last round without a drain has no barrier of its own: every add lands before the copy
   for (int i = threadIdx.x; i < kLeafWords; i += blockDim.x) partials[uint64_t(blockIdx.x) * kLeafWords + i] = hw[i];
 }
 
