@@ -232,19 +232,19 @@ __global__ void __launch_bounds__(256, 4) schedule_copy_kernel(const K* k0, cons
 //
 // Overflow is exact (the tapered width of Sec. III-D-1 with an exact spill):
 // every addition returns the counter's old value, and the one addition that
-// takes a counter from below 2^15 to 2^15 subtracts 2^15 from it and adds 2^15
+// takes a counter from below 2^14 to 2^14 subtracts 2^14 from it and adds 2^14
 // to the key's global 64-bit spill counter.  Every round ends at a block
-// barrier, after which every counter is below 2^15 (each crossing's
+// barrier, after which every counter is below 2^14 (each crossing's
 // subtraction comes before its thread's barrier); a round adds at most
-// kLeafRound = 24,576 keys to any counter, so a counter stays below
-// 2^15 + 24,576 < 2^16 (no carry into the neighbouring half) and crosses 2^15
-// at most once per round.  No pass over the table is needed (an earlier form
-// read all 128 KB every 49,152 keys to move large counts out).
+// kLeafRound = 32,768 keys to any counter, so a counter stays below
+// 2^14 + 32,768 < 2^16 (no carry into the neighbouring half).  No pass over
+// the table is needed (an earlier form read all 128 KB every 49,152 keys to
+// move large counts out).
 constexpr int kLeafThreads = 1024;
 constexpr int kLeafWords = 32768;
-constexpr int kLeafVecPerThread = 3;                                   // uint4 = 8 keys each
-constexpr int kLeafRound = kLeafThreads * kLeafVecPerThread * 8;       // 24,576 keys
-constexpr uint32_t kLeafSpill = 0x8000u;                               // 2^15: moved to the spill on crossing
+constexpr int kLeafVecPerThread = 4;                                   // uint4 = 8 keys each
+constexpr int kLeafRound = kLeafThreads * kLeafVecPerThread * 8;       // 32,768 keys
+constexpr uint32_t kLeafSpill = 0x4000u;                               // 2^14: moved to the spill on crossing
 static_assert(kLeafSpill + kLeafRound <= 65535, "a round must not carry a counter into its neighbour");
 
 __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16_t* __restrict__ keys, uint64_t n,
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
   auto add = [&](uint32_t k) {
     const uint32_t sh = (k >> 15) * 16;
     const uint32_t old = (atomicAdd(&hw[k & 32767u], 1u << sh) >> sh) & 0xFFFFu;
-    if (old == kLeafSpill - 1u) {  // this addition took the counter to 2^15
+    if (old == kLeafSpill - 1u) {  // this addition took the counter to kLeafSpill
       atomicSub(&hw[k & 32767u], kLeafSpill << sh);
       atomicAdd(&spill[k], (unsigned long long)kLeafSpill);
     }
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) leaf_hist_kernel(const uint16
     } else {
       for (uint64_t i = r * kLeafRound + threadIdx.x; i < n; i += blockDim.x) add(keys[i]);
     }
-    __syncthreads();  // every counter is below 2^15 again (see above)
+    __syncthreads();  // every counter is below kLeafSpill again (see above)
   }
   for (int i = threadIdx.x; i < kLeafWords; i += blockDim.x) partials[uint64_t(blockIdx.x) * kLeafWords + i] = hw[i];
 }
