@@ -581,6 +581,14 @@ def run_serving(fs, workloads, torch, stream, requests: int = 48, lo: int = 16, 
             "requests": requests, "lanes": lanes, "hbm_budget_bytes": budget, "p50_ms": rank(0.50), "p99_ms": rank(0.99),
             "mean_ms": float(np.mean(lat)), "max_ms": lat[-1], "keys_per_s": sum(sizes) / span, "span_s": span,
             "queue_ms_mean": float(np.mean([r["queue_ms"] for r in results.values()])),
+            # where the tail's time went: the slowest requests split into waiting for a lane and running
+            # (copies in, sort, copies out), and the running time per key by size
+            "slowest": [{"n": int(r["n"]), "latency_ms": r["latency_ms"], "queue_ms": r["queue_ms"],
+                         "run_ms": r["run_ms"], "run_ns_per_key": 1e6 * r["run_ms"] / max(1, int(r["n"]))}
+                        for r in sorted(results.values(), key=lambda r: -r["latency_ms"])[:3]],
+            "run_ns_per_key_by_size": {f"2^{b}..2^{b + 4}": float(np.median(v)) for b, v in (
+                (b, [1e6 * r["run_ms"] / int(r["n"]) for r in results.values()
+                     if b <= np.log2(max(1, int(r["n"]))) < b + 4]) for b in range(lo, hi, 4)) if v},
             "batched_requests": sum(1 for r in results.values() if r["batched"]),
             "max_inflight": st["max_inflight"], "peak_bytes": st["peak_bytes"], "outputs_sorted": ok,
             "api": "fsort_serve_submit / fsort_serve_wait (pinned host buffers; copies in the latency)"}
