@@ -100,6 +100,7 @@ struct fsort_plan {
   uint64_t table_tiles = 0;      // tiles of the largest sort the offset table serves (n < 2^32)
   uint32_t table_chunks = 0;     // chunks of the count kernel (at most two per SM)
   uint32_t* tilerel = nullptr;   // [table_tiles][256] per-tile digit offsets within the tile's chunk
+  uint16_t* stripcnt = nullptr;  // [table_tiles][16][256] per-tile digit counts of each warp strip
   uint32_t* chunksum = nullptr;  // [table_chunks][256] per-chunk digit totals
   uint32_t* chunkoff = nullptr;  // [table_chunks][256] per-chunk digit output offsets
   uint64_t* orand = nullptr;     // [2] OR and AND of the keys of one sort (0 and all ones between calls)
@@ -135,6 +136,7 @@ struct fsort_plan {
   // table form of the large segments (fsort_batch_config::large_form = 1)
   uint64_t max_ttiles = 0, max_tchunks = 0;
   uint32_t* bt_tilerel = nullptr;   // [tiles][256] per-tile digit offsets within the tile's chunk
+  uint16_t* bt_stripcnt = nullptr;  // [tiles][16][256] per-tile digit counts of each warp strip
   uint32_t* bt_chunksum = nullptr;  // [chunks][256]
   uint32_t* bt_chunkoff = nullptr;  // [chunks][256], relative to the segment's start
   uint32_t* d_chunk_seg = nullptr;  // [chunks] segment of each chunk
@@ -318,6 +320,7 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
     ca.tiles = g.tiles;
     ca.chunk_tiles = g.chunk_tiles;
     ca.tilerel = p->tilerel;
+    ca.stripcnt = p->stripcnt;
     ca.chunksum = p->chunksum;
     ca.totals = p->totals;
     ca.orand = p->orand;
@@ -354,6 +357,7 @@ fsort_status enqueue_sort(fsort_plan* p, const void* keys_in, const uint32_t* va
       a.tiles = g.tiles;
       a.chunk_tiles = g.chunk_tiles;
       a.tilerel = p->tilerel;
+      a.stripcnt = p->stripcnt;
       a.chunkoff = p->chunkoff;
       a.totals = p->totals + (j & 1) * kRadix;
       a.sched = p->sched;
@@ -612,6 +616,7 @@ cudaError_t enqueue_batch(fsort_plan* p, const BatchShape& b, int key_bits, int 
       ca.tiles = b.total_tiles;
       ca.chunk_tiles = kBatchChunkTiles;
       ca.tilerel = p->bt_tilerel;
+      ca.stripcnt = p->bt_stripcnt;
       ca.chunksum = p->bt_chunksum;
       ca.pass = j;
       ca.status = p->status;
@@ -628,6 +633,7 @@ cudaError_t enqueue_batch(fsort_plan* p, const BatchShape& b, int key_bits, int 
       a.tiles = b.total_tiles;
       a.chunk_tiles = kBatchChunkTiles;
       a.tilerel = p->bt_tilerel;
+      a.stripcnt = p->bt_stripcnt;
       a.chunkoff = p->bt_chunkoff;
       a.pass = j;
       a.status = p->status;
@@ -897,6 +903,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   const size_t o_sched = take(sizeof(Schedule));
   const size_t o_status = take(sizeof(uint32_t));
   const size_t o_trel = take(size_t(p->table_tiles) * kRadix * 4);
+  const size_t o_tsc = take(size_t(p->table_tiles) * kTableStrips * kRadix * 2);
   const size_t o_csum = take(size_t(p->table_chunks) * kRadix * 4);
   const size_t o_coff = take(size_t(p->table_chunks) * kRadix * 4);
   const size_t o_orand = take(2 * sizeof(uint64_t));
@@ -909,7 +916,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   }
   const int pmax = batch_max_passes(desc->key_bits);
   size_t o_bsl = 0, o_bss = 0, o_bch = 0, o_bts = 0, o_bh = 0, o_bb = 0, o_bctr = 0;
-  size_t o_btr = 0, o_btcs = 0, o_btco = 0, o_btseg = 0;
+  size_t o_btr = 0, o_btcs = 0, o_btco = 0, o_btseg = 0, o_btsc = 0;
   if (batch) {
     p->max_hist_chunks = n / kBatchHistChunk + desc->max_segments + 1;
     o_bsl = take(size_t(desc->max_segments) * sizeof(SegDesc));
@@ -923,6 +930,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     p->max_ttiles = n / tt + desc->max_segments + 1;  // every segment may add one partial tile
     p->max_tchunks = p->max_ttiles / kBatchChunkTiles + desc->max_segments + 1;
     o_btr = take(size_t(p->max_ttiles) * kRadix * 4);
+    o_btsc = take(size_t(p->max_ttiles) * kTableStrips * kRadix * 2);
     o_btcs = take(size_t(p->max_tchunks) * kRadix * 4);
     o_btco = take(size_t(p->max_tchunks) * kRadix * 4);
     o_btseg = take(size_t(p->max_tchunks) * 4);
@@ -1002,6 +1010,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
   p->sched = reinterpret_cast<Schedule*>(w + o_sched);
   p->status = reinterpret_cast<uint32_t*>(w + o_status);
   p->tilerel = reinterpret_cast<uint32_t*>(w + o_trel);
+  p->stripcnt = reinterpret_cast<uint16_t*>(w + o_tsc);
   p->chunksum = reinterpret_cast<uint32_t*>(w + o_csum);
   p->chunkoff = reinterpret_cast<uint32_t*>(w + o_coff);
   p->orand = reinterpret_cast<uint64_t*>(w + o_orand);
@@ -1015,6 +1024,7 @@ fsort_status fsort_plan_create(const fsort_plan_desc* desc, fsort_plan** out_pla
     p->d_bbases = reinterpret_cast<uint64_t*>(w + o_bb);
     p->d_small_counter = reinterpret_cast<uint32_t*>(w + o_bctr);
     p->bt_tilerel = reinterpret_cast<uint32_t*>(w + o_btr);
+    p->bt_stripcnt = reinterpret_cast<uint16_t*>(w + o_btsc);
     p->bt_chunksum = reinterpret_cast<uint32_t*>(w + o_btcs);
     p->bt_chunkoff = reinterpret_cast<uint32_t*>(w + o_btco);
     p->d_chunk_seg = reinterpret_cast<uint32_t*>(w + o_btseg);

@@ -4,17 +4,19 @@
 //
 //  KT1 tile_count_kernel      one read of a pass's input, one CTA per chunk of
 //                             consecutive tiles: for every tile the counts of
-//                             each digit in the chunk's earlier tiles, the
-//                             chunk's totals, the pass's totals; on the first
-//                             read of the input also the OR and AND of all keys
+//                             each digit in the chunk's earlier tiles and in
+//                             each of the tile's 16 warp strips, the chunk's
+//                             totals, the pass's totals; on the first read of
+//                             the input also the OR and AND of all keys
 //  table_schedule_kernel      trivial passes (OR and AND agree on the digit)
 //                             and the buffer routing
 //  KT2 chunk_scan_kernel      per digit, the keys of lower digits plus the
 //                             exclusive scan of the chunk totals (Alg. 3's rank
 //                             of every leaf, split over chunks)
 //  KT3 tile_scatter_kernel    one CTA per tile: bulk copy of keys and values
-//                             into shared memory, per-warp digit counts, the
-//                             tile's digit prefixes, stable ranks placed
+//                             into shared memory, the per-warp digit counts
+//                             from KT1's strip table, the tile's digit
+//                             prefixes, stable ranks placed
 //                             straight into digit order in shared memory, and
 //                             the write-out in digit runs at the tile's offsets
 //                             (chunk offset + offset within the chunk).
@@ -61,8 +63,11 @@ __device__ __forceinline__ T* pick(T* const (&b)[3], int sel) {
 // ------------------------------------------------------------------ KT1 ----
 // One digit (shift, mask) per launch.  CTA c walks the tiles of chunk c in
 // order and writes for each tile the counts of its digits in the chunk's
-// earlier tiles (tilerel[t][256]), then the chunk's totals (chunksum[c][256])
-// and adds them to the pass's digit totals (totals[256], zero on entry).
+// earlier tiles (tilerel[t][256]) and the digit counts of each of the tile's
+// 16 strips (stripcnt[t][w][256], 16 bits: strip w is the keys KT3's warp w
+// ranks, so KT3 needs no counting pass of its own), then the chunk's totals
+// (chunksum[c][256]) and adds them to the pass's digit totals (totals[256],
+// zero on entry).
 // kOrAnd (the first read of the input) also folds every key into
 // orand[0] |= k and orand[1] &= k: a pass is trivial (all keys share its
 // digit) exactly when the two agree on the digit's bits, so the schedule needs
@@ -114,14 +119,15 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
   constexpr int kCountVecs = count_vecs<K>();
   static_assert(uint32_t(kThreads) * kVec * kCountVecs == kTileKeys, "threads cover a tile exactly");
   extern __shared__ __align__(128) unsigned char smem[];  // [kCountStages][tile keys]
-  // Running counts of the chunk's tiles so far, tiles alternating between two
-  // sets.  Each digit has 16 copies, one per lane & 15: word [d][c] sits in
-  // bank 16 (d & 1) + c, so of a warp's 32 additions only lanes l and l + 16
-  // can meet in a bank (when their digits have the same parity).  The counts
-  // are never cleared: the thread of digit d sums its 16 copies after each
-  // tile and subtracts the sum it saw two tiles earlier (same set).  Sums stay
-  // below 2^32: a chunk holds fewer than 2^32 keys.
-  __shared__ __align__(128) uint32_t s_cnt[2][kRadix][16];
+  // Counts of one tile per strip and digit, tiles alternating between two
+  // sets: the thread of digit d reads its 16 strip counts after the tile's
+  // barrier and clears them, and the set is counted into again two tiles later
+  // (after another barrier).
+  constexpr uint32_t kStripKeys = 32u * uint32_t(TileShape<K>::kIpt);  // keys of one KT3 warp strip
+  constexpr int kStrips = TileShape<K>::kBlock / 32;
+  static_assert(kStrips == kTableStrips && kStripKeys % kVec == 0 && kStrips * kStripKeys == kTileKeys,
+                "strips of whole vectors tile the tile");
+  __shared__ __align__(128) uint32_t s_cnt[2][kStrips][kRadix];
   __shared__ uint64_t s_bar[kCountStages];
   __shared__ uint32_t s_fail[2];  // by tile parity: a tile reads only its own flag after its barrier
   K* buf = reinterpret_cast<K*>(smem);
@@ -172,11 +178,10 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
     s_fail[0] = s_fail[1] = 0;
     for (uint32_t st = 0; st < steps && st < uint32_t(kCountStages); ++st) issue(st);
   }
-  for (int i = tid; i < 2 * kRadix * 16; i += kThreads) (&s_cnt[0][0][0])[i] = 0;
+  for (int i = tid; i < 2 * kStrips * kRadix; i += kThreads) (&s_cnt[0][0][0])[i] = 0;
   __syncthreads();
 
   const uint32_t shift = a.shift, mask = a.mask;
-  const uint32_t copy = uint32_t(tid) & 15u;
   uint64_t k_or = 0, k_and = ~0ull;  // this thread's keys of ragged ends folded
   // Whole 16-byte vectors are folded word by word: w_or[h] / w_and[h] cover the
   // vector words of parity h (for 64-bit keys the low and high halves; for
@@ -191,10 +196,9 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
     }
   };
   uint32_t set = 0;
-  uint32_t seen0 = 0, seen1 = 0;  // thread d < 256: digit d's sum over set 0's / set 1's copies at its last tile
-  auto count_key = [&](K k) { atomicAdd(&s_cnt[set][dig(k, shift, mask)][copy], 1u); };
-  auto count_ragged = [&](K k) {
-    count_key(k);
+  auto count_key = [&](K k, uint32_t strip) { atomicAdd(&s_cnt[set][strip][dig(k, shift, mask)], 1u); };
+  auto count_ragged = [&](K k, uint32_t strip) {
+    count_key(k, strip);
     if (kOrAnd) {
       k_or |= uint64_t(k);
       k_and &= uint64_t(k);
@@ -211,19 +215,22 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
     if (body == kTileKeys) {
 #pragma unroll
       for (int j = 0; j < kCountVecs; ++j) {
-        const uint4 q = bv[tid + j * kThreads];
+        const uint32_t v = uint32_t(tid + j * kThreads);
+        const uint4 q = bv[v];
         fold_vec(q);
+        const uint32_t strip = v * kVec / kStripKeys;  // a vector lies in one strip
 #pragma unroll
-        for (int e = 0; e < int(kVec); ++e) count_key(vec_key<K>(q, e));
+        for (int e = 0; e < int(kVec); ++e) count_key(vec_key<K>(q, e), strip);
       }
     } else {  // the last, short tile
       for (uint32_t v = tid; v < body / kVec; v += kThreads) {
         const uint4 q = bv[v];
         fold_vec(q);
+        const uint32_t strip = v * kVec / kStripKeys;
 #pragma unroll
-        for (int e = 0; e < int(kVec); ++e) count_key(vec_key<K>(q, e));
+        for (int e = 0; e < int(kVec); ++e) count_key(vec_key<K>(q, e), strip);
       }
-      for (uint32_t i = body + tid; i < keys_n; i += kThreads) count_ragged(keys[e0 + i]);  // ragged end
+      for (uint32_t i = body + tid; i < keys_n; i += kThreads) count_ragged(keys[e0 + i], i / kStripKeys);  // ragged end
     }
     __syncthreads();
     if (s_fail[st & 1u]) {  // the table would be wrong: mark it so that no scatter uses it
@@ -235,16 +242,18 @@ __global__ void __launch_bounds__(count_threads<K>(), count_ctas_per_sm<K>()) ti
       return;
     }
     if (tid < kRadix) {  // meanwhile the next tile counts into the other set
-      a.tilerel[uint64_t(g_tile0 + st) * kRadix + tid] = acc;
-      // digit tid's 16 copies, visited in a rotated order so that the warp's
-      // 32 reads fall in 32 banks (bank 16 (tid & 1) + copy)
-      const uint32_t* row = s_cnt[set][tid];
+      const uint64_t g_tile = uint64_t(g_tile0 + st);
+      a.tilerel[g_tile * kRadix + tid] = acc;
+      uint16_t* sc = a.stripcnt + g_tile * (kStrips * kRadix) + tid;
       uint32_t c = 0;
 #pragma unroll
-      for (uint32_t l = 0; l < 16; ++l) c += row[(l + (uint32_t(tid) >> 1)) & 15u];
-      acc += c - (set ? seen1 : seen0);
-      if (set) seen1 = c;
-      else seen0 = c;
+      for (int w = 0; w < kStrips; ++w) {
+        const uint32_t x = s_cnt[set][w][tid];
+        s_cnt[set][w][tid] = 0;  // counted into again two tiles later, after another barrier
+        sc[w * kRadix] = uint16_t(x);
+        c += x;
+      }
+      acc += c;
     }
     if (tid == 0 && st + kCountStages < steps) {  // every thread has read this buffer (barrier above)
       fence_proxy_async_smem();
@@ -418,6 +427,7 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   constexpr int kTile = L::kTile;
   constexpr int kWarps = L::kWarps;
   static_assert(kTile <= 65536, "in-warp ranks and source positions are kept in 16 bits");
+  static_assert(kWarps == kTableStrips, "one warp per strip of KT1's strip counts");
   static_assert(L::kVals_ % 16 == 0 && L::kWcnt % 16 == 0 && L::kGrp % 128 == 0,
                 "bulk-copy targets, 16-byte clears, one bank per group word");
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -473,8 +483,8 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   const uint32_t tile_n = uint32_t((n_keys - t0 < uint64_t(kTile)) ? (n_keys - t0) : uint64_t(kTile));
 
   // 1. stage the tile: bulk copies for the 16-byte-aligned body, plain loads
-  // for a ragged end; meanwhile clear the warp counters and read the tile's
-  // offsets from the table.
+  // for a ragged end; meanwhile read the tile's offsets and its strips' digit
+  // counts (KT1 counted them) from the table.
   const uint32_t kbody = (tile_n * uint32_t(sizeof(K))) & ~15u;
   const uint32_t vbody = kVals ? ((tile_n * 4u) & ~15u) : 0u;
   if (tid == 0) {
@@ -485,8 +495,9 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
     if (vbody) bulk_copy_g2s(s_vals, vin + t0, vbody, s_bar);
   }
   {
-    uint4* z = reinterpret_cast<uint4*>(s_wcnt);
-    for (int i = tid; i < kWarps * kRadix / 4; i += kBlock) z[i] = make_uint4(0, 0, 0, 0);
+    const uint16_t* sc = a.stripcnt + uint64_t(tile) * (kWarps * kRadix);
+#pragma unroll
+    for (int i = tid; i < kWarps * kRadix; i += kBlock) s_wcnt[i] = sc[i];
   }
   if (tid < kRadix)  // lands while the copy does
     s_off[tid] = a.chunkoff[uint64_t(chunk) * kRadix + tid] + a.tilerel[uint64_t(tile) * kRadix + tid];
@@ -504,27 +515,25 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
     return;
   }
 
-  // 2. each warp counts the digits of its strip (item i of lane l is the key
-  // at wbase + i*32 + l); the keys stay in registers
+  // 2. each warp loads its strip (item i of lane l is the key at
+  // wbase + i*32 + l) into registers
   const uint32_t shift = a.shift, mask = a.mask;
   uint32_t* wcnt = s_wcnt + warp * kRadix;
   const int wbase = warp * 32 * kIpt;
   KeyRegs<K, kIpt> kr;
   // steps 2 and 4 are compiled twice: for whole tiles (every position valid) and the short last one
-  auto count_step = [&](auto full) {
+  auto load_step = [&](auto full) {
     constexpr bool kFull = decltype(full)::value;
 #pragma unroll
     for (int i = 0; i < kIpt; ++i) {
       const int pos = wbase + i * 32 + lane;
       const bool valid = kFull || uint32_t(pos) < tile_n;
-      const K k = valid ? s_keys[pos] : K(0);
-      kr.set(i, k);
-      if (valid) atomicAdd(&wcnt[dig(k, shift, mask)], 1u);
+      kr.set(i, valid ? s_keys[pos] : K(0));
     }
   };
-  if (tile_n == uint32_t(kTile)) count_step(FullTile<true>{});
-  else count_step(FullTile<false>{});
-  __syncthreads();
+  if (tile_n == uint32_t(kTile)) load_step(FullTile<true>{});
+  else load_step(FullTile<false>{});
+  // (no barrier: the warp counts came from the table before the copy barrier, and the loads only read)
 
   // 3. per digit: each warp's first position of the digit in the tile's
   // digit order (warp prefixes on top of the tile's exclusive digit prefix),

@@ -109,6 +109,9 @@ struct TableGeom {
 };
 int table_tile_keys_for(int key_bits);
 TableGeom table_geometry(uint64_t n, int key_bits, int sms);
+// Warp strips of a table-form tile (KT3's warps): KT1 counts every tile's
+// digits per strip, 16-bit counts in stripcnt[tile][strip][256].
+constexpr int kTableStrips = 16;
 
 // KT1: for the digit (shift, mask), per tile the counts of each digit in the
 // earlier tiles of its chunk (tilerel[t][256]), per chunk the digit totals
@@ -141,6 +144,9 @@ struct TileCountArgs {
   // (SegDesc::first_tile), totals and orand are unused.
   const SegDesc* segs = nullptr;
   const uint32_t* chunk_seg = nullptr;
+  // Digit counts of every tile's 16 strips (the keys KT3's warp w ranks):
+  // stripcnt[t][w][256], 16 bits, indexed by global tile like tilerel.
+  uint16_t* stripcnt = nullptr;
 };
 cudaError_t launch_tile_count(const TileCountArgs& a, int key_bits, uint32_t chunks, cudaStream_t stream);
 // Segmented KT2: for every segment (one CTA each) and digit d, the exclusive
@@ -179,6 +185,8 @@ struct TileScatterArgs {
   // even passes write the segment's scratch space, odd passes its own buffers.
   const SegDesc* segs = nullptr;
   const uint32_t* tile_seg = nullptr;
+  // The tile's per-strip digit counts from KT1 (stripcnt[t][w][256]).
+  const uint16_t* stripcnt = nullptr;
 };
 cudaError_t launch_tile_scatter(const TileScatterArgs& a, int key_bits, bool has_vals, cudaStream_t stream);
 
