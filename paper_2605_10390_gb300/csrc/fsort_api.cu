@@ -70,6 +70,10 @@ struct LearnedWs {
   fsort::LearnedState* h_st = nullptr;  // pinned
   bool fitted = false;
   int32_t used = -1;
+  // Host bound on st->heavy_count for the level-1 count's shared memory: the
+  // maximum after a fit (the fit is stream-ordered), exact after a model is
+  // set or a learned sort has read the state back.
+  uint32_t heavy_count = kLearnMaxHeavy;
   uint32_t steps = 0, last_b = 0, last_limit = 0, last_max = 0, last_heavy = 0;
   double last_imbalance = 0.0;
 };
@@ -440,7 +444,7 @@ fsort_status enqueue_learned(fsort_plan* p, const void* keys_in, void* keys_out,
   if (e == cudaSuccess) e = cudaMemsetAsync(L.bitmap, 0, size_t(g.nids / 32 + 1) * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(L.counts1 + l1n, 0, 4, s);
   if (e == cudaSuccess) e = launch_learn_heavy_ids(mp, L.st, L.hid, L.bitmap, s);
-  if (e == cudaSuccess) e = launch_learn_l1(kin, n, g, mp, L.st, L.counts1, L.hcount, L.ids, s);
+  if (e == cudaSuccess) e = launch_learn_l1(kin, n, g, mp, L.st, L.heavy_count, L.counts1, L.hcount, L.ids, s);
   tm.mark(FSORT_KERNEL_LEARN_COUNT1, -1);
   if (e == cudaSuccess) e = launch_scan_u32(L.counts1, l1n + 1, L.off1, nullptr, L.sums, s);
   if (e == cudaSuccess) e = launch_learn_l1_scatter(kin, L.ids, n, g, L.off1, alt, L.fine, s);
@@ -460,6 +464,7 @@ fsort_status enqueue_learned(fsort_plan* p, const void* keys_in, void* keys_out,
   L.last_limit = uint32_t(limit);
   L.last_max = mx;
   L.last_heavy = L.h_st->heavy_count;
+  L.heavy_count = L.h_st->heavy_count < uint32_t(kLearnMaxHeavy) ? L.h_st->heavy_count : uint32_t(kLearnMaxHeavy);
   L.last_imbalance = double(mx) * double(B) / double(n);
   if (!accept) return enqueue_sort(p, keys_in, nullptr, keys_out, nullptr, n, 64, 64, s);
   e = launch_scan_u32(L.counts, g.nids, L.offsets, nullptr, L.sums, s);
@@ -1420,6 +1425,7 @@ fsort_status learned_fit_impl(fsort_plan* plan, const void* keys, uint64_t n, co
     L.fitted = true;
     L.steps = 0;
     L.used = -1;
+    L.heavy_count = kLearnMaxHeavy;
     return finish_call(plan, s);
   }
   if (e == cudaSuccess) e = launch_learn_init_kinks(L.train, L.st, L.master, s);
@@ -1437,6 +1443,7 @@ fsort_status learned_fit_impl(fsort_plan* plan, const void* keys, uint64_t n, co
   L.fitted = true;
   L.steps = steps;
   L.used = -1;
+  L.heavy_count = kLearnMaxHeavy;
   return finish_call(plan, s);
 }
 }  // namespace
@@ -1538,6 +1545,7 @@ fsort_status fsort_learned_set_model(fsort_plan* plan, const float* params_host,
   L.fitted = true;
   L.steps = 0;
   L.used = -1;
+  L.heavy_count = heavy_count;
   return FSORT_OK;
 }
 

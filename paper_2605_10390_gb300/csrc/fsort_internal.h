@@ -319,8 +319,8 @@ cudaError_t launch_learn_heavy_ids(const LearnedMap& mp, LearnedState* st, uint3
 // counts1[nsuper * nch] (super-bucket major), hcount[kLearnMaxHeavy] accumulated,
 // ids[n] every key's bucket id (all ones for heavy keys).
 cudaError_t launch_learn_l1(const uint64_t* keys, uint64_t n, const LearnedGeom& g, const LearnedMap& mp,
-                            const LearnedState* st, uint32_t* counts1, uint32_t* hcount, uint32_t* ids,
-                            cudaStream_t stream);
+                            const LearnedState* st, uint32_t heavy_count, uint32_t* counts1, uint32_t* hcount,
+                            uint32_t* ids, cudaStream_t stream);
 // off1: exclusive scan of counts1 with one extra entry (the total); fine[] receives
 // each scattered key's fine digit (id & (2^fbits - 1)) at the key's position in alt.
 cudaError_t launch_learn_l1_scatter(const uint64_t* keys, const uint32_t* ids, uint64_t n, const LearnedGeom& g,

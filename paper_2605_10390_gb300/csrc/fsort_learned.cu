@@ -765,12 +765,15 @@ __global__ void __launch_bounds__(kPartThreads) learn_l1_count_kernel(const uint
                                                                       const LearnedState* __restrict__ st,
                                                                       uint32_t* __restrict__ counts1,
                                                                       uint32_t* __restrict__ hcount,
-                                                                      uint32_t* __restrict__ ids) {
+                                                                      uint32_t* __restrict__ ids, uint32_t heavy_cap) {
+  // Shared memory sized to this sort (nsuper + heavy_cap words, heavy_cap the
+  // host's count of heavy keys, at most kLearnMaxHeavy): the rest of the SM's
+  // L1/shared capacity stays L1 cache for the map lookups.
   extern __shared__ uint32_t l1_smem[];
-  uint32_t* s_cnt = l1_smem;                 // [kMaxSuper]
-  uint32_t* s_heavy = l1_smem + kMaxSuper;   // [kLearnMaxHeavy]
-  for (int i = threadIdx.x; i < kMaxSuper; i += kPartThreads) s_cnt[i] = 0;
-  for (int i = threadIdx.x; i < kLearnMaxHeavy; i += kPartThreads) s_heavy[i] = 0;
+  const uint32_t m = min(st->heavy_count, heavy_cap);
+  uint32_t* s_cnt = l1_smem;             // [nsuper]
+  uint32_t* s_heavy = l1_smem + nsuper;  // [m]
+  for (uint32_t i = threadIdx.x; i < nsuper + m; i += kPartThreads) l1_smem[i] = 0;
   __syncthreads();
   const uint32_t c = blockIdx.x;
   const uint64_t lo = uint64_t(c) * chunk, hi = lo + chunk < n ? lo + chunk : n;
@@ -779,13 +782,12 @@ __global__ void __launch_bounds__(kPartThreads) learn_l1_count_kernel(const uint
     uint32_t t = 0;
     const uint32_t id = map_id(k, mp, hit, t);
     if (valid) {
-      atomicAdd(hit ? &s_heavy[t] : &s_cnt[id >> fbits], 1u);
+      atomicAdd(hit ? &s_heavy[t < m ? t : 0u] : &s_cnt[id >> fbits], 1u);  // t < m whenever the host's count is right
       ids[i] = hit ? kHeavyId : id;
     }
   });
   __syncthreads();
   for (uint32_t s = threadIdx.x; s < nsuper; s += kPartThreads) counts1[uint64_t(s) * nch + c] = s_cnt[s];
-  const uint32_t m = st->heavy_count;
   for (uint32_t t = threadIdx.x; t < m; t += kPartThreads)
     if (s_heavy[t]) atomicAdd(&hcount[t], s_heavy[t]);
 }
@@ -1628,13 +1630,15 @@ LearnedGeom learned_geometry(uint64_t n, uint32_t buckets) {
 }
 
 cudaError_t launch_learn_l1(const uint64_t* keys, uint64_t n, const LearnedGeom& g, const LearnedMap& mp,
-                            const LearnedState* st, uint32_t* counts1, uint32_t* hcount, uint32_t* ids,
-                            cudaStream_t stream) {
-  constexpr int kBytes = (kMaxSuper + kLearnMaxHeavy) * 4;
-  static const cudaError_t attr = set_smem_attrs(learn_l1_count_kernel, kBytes, false);
+                            const LearnedState* st, uint32_t heavy_count, uint32_t* counts1, uint32_t* hcount,
+                            uint32_t* ids, cudaStream_t stream) {
+  constexpr int kMaxBytes = (kMaxSuper + kLearnMaxHeavy) * 4;
+  static const cudaError_t attr = set_smem_attrs(learn_l1_count_kernel, kMaxBytes, false);
   if (attr != cudaSuccess) return attr;
-  learn_l1_count_kernel<<<g.nch, kPartThreads, kBytes, stream>>>(keys, n, g.chunk, g.nch, g.nsuper, g.fbits, mp, st,
-                                                                 counts1, hcount, ids);
+  if (g.nsuper > uint32_t(kMaxSuper) || heavy_count > uint32_t(kLearnMaxHeavy)) return cudaErrorInvalidValue;
+  const size_t bytes = size_t(g.nsuper + heavy_count) * 4;
+  learn_l1_count_kernel<<<g.nch, kPartThreads, bytes, stream>>>(keys, n, g.chunk, g.nch, g.nsuper, g.fbits, mp, st,
+                                                                counts1, hcount, ids, heavy_count);
   return cudaGetLastError();
 }
 
