@@ -533,7 +533,10 @@ __global__ void __launch_bounds__(TileShape<K>::kBlock, TileShape<K>::kMinBlocks
   };
   if (tile_n == uint32_t(kTile)) load_step(FullTile<true>{});
   else load_step(FullTile<false>{});
-  // (no barrier: the warp counts came from the table before the copy barrier, and the loads only read)
+  // No barrier here: the warp counts came from the table before the copy
+  // barrier, and the scan below holds a block barrier that every warp reaches
+  // only after its loads, so no record store of the rank step (they overwrite
+  // the staged keys) can come before another warp's load.
 
   // 3. per digit: each warp's first position of the digit in the tile's
   // digit order (warp prefixes on top of the tile's exclusive digit prefix),
