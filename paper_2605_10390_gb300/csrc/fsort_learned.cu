@@ -1031,56 +1031,69 @@ __global__ void __launch_bounds__(256) learn_fill_kernel(LearnedMap mp, const Le
 }
 
 // On-chip sort of the buckets, one unit per CTA iteration, in place.  A unit
-// is a run of consecutive non-heavy buckets with at most 8192 keys in all
-// (contiguous in memory).  The unit's keys are split into at most 8192
-// sub-buckets by the top 13 bits of key - min in one counting pass through
-// shared memory (16-bit counters, two to a word: no count or offset exceeds
-// 8192); a key of a sub-bucket of at most 16 keys finds its place by
-// counting the smaller keys there, and the larger sub-buckets (in practice a
-// moderately frequent key among a few others) are split again by warps.  The
-// next unit's keys are prefetched into shared memory (cp.async) while one is
-// sorted.  A unit whose large ranges overflow the round list is finished by a
-// bitonic network instead.
-constexpr int kBsThreads = 1024;
-constexpr int kBsWarps = kBsThreads / 32;
-constexpr int kBsIpt = kLearnBucketCap / kBsThreads;  // keys per thread
-constexpr int kSubBits = 13;
-constexpr int kSub = 1 << kSubBits;
-constexpr int kSubPerThread = kSub / kBsThreads;
+// is a run of consecutive non-heavy buckets with at most 4096 keys in all
+// (contiguous in memory), sorted by a 512-thread CTA (two per SM), or one
+// bucket of 4097 to 8192 keys, sorted by a 1024-thread CTA.  A unit of
+// capacity 2^c is split into at most 2^c sub-buckets by the top c bits of
+// key - min in one counting pass through shared memory (16-bit counters, two
+// to a word: no count or offset exceeds the capacity); a key of a sub-bucket
+// of at most 16 keys finds its place by counting the smaller keys there, and
+// the larger sub-buckets (in practice a moderately frequent key among a few
+// others) are split again by warps.  The next unit's keys are prefetched into
+// shared memory (cp.async) while one is sorted.  A unit whose large ranges
+// overflow the round list is finished by a bitonic network instead.
+template <int kThreadsT, int kCapBits>
+struct BsGeom {
+  static constexpr int kThreads = kThreadsT;
+  static constexpr int kWarps = kThreads / 32;
+  static constexpr int kCap = 1 << kCapBits;       // keys of a unit
+  static constexpr int kIpt = kCap / kThreads;     // keys per thread
+  static constexpr int kSubBits = kCapBits;        // as many sub-buckets as keys
+  static constexpr int kSub = 1 << kSubBits;
+  static constexpr int kSubPerThread = kSub / kThreads;
+  static constexpr uint32_t kMaxBig = kCap / 16;   // large ranges a round holds (more: the bitonic sort)
+  static constexpr int kBytes = 3 * kCap * 8;      // dynamic shared memory: the unit, two prefetch buffers
+  static constexpr int kMinBlocks = kThreads <= 512 ? 2 : 1;  // resident CTAs per SM (64 registers a thread)
+  static_assert(kSub % kThreads == 0 && kSubPerThread == 8, "sub-bucket ownership: four words per thread");
+  static_assert(kSub <= 65535 && kCap <= 65535, "16-bit sub-bucket counters and offsets");
+  static_assert(kWarps <= 32, "one warp partial per lane");
+};
+using BsNarrow = BsGeom<512, 12>;  // units of up to 4096 keys, two CTAs per SM
+using BsWide = BsGeom<1024, 13>;   // single buckets of up to 8192 keys
+static_assert(BsWide::kCap == kLearnBucketCap, "the wide sort takes any bucket the judge accepts");
 constexpr int kGroup = 32;  // ids one unit-list thread packs
-static_assert(kSub % kBsThreads == 0 && kSubPerThread == 8, "sub-bucket ownership: four words per thread");
-static_assert(kSub <= 65535 && kLearnBucketCap <= 65535, "16-bit sub-bucket counters and offsets");
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
 
 constexpr uint32_t kBigSub = 16;     // larger ranges are split by a warp
-constexpr uint32_t kMaxBig = 512;    // such ranges a round holds (more: the bitonic sort)
 constexpr int kSplitBits = 5;        // a warp splits a range into 32 bins
 constexpr int kMaxRounds = (64 + kSplitBits - 1) / kSplitBits;  // each round drops 5 bits of key range
 
+template <class G>
 struct BsShared {
-  uint2 big[2][kMaxBig];       // [lo, hi) ranges of more than kBigSub keys: this round's, the next
+  uint2 big[2][G::kMaxBig];        // [lo, hi) ranges of more than kBigSub keys: this round's, the next
   uint32_t nbig[2];
-  uint32_t bins[kBsWarps][32]; // per-warp bin counters of the split
-  __align__(16) uint32_t sub[kSub / 2 + 4];  // 16-bit counters, then offsets; entry kSub = the unit's size (uint4-aligned clears)
-  uint64_t red[2 * kBsWarps];  // per-warp key min / max
-  uint32_t warp_sum[kBsWarps]; // per-warp totals of the sub-bucket counts
+  uint32_t bins[G::kWarps][32];    // per-warp bin counters of the split
+  __align__(16) uint32_t sub[G::kSub / 2 + 4];  // 16-bit counters, then offsets; entry kSub = the unit's size (uint4-aligned clears)
+  uint64_t red[2 * G::kWarps];     // per-warp key min / max
+  uint32_t warp_sum[G::kWarps];    // per-warp totals of the sub-bucket counts
   uint32_t flag;
 };
 
 // Sorts one unit whose keys the threads hold (key j of thread t is element
-// j * kBsThreads + t) into g[0, cnt), 2 <= cnt <= kLearnBucketCap; every
-// thread calls it.
-__device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g, uint32_t cnt,
-                          uint64_t* __restrict__ s_out, uint64_t* __restrict__ s_tmp, BsShared& sh) {
+// j * G::kThreads + t) into g[0, cnt), 2 <= cnt <= G::kCap; every thread
+// calls it.
+template <class G>
+__device__ void sort_unit(const uint64_t (&k)[G::kIpt], uint64_t* __restrict__ g, uint32_t cnt,
+                          uint64_t* __restrict__ s_out, uint64_t* __restrict__ s_tmp, BsShared<G>& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint16_t* sub16 = reinterpret_cast<const uint16_t*>(sh.sub);  // the offsets, after the scan
-  uint32_t v[kBsIpt];  // sub-bucket << 16 | slot
+  uint32_t v[G::kIpt];  // sub-bucket << 16 | slot
   uint64_t kmn = ~0ull, kmx = 0;
 #pragma unroll
-  for (int j = 0; j < kBsIpt; ++j) {
-    const uint32_t i = uint32_t(j * kBsThreads + tid);
+  for (int j = 0; j < G::kIpt; ++j) {
+    const uint32_t i = uint32_t(j * G::kThreads + tid);
     if (i < cnt) {
       kmn = umin64(kmn, k[j]);
       kmx = umax64(kmx, k[j]);
@@ -1093,17 +1106,16 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
   }
   if (lane == 0) {
     sh.red[warp] = kmn;
-    sh.red[kBsWarps + warp] = kmx;
+    sh.red[G::kWarps + warp] = kmx;
   }
   if (tid == 0) {
     sh.flag = 0;
     sh.nbig[0] = sh.nbig[1] = 0;
   }
   __syncthreads();
-  {  // every warp folds the 32 per-warp partials itself: no second barrier
-    static_assert(kBsWarps == 32, "one partial per lane");
-    kmn = sh.red[lane];
-    kmx = sh.red[kBsWarps + lane];
+  {  // every warp folds the per-warp partials itself: no second barrier
+    kmn = lane < G::kWarps ? sh.red[lane] : ~0ull;
+    kmx = lane < G::kWarps ? sh.red[G::kWarps + lane] : 0ull;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       kmn = umin64(kmn, __shfl_xor_sync(0xffffffffu, kmn, o));
@@ -1112,17 +1124,17 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
   }
   const uint64_t krange = kmx - kmn;
   if (krange == 0) {  // all keys equal: already in order
-    for (uint32_t i = tid; i < cnt; i += kBsThreads) g[i] = kmn;
+    for (uint32_t i = tid; i < cnt; i += G::kThreads) g[i] = kmn;
     return;
   }
-  // sub-bucket = the top 12 bits of key - min: the map is near-linear inside
+  // sub-bucket = the top kSubBits bits of key - min: the map is near-linear inside
   // a unit, so the keys spread about evenly over the sub-buckets, except for
   // runs of one key, which the warp split below takes apart cheaply
   const int bits = 64 - __clzll(static_cast<long long>(krange));
-  const int shf = bits > kSubBits ? bits - kSubBits : 0;
+  const int shf = bits > G::kSubBits ? bits - G::kSubBits : 0;
 #pragma unroll
-  for (int j = 0; j < kBsIpt; ++j) {
-    const uint32_t i = uint32_t(j * kBsThreads + tid);
+  for (int j = 0; j < G::kIpt; ++j) {
+    const uint32_t i = uint32_t(j * G::kThreads + tid);
     if (i < cnt) {
       const uint32_t sb = uint32_t((k[j] - kmn) >> shf);
       const uint32_t half = (sb & 1u) * 16u;
@@ -1130,7 +1142,7 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
     }
   }
   __syncthreads();
-  uint32_t own[kSubPerThread], sum = 0;
+  uint32_t own[G::kSubPerThread], sum = 0;
   {
     const uint4 w = reinterpret_cast<const uint4*>(sh.sub)[tid];
     const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
@@ -1141,7 +1153,7 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
     }
   }
 #pragma unroll
-  for (int q = 0; q < kSubPerThread; ++q) sum += own[q];
+  for (int q = 0; q < G::kSubPerThread; ++q) sum += own[q];
   uint32_t inc = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1152,7 +1164,7 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
   __syncthreads();
   uint32_t before;
   {  // every warp scans the warp totals itself: no second barrier
-    uint32_t y = sh.warp_sum[lane];
+    uint32_t y = lane < G::kWarps ? sh.warp_sum[lane] : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
@@ -1171,20 +1183,20 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
     }
     reinterpret_cast<uint4*>(sh.sub)[tid] = make_uint4(ws[0], ws[1], ws[2], ws[3]);
   }
-  if (tid == kBsThreads - 1) sh.sub[kSub / 2] = cnt;
+  if (tid == G::kThreads - 1) sh.sub[G::kSub / 2] = cnt;
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < kBsIpt; ++j) {
-    const uint32_t i = uint32_t(j * kBsThreads + tid);
+  for (int j = 0; j < G::kIpt; ++j) {
+    const uint32_t i = uint32_t(j * G::kThreads + tid);
     if (i < cnt) s_tmp[sub16[v[j] >> 16] + (v[j] & 0xFFFFu)] = k[j];
   }
 #pragma unroll
-  for (int q = 0; q < kSubPerThread; ++q) {  // sub-buckets above kBigSub keys go to the warp split below
-    const int sb = tid * kSubPerThread + q;
+  for (int q = 0; q < G::kSubPerThread; ++q) {  // sub-buckets above kBigSub keys go to the warp split below
+    const int sb = tid * G::kSubPerThread + q;
     const uint32_t lo = sub16[sb], hi = sub16[sb + 1];
     if (hi - lo > kBigSub) {
       const uint32_t at = atomicAdd(&sh.nbig[0], 1u);
-      if (at < kMaxBig) sh.big[0][at] = make_uint2(lo, hi); else sh.flag = 1;
+      if (at < G::kMaxBig) sh.big[0][at] = make_uint2(lo, hi); else sh.flag = 1;
     }
   }
   __syncthreads();
@@ -1192,7 +1204,7 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
   // keys there below it + the equal keys before p: independent loads, and
   // the lanes of a warp take consecutive positions, so they mostly read the
   // same words
-  for (uint32_t p = uint32_t(tid); p < cnt; p += kBsThreads) {
+  for (uint32_t p = uint32_t(tid); p < cnt; p += G::kThreads) {
     const uint64_t key = s_tmp[p];
     const uint32_t sb = uint32_t((key - kmn) >> shf);
     const uint32_t lo = sub16[sb], hi = sub16[sb + 1];
@@ -1218,7 +1230,7 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
     const uint32_t nr = sh.nbig[cur];
     if (sh.flag || nr == 0) break;
     uint32_t* wb = sh.bins[warp];
-    for (uint32_t b = uint32_t(warp); b < nr; b += kBsWarps) {
+    for (uint32_t b = uint32_t(warp); b < nr; b += G::kWarps) {
       const uint2 rg = sh.big[cur][b];
       uint64_t mn = ~0ull, mx = 0;
       for (uint32_t i = rg.x + lane; i < rg.y; i += 32) {
@@ -1256,7 +1268,7 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
       __syncwarp();
       if (c > kBigSub) {
         const uint32_t at = atomicAdd(&sh.nbig[cur ^ 1], 1u);
-        if (at < kMaxBig) sh.big[cur ^ 1][at] = make_uint2(start, start + c); else sh.flag = 1;
+        if (at < G::kMaxBig) sh.big[cur ^ 1][at] = make_uint2(start, start + c); else sh.flag = 1;
       } else {
         for (uint32_t x = start + 1; x < start + c; ++x) {
           const uint64_t key = s_out[x];
@@ -1279,11 +1291,11 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
   if (sh.flag) {  // bitonic network over the next power of two, padded with the largest key
     uint32_t p2 = 2;
     while (p2 < cnt) p2 <<= 1;
-    for (uint32_t i = cnt + tid; i < p2; i += kBsThreads) s_out[i] = ~0ull;
+    for (uint32_t i = cnt + tid; i < p2; i += G::kThreads) s_out[i] = ~0ull;
     __syncthreads();
     for (uint32_t size = 2; size <= p2; size <<= 1) {
       for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-        for (uint32_t i = tid; i < p2 / 2; i += kBsThreads) {
+        for (uint32_t i = tid; i < p2 / 2; i += G::kThreads) {
           const uint32_t a = 2 * i - (i & (stride - 1)), c = a + stride;
           const bool up = (a & size) == 0;
           const uint64_t x = s_out[a], y = s_out[c];
@@ -1296,22 +1308,27 @@ __device__ void sort_unit(const uint64_t (&k)[kBsIpt], uint64_t* __restrict__ g,
       }
     }
   }
-  for (uint32_t i = tid; i < cnt; i += kBsThreads) g[i] = s_out[i];
-  for (int i = tid; i < kSub / 2 + 4; i += kBsThreads) sh.sub[i] = 0;
+  for (uint32_t i = tid; i < cnt; i += G::kThreads) g[i] = s_out[i];
+  for (int i = tid; i < G::kSub / 2 + 4; i += G::kThreads) sh.sub[i] = 0;
 }
 
-// The unit list (units + 1; units[0].x counts them; order arbitrary): each
-// thread walks kGroup consecutive ids and packs runs of non-heavy buckets into
-// units of at most the capacity (contiguous in memory); heavy ids end a unit.
+// The unit lists (order arbitrary).  units[1 .. units[0].x] are the narrow
+// units: each thread walks kGroup consecutive ids and packs runs of
+// non-heavy buckets into units of at most BsNarrow::kCap keys (contiguous in
+// memory); heavy ids end a unit.  A bucket above that capacity is a wide unit
+// of its own, units[nb], units[nb - 1], ... (units[0].y of them).  Every unit
+// holds a bucket with two or more keys that no other unit holds, so the two
+// lists stay within units[1 .. nb] without meeting.
 __global__ void learn_units_kernel(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets,
                                    const uint32_t* __restrict__ bitmap, uint32_t nb, uint2* __restrict__ units,
                                    uint32_t* status) {
   const uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi * kGroup >= nb) return;
-  uint32_t* count = &units[0].x;
+  uint32_t* narrow = &units[0].x;
+  uint32_t* wide = &units[0].y;
   uint32_t start = 0, tot = 0;
   auto close = [&]() {
-    if (tot >= 2) units[1 + atomicAdd(count, 1u)] = make_uint2(start, tot);
+    if (tot >= 2) units[1 + atomicAdd(narrow, 1u)] = make_uint2(start, tot);
     tot = 0;
   };
   for (uint32_t id = gi * kGroup; id < nb && id < (gi + 1) * kGroup; ++id) {
@@ -1320,55 +1337,64 @@ __global__ void learn_units_kernel(const uint32_t* __restrict__ counts, const ui
       continue;
     }
     const uint32_t c = counts[id];
-    if (c > uint32_t(kLearnBucketCap)) {  // the judge rejects such maps; never sort past capacity
+    if (c > uint32_t(BsWide::kCap)) {  // the judge rejects such maps; never sort past capacity
       atomicOr(status, kDevBadBucket);
       close();
       continue;
     }
-    if (tot + c > uint32_t(kLearnBucketCap)) close();
+    if (c > uint32_t(BsNarrow::kCap)) {
+      close();
+      units[nb - atomicAdd(wide, 1u)] = make_uint2(offsets[id], c);
+      continue;
+    }
+    if (tot + c > uint32_t(BsNarrow::kCap)) close();
     if (tot == 0) start = offsets[id];
     tot += c;
   }
   close();
 }
 
-__global__ void __launch_bounds__(kBsThreads, 1) learn_bucket_sort_kernel(uint64_t* __restrict__ keys,
-                                                                          const uint2* __restrict__ units) {
-  extern __shared__ uint64_t s_dyn[];  // [3][kLearnBucketCap]: the unit, two prefetch buffers
+// Unit u of a list is list[step * u] (step +1: the narrow list from its
+// start, -1: the wide list from its end); *count units in all.
+template <class G>
+__global__ void __launch_bounds__(G::kThreads, G::kMinBlocks)
+    learn_bucket_sort_kernel(uint64_t* __restrict__ keys, const uint2* __restrict__ list, int step,
+                             const uint32_t* __restrict__ count) {
+  extern __shared__ uint64_t s_dyn[];  // [3][G::kCap]: the unit, two prefetch buffers
   uint64_t* s_out = s_dyn;
-  __shared__ BsShared sh;
+  __shared__ BsShared<G> sh;
   const int tid = threadIdx.x;
-  const uint32_t nunits = units[0].x;
-  const uint2* list = units + 1;
-  for (int i = tid; i < kSub / 2 + 4; i += kBsThreads) sh.sub[i] = 0;
+  const uint32_t nunits = *count;
+  for (int i = tid; i < G::kSub / 2 + 4; i += G::kThreads) sh.sub[i] = 0;
+  auto at = [&](uint32_t u) { return list[ptrdiff_t(step) * ptrdiff_t(u)]; };
   auto prefetch = [&](uint2 x, int buf) {
-    uint64_t* dst = s_dyn + (1 + buf) * kLearnBucketCap;
-    for (uint32_t i = tid; i < x.y; i += kBsThreads) cp_async8(&dst[i], &keys[x.x + i]);
+    uint64_t* dst = s_dyn + (1 + buf) * G::kCap;
+    for (uint32_t i = tid; i < x.y; i += G::kThreads) cp_async8(&dst[i], &keys[x.x + i]);
     cp_async_commit();
   };
   uint32_t u = blockIdx.x;
   uint2 cur = make_uint2(0, 0);
   int buf = 0;
   if (u < nunits) {
-    cur = list[u];
+    cur = at(u);
     prefetch(cur, 0);
   }
   while (u < nunits) {
     const uint32_t nx = u + gridDim.x;
-    const uint2 next = nx < nunits ? list[nx] : make_uint2(0, 0);
+    const uint2 next = nx < nunits ? at(nx) : make_uint2(0, 0);
     cp_async_wait_all();
     __syncthreads();
-    const uint64_t* s_pre = s_dyn + (1 + buf) * kLearnBucketCap;
-    uint64_t k[kBsIpt];
+    const uint64_t* s_pre = s_dyn + (1 + buf) * G::kCap;
+    uint64_t k[G::kIpt];
 #pragma unroll
-    for (int j = 0; j < kBsIpt; ++j) {
-      const uint32_t i = uint32_t(j * kBsThreads + tid);
+    for (int j = 0; j < G::kIpt; ++j) {
+      const uint32_t i = uint32_t(j * G::kThreads + tid);
       k[j] = i < cur.y ? s_pre[i] : 0;
     }
     // the other buffer was read in the previous iteration, before the barrier above
     if (nx < nunits) prefetch(next, buf ^ 1);
     // this unit's prefetch buffer is consumed (the keys are in registers): it is the scratch
-    sort_unit(k, keys + cur.x, cur.y, s_out, s_dyn + (1 + buf) * kLearnBucketCap, sh);
+    sort_unit<G>(k, keys + cur.x, cur.y, s_out, s_dyn + (1 + buf) * G::kCap, sh);
     u = nx;
     cur = next;
     buf ^= 1;
@@ -1687,6 +1713,23 @@ cudaError_t launch_learn_fill(const LearnedMap& mp, const LearnedState* st, cons
   return cudaGetLastError();
 }
 
+template <class G>
+cudaError_t launch_bucket_sort_geom(uint64_t* keys, const uint2* list, int step, const uint32_t* count, int sms,
+                                    cudaStream_t stream) {
+  static const int per_sm = [] {  // resident CTAs per SM (0: the attributes could not be set)
+    int v = 0;
+    if (set_smem_attrs(learn_bucket_sort_kernel<G>, G::kBytes, true) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, learn_bucket_sort_kernel<G>, G::kThreads, G::kBytes) !=
+        cudaSuccess)
+      return 0;
+    return v < 1 ? 1 : v;
+  }();
+  if (!per_sm) return cudaErrorInvalidConfiguration;
+  learn_bucket_sort_kernel<G><<<unsigned(sms) * unsigned(per_sm), G::kThreads, G::kBytes, stream>>>(keys, list, step,
+                                                                                                     count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_learn_bucket_sort(uint64_t* keys, const uint32_t* counts, const uint32_t* offsets,
                                      const uint32_t* bitmap, uint32_t nb, uint2* units, uint32_t* status, int sms,
                                      cudaStream_t stream) {
@@ -1695,20 +1738,9 @@ cudaError_t launch_learn_bucket_sort(uint64_t* keys, const uint32_t* counts, con
   if (e != cudaSuccess) return e;
   learn_units_kernel<<<grid_for(ngroups, 256), 256, 0, stream>>>(counts, offsets, bitmap, nb, units, status);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  constexpr int kBytes = 3 * kLearnBucketCap * 8;
-  static const int per_sm = [] {  // resident CTAs per SM (0: the attributes could not be set)
-    int v = 0;
-    if (set_smem_attrs(learn_bucket_sort_kernel, kBytes, true) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, learn_bucket_sort_kernel, kBsThreads, kBytes) != cudaSuccess)
-      return 0;
-    return v < 1 ? 1 : v;
-  }();
-  if (!per_sm) return cudaErrorInvalidConfiguration;
-  const uint64_t want = uint64_t(sms) * per_sm;
-  const unsigned grid = unsigned(ngroups < want ? ngroups : want);
-  learn_bucket_sort_kernel<<<grid, kBsThreads, kBytes, stream>>>(keys, units);
-  return cudaGetLastError();
+  if (e == cudaSuccess) e = launch_bucket_sort_geom<BsNarrow>(keys, units + 1, 1, &units[0].x, sms, stream);
+  if (e == cudaSuccess) e = launch_bucket_sort_geom<BsWide>(keys, units + nb, -1, &units[0].y, sms, stream);
+  return e;
 }
 
 cudaError_t launch_learn_bucket_ids(const uint64_t* keys, uint64_t n, const LearnedMap& mp, uint32_t* ids,

@@ -45,12 +45,15 @@ def heavy_of(keys, min_count):
     return u[c >= min_count][: fs.FSORT_LEARN_MAX_HEAVY]
 
 
-def empirical_table(keys, heavy):
-    """A map table from the data's own CDF (non-heavy keys): balanced by construction."""
+def empirical_table(keys, heavy, warp=None):
+    """A map table from the data's own CDF (non-heavy keys): balanced by construction,
+    unless `warp` (a monotone map of [0, 1] onto itself) is applied to the CDF."""
     nh = np.sort(keys[~np.isin(keys, heavy)])
     starts = ol.cell_start(np.arange(ol.CELLS, dtype=np.uint64))
     t = np.zeros((ol.CELLS + 1, 2), np.uint32)
     frac = np.searchsorted(nh, starts, side="left") / max(nh.size, 1)
+    if warp is not None:
+        frac = warp(frac)
     t[:ol.CELLS, 0] = np.minimum(np.floor(frac * 2.0 ** 32), 0xFFFFFFFF).astype(np.uint64)
     t[:ol.CELLS, 1] = np.searchsorted(heavy, starts, side="left")
     t[ol.CELLS] = (0xFFFFFFFF, heavy.size)
@@ -148,6 +151,27 @@ def test_sort_with_balanced_table_matches_oracle(n):
     assert (st["max_bucket"], st["limit"], st["buckets"]) == (mx, limit, b)
     if n >= 70_001:
         assert ok  # the data's own CDF balances the buckets
+
+
+def test_buckets_above_the_narrow_unit_capacity_sort_exactly():
+    """A CDF squeezed five-fold over a band of 16 bucket widths: a dozen buckets of 4,600 to
+    4,750 keys, above the 4,096 keys a narrow unit holds but within the judge's limit (8 x 1,024),
+    so they take the wide bucket sort while the rest are packed into narrow units."""
+    n = 1 << 20
+    keys = mixture(n, stream=6)
+    heavy = heavy_of(keys, n // 4096)
+    d = 16 / 1024
+    table = empirical_table(keys, heavy, lambda f: np.interp(f, [0.0, 0.1, 0.1 + 5 * d, 1.0],
+                                                             [0.0, 0.1, 0.1 + d, 1.0]))
+    ok, mx, limit, b = ol.judge(keys, table, heavy)
+    ids = ol.bucket_ids(keys, table, heavy, n)
+    wide = int((np.bincount(ids[~np.isin(keys, heavy)]) > 4096).sum())
+    assert ok and wide >= 8 and 4096 < mx <= limit
+    with learned_plan(n) as plan:
+        fs.fsort_learned_set_model(plan.handle, cells=table, heavy=heavy, center=0.6, half=0.3)
+        sort_and_check(plan, keys)
+        st = plan.learned_stats()
+    assert st["used"] == 1 and (st["max_bucket"], st["limit"], st["buckets"]) == (mx, limit, b)
 
 
 def test_sort_rejected_by_judge_falls_back_exactly():
