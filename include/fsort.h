@@ -529,8 +529,6 @@ FSORT_API fsort_status fsort_plan_timing_report(fsort_plan* plan, fsort_kernel_t
  *   - The call is synchronous: it enqueues its kernels and the read-back of
  *     its status word on `stream`, waits for that stream (and for nothing
  *     else), and returns FSORT_ERR_TIMEOUT if a device-side wait gave up.
- *     Because it waits, it must not be called on a stream that is capturing
- *     a CUDA graph.
  *   - All calls on one device share its array, which keeps the last call's
  *     contents (the call clears what must start at zero).  The library lets
  *     one call at a time per device use it: calls from several host threads
